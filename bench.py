@@ -1,0 +1,265 @@
+"""Benchmark: certified minimum distance on one GB300 (or N replicas).
+
+One step certifies d of the workload code once, the whole hot path
+(every pass of the Brouwer-Zimmermann search, Sec. 3.1 Alg. 6, on the
+device).  Default workload: the F_3 [80,40] random systematic code
+(PCG64 seed 2), the largest single-code configuration.
+
+value     codewords/s of the device search with the code's tables already
+          resident in HBM (CUDA events around each step; L2 flushed between
+          steps with a 256 MiB memset outside the timed windows).
+e2e       the same metric through fpcode_min_distance() from a host matrix:
+          host preparation, H2D, search, D2H read-back of the result.
+roofline  the enumeration kernel against the POPC issue ceiling of the SMs
+          (16 POPC lane-ops per clock per SM at the maximum SM clock).
+cpu_baseline  the CPU oracle (test infrastructure) on the same code, all
+          host cores.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W]
+                       [--impl ours|reference] [--workload NAME]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "f3_n80_k40": "F_3 [80,40] random systematic code G=[I|A], A uniform, PCG64 seed 2",
+    "f7_n40_k20": "F_7 [40,20] random systematic code G=[I|A], A uniform, PCG64 seed 1",
+    "f3_n30_k15": "F_3 [30,15] random systematic code G=[I|A], A uniform, PCG64 seed 0",
+}
+POPC_PER_CLK_SM = 16.0   # measured by fpcode_int_peaks on GB300 (and CUDA's documented rate)
+SM_MAX_MHZ = 2070.0      # GB300 maximum SM clock
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        mhz, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                mhz.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+def cpu_baseline(code, budget_s: float = 30.0) -> dict:
+    """The oracle as it stands, on every host core, on the same code."""
+    import oracle
+
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    r = oracle.bz(code, threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": r.evaluated / dt, "unit": "codewords/s", "cores": threads, "kind": "oracle",
+            "sample": f"full certified search of the same code ({r.evaluated} codewords, d={r.d}) in {dt:.2f} s",
+            "d": r.d, "seconds": dt}
+
+
+def run_reference(args, code, rank: int):
+    """Reference arm: the CPU oracle on the host cores, same metric."""
+    if rank != 0:
+        return
+    import oracle
+
+    threads = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle.bz(code, threads=threads)
+    times, ev = [], 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle.bz(code, threads=threads)
+        times.append(time.perf_counter() - t0)
+        ev = r.evaluated
+    total = sum(times)
+    value = ev * args.steps / total
+    line = {
+        "impl": "reference", "metric": "codewords_per_s", "value": value, "unit": "codewords/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "d": r.d},
+        "cpu_baseline": {"value": value, "unit": "codewords/s", "cores": threads, "kind": "oracle",
+                         "sample": f"full certified search of the same code per step ({ev} codewords)"},
+        "e2e": {"value": value, "unit": "codewords/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="f3_n80_k40", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    from paper_2603_29942_gb300 import inputs
+
+    rank, world, local = dist_env()
+    code = inputs.single(args.workload)
+    if args.impl == "reference":
+        run_reference(args, code, rank)
+        return
+
+    import torch
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2603_29942_gb300 import _binding as B
+    from paper_2603_29942_gb300 import build as _b
+
+    _b.build()
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    # --- value: device search on resident tables ---
+    prep = B.fpcode_prepare(code.p, code.n, code.k, code.G)
+    B.fpcode_prepared_upload(prep, stream)
+    for _ in range(args.warmup):
+        B.fpcode_search_enqueue(prep, stream)
+        res = B.fpcode_search_finish(prep, stream)
+    assert res.status == B.OK
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kern = []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            for i in range(args.steps):
+                flush.fill_(i & 0xFF)  # L2 flush, outside the timed window
+                evs[i][0].record(stream)
+                B.fpcode_search_enqueue(prep, stream)
+                evs[i][1].record(stream)
+                r = B.fpcode_search_finish(prep, stream, want_witness=(i == args.steps - 1))
+                assert r.status == B.OK and r.d == res.d
+                kern.append(r.t_kernel_ms)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    t_ms = sum(step_ms)
+    codewords = r.enumerated  # evaluated per step (the last step; all steps enumerate the same passes)
+    counts_total = sum(r.counts)
+    if world > 1:
+        t = torch.tensor([t_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(t.item())
+    value = world * codewords * args.steps / (t_ms * 1e-3)
+
+    # --- e2e: public API from host matrices, with copies ---
+    h2d, d2h = B.fpcode_prepared_bytes(prep)
+    G_host = torch.from_numpy(code.G.copy()).pin_memory().numpy()
+    for _ in range(3):
+        B.fpcode_min_distance(code.p, code.n, code.k, G_host, stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        d, _w = B.fpcode_min_distance(code.p, code.n, code.k, G_host, stream)
+        assert d == res.d
+    e2e_s = time.perf_counter() - t0
+    e2e_value = world * counts_total * args.steps / e2e_s
+
+    # --- roofline of the enumeration kernel ---
+    kern_ms = statistics.mean(kern)
+    W = max(1, -(-(code.n - code.k) // 32))
+    popc_per_cw = W  # one popcount per 32-bit word of the redundant part
+    achieved = codewords * popc_per_cw / (kern_ms * 1e-3) / 1e12
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peak = POPC_PER_CLK_SM * sms * SM_MAX_MHZ * 1e6 / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tpopc/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "bz_kernel", "ops_per_codeword": popc_per_cw,
+            "peak_basis": f"{POPC_PER_CLK_SM:.0f} POPC/clk/SM x {sms} SMs x {SM_MAX_MHZ:.0f} MHz"}
+
+    line = {
+        "metric": "codewords_per_s", "value": value, "unit": "codewords/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "d": res.d,
+                   "codewords_per_step": codewords, "schedule_codewords": counts_total,
+                   "time_to_certified_d_ms": t_ms / args.steps, "l2": "flushed between timed steps (256 MiB memset)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": "codewords/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": 1e3 * e2e_s / args.steps},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(code)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,208 @@
+/*
+ * fpcode.h -- C ABI of libfpcode: certified minimum Hamming distance of a
+ * linear [n,k] code over a prime field F_p on one NVIDIA GB300 (sm_103a).
+ *
+ * The method is the Brouwer-Zimmermann search of arXiv 2603.29942
+ * (Sec. 3.1, Alg. 6): for each systematic generator matrix Gamma_j of the
+ * code on disjoint information sets, every codeword that is a combination
+ * of exactly g rows with nonzero coefficients is enumerated; g grows until
+ * the lower bound L meets the best weight U found.  Codewords are held in
+ * the paper's bit-sliced natural encoding (Sec. 2, Sec. 4.1), so F_p
+ * addition is a boolean formula over 32-bit words (Alg. 3, Alg. 4) and a
+ * weight is the popcount of the OR of the slices (Sec. 4.3).
+ *
+ * Conventions for every call:
+ *   - Returns an fpcode status (FPCODE_OK = 0).  Outputs are written only on
+ *     FPCODE_OK, except that FPCODE_EBUDGET / FPCODE_ETIMEOUT still fill the
+ *     certified interval [L, U] and the counts of an fpcode_result.
+ *   - Matrices are row-major uint8 arrays in host memory with entries in
+ *     [0, p); they are copied, never retained.
+ *   - `stream` is a cudaStream_t (NULL: the legacy default stream).  Calls
+ *     that return results synchronise that stream before returning.
+ *   - Device memory belongs to the library (per-device workspace, or the
+ *     prepared object / server that asked for it).
+ *   - Limits: p an odd prime < 256; 1 <= k <= 64; k <= n <= 255;
+ *     n - k <= 128; a code whose bit-sliced row multiples of one
+ *     information set exceed 96 KiB is rejected (FPCODE_EINVAL).
+ *     Passes beyond 255 per code or beyond 2^34 prefixes are not entered
+ *     (FPCODE_EBUDGET with [L, U]).
+ *   - Thread safety: calls on different prepared objects / servers may run
+ *     concurrently; calls that use the shared per-device workspace
+ *     (fpcode_min_distance, fpcode_min_distance_batch) serialise on it.
+ */
+#ifndef FPCODE_H
+#define FPCODE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FPCODE_MAX_K 64
+#define FPCODE_MAX_N 255
+#define FPCODE_MAX_M 255
+
+enum fpcode_status {
+  FPCODE_OK = 0,
+  FPCODE_EINVAL = 1,   /* bad argument: p not an odd prime < 256, k, n out of range,
+                          an entry >= p, rank(G) < k, a table too large */
+  FPCODE_ENOMEM = 2,   /* host or device allocation failed */
+  FPCODE_ECUDA = 3,    /* a CUDA call failed (message: fpcode_last_error) */
+  FPCODE_EBUDGET = 4,  /* not certified within the budget: L < U returned */
+  FPCODE_ETIMEOUT = 5, /* time limit, or a bounded device wait gave up */
+  FPCODE_EBUSY = 6,    /* serving: no free slot */
+  FPCODE_ENOTREADY = 7 /* serving: the ticket is still running */
+};
+
+/* Search options.  fpcode_opts_default() fills the defaults shown. */
+typedef struct fpcode_opts {
+  int per_round_check; /* 0: test L >= U after every pass (default);
+                          1: only after each full round g (Alg. 6 line 3) */
+  int defer;           /* 1 (default): a rank-deficient Gamma_j is first
+                          enumerated in round g = k - k_j (it cannot raise L
+                          earlier), catching up its levels 1..g */
+  int mid_pass_exit;   /* 1 (default): stop a pass as soon as U <= L held
+                          before it (early termination, Sec. 4.4); d and the
+                          per-level counts are unchanged, `enumerated` and
+                          the choice among equal-weight witnesses may vary */
+  int ctas_per_sm;     /* 0: from the occupancy calculator */
+  int prefixes_per_lane; /* 0: autotuned per pass; else fixed (1..64) */
+  int reserved0;
+  uint64_t budget;     /* 0: unlimited; else a pass is not entered if it
+                          would take the per-level count total above it */
+  double timeout_s;    /* 0: none; else time limit of one device search */
+  double wait_limit_s; /* bound on one device wait at a pass hand-off
+                          (default 10 s); past it the kernel exits with
+                          FPCODE_ETIMEOUT instead of spinning */
+  int reserved[4];
+} fpcode_opts;
+
+typedef struct fpcode_result {
+  int status;          /* FPCODE_OK: d certified */
+  int d;               /* minimum distance (FPCODE_OK), else -1 */
+  int L;               /* lower bound when the search stopped */
+  int U;               /* best weight found (upper bound) */
+  int m;               /* number of information sets */
+  int npasses;         /* passes entered (last pass index + 1) */
+  int reserved0, reserved1;
+  uint64_t enumerated; /* codewords the GPU evaluated */
+  uint64_t counts[FPCODE_MAX_K + 1]; /* per level g: codewords of the passes
+                          entered, C(k,g)(p-1)^(g-1) each (equals the
+                          enumeration when mid_pass_exit = 0) */
+  int kj[FPCODE_MAX_M]; /* fresh pivot columns of each Gamma_j */
+  int reserved2;
+  double t_prepare_ms; /* host elimination and bit-slicing */
+  double t_h2d_ms;     /* upload */
+  double t_kernel_ms;  /* device search (CUDA events) */
+  double t_d2h_ms;     /* result read-back */
+  double t_total_ms;   /* whole call, host clock */
+} fpcode_result;
+
+typedef struct fpcode_prepared fpcode_prepared; /* opaque, library-owned */
+
+/* Fill *o with the defaults. */
+void fpcode_opts_default(fpcode_opts *o);
+
+/* Text of the last error on this thread (never NULL). */
+const char *fpcode_last_error(void);
+
+/* Host preparation (not on the hot path): Gaussian elimination mod p of G
+ * into Gamma_1..Gamma_m on disjoint information sets (Sec. 3.1; the paper
+ * leaves the choice open -- Gamma_1 pivots on the leftmost independent
+ * columns, each later Gamma_j greedily on the leftmost columns unused so
+ * far, completed with used ones if rank-deficient), the p-1 multiples of
+ * every row restricted to the non-pivot columns, bit-sliced into
+ * ceil((n-k)/32) words per slice (Sec. 2, Sec. 4.1), and the pass
+ * schedule.  G: k x n, row-major, entries in [0, p), copied.  opts may be
+ * NULL.  On success *out owns host memory; free with fpcode_prepared_free.
+ * Errors: FPCODE_EINVAL, FPCODE_ENOMEM. */
+int fpcode_prepare(int p, int n, int k, const uint8_t *G, const fpcode_opts *opts, fpcode_prepared **out);
+
+/* Release a prepared object and its device copy (if any).  NULL is a no-op. */
+void fpcode_prepared_free(fpcode_prepared *prep);
+
+/* Copy the prepared tables into device memory owned by `prep` (once; later
+ * calls are no-ops), enqueued on `stream`, synchronised before return.
+ * Errors: FPCODE_ENOMEM, FPCODE_ECUDA. */
+int fpcode_prepared_upload(fpcode_prepared *prep, void *stream);
+
+/* Enqueue one device search on the uploaded `prep` (state reset, the
+ * persistent kernel, and the read-back into pinned host memory of `prep`)
+ * without synchronising.  Pair with fpcode_search_finish on the same
+ * stream.  Errors: FPCODE_EINVAL (not uploaded), FPCODE_ECUDA. */
+int fpcode_search_enqueue(fpcode_prepared *prep, void *stream, const fpcode_opts *opts);
+
+/* Synchronise `stream` and decode the last enqueued search into *res and,
+ * if witness != NULL, a minimum-weight codeword (n bytes, caller-owned),
+ * rebuilt exactly from its Gamma_j rows and checked to have weight d. */
+int fpcode_search_finish(fpcode_prepared *prep, void *stream, fpcode_result *res, uint8_t *witness);
+
+/* Upload (if needed) + enqueue + finish. */
+int fpcode_min_distance_ex(fpcode_prepared *prep, void *stream, const fpcode_opts *opts, fpcode_result *res,
+                           uint8_t *witness);
+
+/* One call from a host matrix to a certified distance (Sec. 3.1, Alg. 6):
+ * prepare, upload, search, read back.  *d receives the minimum distance;
+ * witness (n bytes, may be NULL) a codeword of weight d.  Uses the shared
+ * per-device workspace.  Errors: as above; FPCODE_EBUDGET cannot occur
+ * (no budget). */
+int fpcode_min_distance(int p, int n, int k, const uint8_t *G, void *stream, int *d, uint8_t *witness);
+
+/* One code of a batch or a served request. */
+typedef struct fpcode_desc {
+  int p, n, k;
+  int reserved;
+  const uint8_t *G;  /* k x n, row-major, host memory, copied */
+  uint64_t budget;   /* per-code budget (0: opts->budget) */
+} fpcode_desc;
+
+/* Many codes of uneven (p, n, k) in one persistent launch: every code keeps
+ * its own pass sequence and bound; CTAs steal tasks across codes.  Codes
+ * with p outside {3, 5, 7} run in further launches.  results: num entries;
+ * witnesses: sum of n_i bytes (code i at the sum of the earlier n), may be
+ * NULL.  Returns FPCODE_OK if every code was processed (each result has
+ * its own status) or the first global error. */
+int fpcode_min_distance_batch(int num, const fpcode_desc *codes, void *stream, const fpcode_opts *opts,
+                              fpcode_result *results, uint8_t *witnesses);
+
+/* Serving: a request loop over the same persistent kernel.  Requests are
+ * admitted into free slots as device memory allows, kept resident with
+ * their bounds, and interleaved on the GPU with the codes already running;
+ * results are polled without blocking. */
+typedef struct fpcode_serve_opts {
+  int slots;              /* concurrent codes on the device (default 64) */
+  int ctas_per_sm;        /* 0: occupancy calculator */
+  size_t device_bytes;    /* device memory for code tables (default 64 MiB) */
+  double idle_exit_s;     /* persistent kernel exits after this long idle
+                             (default 0.02 s); it is relaunched on demand */
+  fpcode_opts search;     /* per-code search options */
+} fpcode_serve_opts;
+
+typedef struct fpcode_server fpcode_server;
+
+void fpcode_serve_opts_default(fpcode_serve_opts *o);
+int fpcode_serve_create(const fpcode_serve_opts *o, void *stream, fpcode_server **out);
+/* Prepare and admit one code; *ticket identifies it.  FPCODE_EBUSY: no slot
+ * or memory free right now (retry after polling). */
+int fpcode_serve_submit(fpcode_server *s, const fpcode_desc *code, uint64_t *ticket);
+/* Collect up to `max` finished codes (non-blocking).  witnesses: max * 255
+ * bytes (row i at i*255), may be NULL. */
+int fpcode_serve_poll(fpcode_server *s, fpcode_result *out, uint64_t *tickets, uint8_t *witnesses, int max,
+                      int *n_out);
+/* Wait until every admitted code has finished (bounded by timeout_ms). */
+int fpcode_serve_drain(fpcode_server *s, int timeout_ms);
+void fpcode_serve_destroy(fpcode_server *s);
+
+/* Measured integer issue rates of this GPU (LOP3, POPC, IADD lanes per
+ * clock per SM and per second), from a microbenchmark with independent
+ * instruction chains on every SM; the ceiling the enumeration kernel is
+ * compared with.  rates: 6 doubles {lop3/clk/SM, popc/clk/SM,
+ * iadd/clk/SM, lop3/s, popc/s, sm_clock_mhz}. */
+int fpcode_int_peaks(void *stream, double *rates);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FPCODE_H */

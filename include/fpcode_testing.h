@@ -1,0 +1,67 @@
+/*
+ * fpcode_testing.h -- introspection and unit hooks of libfpcode, used by
+ * the test-suite to check host logic and the bit-sliced F_p arithmetic on
+ * their own.  Not needed to compute distances.
+ */
+#ifndef FPCODE_TESTING_H
+#define FPCODE_TESTING_H
+
+#include <stdint.h>
+
+#include "fpcode.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Bit-sliced operations (lane-wise over 32 symbols; r = floor(log2 p) + 1
+ * slices per operand, slice i = bit i of the natural binary expansion,
+ * Sec. 2):
+ *   0 FPCODE_OP_ADD       exact a + b (Alg. 3 for p = 3, Alg. 4 for p = 7,
+ *                         ripple add + conditional subtract otherwise)
+ *   1 FPCODE_OP_NZ_SUB    mask of a - b != 0 (isometric subtraction, Sec. 4.3)
+ *   2 FPCODE_OP_NZ_ADD    mask of a + b != 0 (isometric addition, Sec. 4.3;
+ *                         p = 3 or p = 2^r - 1 only)
+ *   3 FPCODE_OP_NEG       -a (p = 2^r - 1 only: complement where nonzero)
+ *   4 FPCODE_OP_MUL2      2a (p = 2^r - 1 only: slice rotation, Sec. 4.2)
+ * a, b, out: r words each (out: 1 word for the masks).  Host evaluation. */
+enum { FPCODE_OP_ADD = 0, FPCODE_OP_NZ_SUB = 1, FPCODE_OP_NZ_ADD = 2, FPCODE_OP_NEG = 3, FPCODE_OP_MUL2 = 4 };
+int fpcode_test_bitslice_host(int op, int p, const uint32_t *a, const uint32_t *b, uint32_t *out);
+
+/* The same operations in a GPU kernel over `count` independent operand
+ * sets laid out back to back (a, b: count * r words; out: count * r words,
+ * or count words for the masks).  Host pointers; copies in and out. */
+int fpcode_test_bitslice_device(int op, int p, int count, const uint32_t *a, const uint32_t *b, uint32_t *out);
+
+/* Revolving-door order of t-subsets of {0..n-1}, subsets as bit masks. */
+uint64_t fpcode_test_rd_unrank(uint64_t rank, int n, int t);
+uint64_t fpcode_test_rd_rank(uint64_t subset, int n, int t);
+/* 1 and *next = successor, or 0 if `subset` is the last one. */
+int fpcode_test_rd_next(uint64_t subset, int n, int t, uint64_t *next);
+
+/* Prefix index I of pass g (k rows, prime p) -> largest row m, subset mask
+ * Q and the coefficients of Q's members in increasing row order (coefs:
+ * g - 2 ints). */
+int fpcode_test_prefix_unrank(uint64_t I, int k, int g, int p, int *m, uint64_t *Q, int *coefs);
+/* The walk the kernel takes from prefix I to I + 1, on the host: same
+ * outputs for I + 1. */
+int fpcode_test_prefix_walk(uint64_t I, uint64_t steps, int k, int g, int p, int *m, uint64_t *Q, int *coefs);
+
+/* Introspection of a prepared object. */
+typedef struct fpcode_pass_info {
+  int g, j, L_before, L_after, round_end, reserved;
+  uint64_t size;
+  uint64_t nprefix;
+} fpcode_pass_info;
+int fpcode_prepared_shape(const fpcode_prepared *prep, int *m, int *kj, int *npasses, int *complete);
+/* Gamma_j (k x n) and its pivot columns (k). */
+int fpcode_prepared_gamma(const fpcode_prepared *prep, int j, uint8_t *gamma, int *pivots);
+int fpcode_prepared_passes(const fpcode_prepared *prep, fpcode_pass_info *passes, int max);
+/* Bytes one search moves: host-to-device (tables, schedule, descriptors)
+ * and device-to-host (final state). */
+int fpcode_prepared_bytes(const fpcode_prepared *prep, uint64_t *h2d, uint64_t *d2h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FPCODE_TESTING_H */

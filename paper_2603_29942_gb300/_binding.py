@@ -1,0 +1,404 @@
+"""ctypes binding of libfpcode (include/fpcode.h, include/fpcode_testing.h).
+
+Argument marshalling only: every step of the search runs in the CUDA
+library.  Functions keep the C names.  Matrices are numpy uint8 arrays;
+``stream`` is a cudaStream_t handle as an int (0: default stream), e.g.
+``torch.cuda.current_stream().cuda_stream``.  Loading fails loudly if the
+compiled library is missing -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import build as _build
+
+MAX_K = 64
+MAX_N = 255
+MAX_M = 255
+
+OK, EINVAL, ENOMEM, ECUDA, EBUDGET, ETIMEOUT, EBUSY, ENOTREADY = range(8)
+STATUS_NAMES = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", EBUDGET: "EBUDGET",
+                ETIMEOUT: "ETIMEOUT", EBUSY: "EBUSY", ENOTREADY: "ENOTREADY"}
+
+OP_ADD, OP_NZ_SUB, OP_NZ_ADD, OP_NEG, OP_MUL2 = range(5)
+
+
+class fpcode_opts(ctypes.Structure):
+    _fields_ = [
+        ("per_round_check", ctypes.c_int),
+        ("defer", ctypes.c_int),
+        ("mid_pass_exit", ctypes.c_int),
+        ("ctas_per_sm", ctypes.c_int),
+        ("prefixes_per_lane", ctypes.c_int),
+        ("reserved0", ctypes.c_int),
+        ("budget", ctypes.c_uint64),
+        ("timeout_s", ctypes.c_double),
+        ("wait_limit_s", ctypes.c_double),
+        ("reserved", ctypes.c_int * 4),
+    ]
+
+
+class fpcode_result(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int),
+        ("d", ctypes.c_int),
+        ("L", ctypes.c_int),
+        ("U", ctypes.c_int),
+        ("m", ctypes.c_int),
+        ("npasses", ctypes.c_int),
+        ("reserved0", ctypes.c_int),
+        ("reserved1", ctypes.c_int),
+        ("enumerated", ctypes.c_uint64),
+        ("counts", ctypes.c_uint64 * (MAX_K + 1)),
+        ("kj", ctypes.c_int * MAX_M),
+        ("reserved2", ctypes.c_int),
+        ("t_prepare_ms", ctypes.c_double),
+        ("t_h2d_ms", ctypes.c_double),
+        ("t_kernel_ms", ctypes.c_double),
+        ("t_d2h_ms", ctypes.c_double),
+        ("t_total_ms", ctypes.c_double),
+    ]
+
+
+class fpcode_desc(ctypes.Structure):
+    _fields_ = [
+        ("p", ctypes.c_int),
+        ("n", ctypes.c_int),
+        ("k", ctypes.c_int),
+        ("reserved", ctypes.c_int),
+        ("G", ctypes.POINTER(ctypes.c_uint8)),
+        ("budget", ctypes.c_uint64),
+    ]
+
+
+class fpcode_serve_opts(ctypes.Structure):
+    _fields_ = [
+        ("slots", ctypes.c_int),
+        ("ctas_per_sm", ctypes.c_int),
+        ("device_bytes", ctypes.c_size_t),
+        ("idle_exit_s", ctypes.c_double),
+        ("search", fpcode_opts),
+    ]
+
+
+class fpcode_pass_info(ctypes.Structure):
+    _fields_ = [
+        ("g", ctypes.c_int),
+        ("j", ctypes.c_int),
+        ("L_before", ctypes.c_int),
+        ("L_after", ctypes.c_int),
+        ("round_end", ctypes.c_int),
+        ("reserved", ctypes.c_int),
+        ("size", ctypes.c_uint64),
+        ("nprefix", ctypes.c_uint64),
+    ]
+
+
+_lib = None
+_U8P = ctypes.POINTER(ctypes.c_uint8)
+_U32P = ctypes.POINTER(ctypes.c_uint32)
+_IP = ctypes.POINTER(ctypes.c_int)
+_VP = ctypes.c_void_p
+
+
+def _declare(lib):
+    sig = {
+        "fpcode_opts_default": (None, [ctypes.POINTER(fpcode_opts)]),
+        "fpcode_last_error": (ctypes.c_char_p, []),
+        "fpcode_prepare": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _U8P,
+                                          ctypes.POINTER(fpcode_opts), ctypes.POINTER(_VP)]),
+        "fpcode_prepared_free": (None, [_VP]),
+        "fpcode_prepared_upload": (ctypes.c_int, [_VP, _VP]),
+        "fpcode_search_enqueue": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(fpcode_opts)]),
+        "fpcode_search_finish": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(fpcode_result), _U8P]),
+        "fpcode_min_distance_ex": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(fpcode_opts),
+                                                  ctypes.POINTER(fpcode_result), _U8P]),
+        "fpcode_min_distance": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _U8P, _VP, _IP, _U8P]),
+        "fpcode_min_distance_batch": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(fpcode_desc), _VP,
+                                                     ctypes.POINTER(fpcode_opts), ctypes.POINTER(fpcode_result),
+                                                     _U8P]),
+        "fpcode_serve_opts_default": (None, [ctypes.POINTER(fpcode_serve_opts)]),
+        "fpcode_serve_create": (ctypes.c_int, [ctypes.POINTER(fpcode_serve_opts), _VP, ctypes.POINTER(_VP)]),
+        "fpcode_serve_submit": (ctypes.c_int, [_VP, ctypes.POINTER(fpcode_desc), ctypes.POINTER(ctypes.c_uint64)]),
+        "fpcode_serve_poll": (ctypes.c_int, [_VP, ctypes.POINTER(fpcode_result), ctypes.POINTER(ctypes.c_uint64),
+                                             _U8P, ctypes.c_int, _IP]),
+        "fpcode_serve_drain": (ctypes.c_int, [_VP, ctypes.c_int]),
+        "fpcode_serve_destroy": (None, [_VP]),
+        "fpcode_int_peaks": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),
+        "fpcode_test_bitslice_host": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _U32P, _U32P, _U32P]),
+        "fpcode_test_bitslice_device": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _U32P, _U32P,
+                                                       _U32P]),
+        "fpcode_test_rd_unrank": (ctypes.c_uint64, [ctypes.c_uint64, ctypes.c_int, ctypes.c_int]),
+        "fpcode_test_rd_rank": (ctypes.c_uint64, [ctypes.c_uint64, ctypes.c_int, ctypes.c_int]),
+        "fpcode_test_rd_next": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_uint64)]),
+        "fpcode_test_prefix_unrank": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int, _IP,
+                                                     ctypes.POINTER(ctypes.c_uint64), _IP]),
+        "fpcode_test_prefix_walk": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                                   ctypes.c_int, _IP, ctypes.POINTER(ctypes.c_uint64), _IP]),
+        "fpcode_prepared_shape": (ctypes.c_int, [_VP, _IP, _IP, _IP, _IP]),
+        "fpcode_prepared_gamma": (ctypes.c_int, [_VP, ctypes.c_int, _U8P, _IP]),
+        "fpcode_prepared_passes": (ctypes.c_int, [_VP, ctypes.POINTER(fpcode_pass_info), ctypes.c_int]),
+        "fpcode_prepared_bytes": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
+    }
+    found = []
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name, None)
+        if fn is None:
+            continue
+        fn.restype = res
+        fn.argtypes = args
+        found.append(name)
+    return found
+
+
+# Every entry point the headers declare (checked by the tests).
+EXPORTS: list[str] = []
+
+
+def lib():
+    """Load (building first if needed) libfpcode.so."""
+    global _lib, EXPORTS
+    if _lib is None:
+        path = _build.LIB if _build.up_to_date() else _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError("libfpcode.so is missing; run paper_2603_29942_gb300.build.build()")
+        _lib = ctypes.CDLL(path)
+        EXPORTS = sorted(_declare(_lib))
+    return _lib
+
+
+def last_error() -> str:
+    return (lib().fpcode_last_error() or b"").decode()
+
+
+class FpcodeError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {STATUS_NAMES.get(status, status)} ({last_error()})")
+        self.status = status
+
+
+def _check(status: int, what: str, ok=(OK,)):
+    if status not in ok:
+        raise FpcodeError(status, what)
+    return status
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _matrix(G) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(G, dtype=np.uint8))
+
+
+def fpcode_opts_default(**over) -> fpcode_opts:
+    o = fpcode_opts()
+    lib().fpcode_opts_default(ctypes.byref(o))
+    for k, v in over.items():
+        setattr(o, k, v)
+    return o
+
+
+@dataclass
+class Result:
+    """Python view of fpcode_result."""
+
+    status: int
+    d: int
+    L: int
+    U: int
+    m: int
+    npasses: int
+    enumerated: int
+    counts: list[int]
+    kj: list[int]
+    t_prepare_ms: float
+    t_kernel_ms: float
+    t_total_ms: float
+    witness: np.ndarray | None = field(default=None, repr=False)
+
+    @classmethod
+    def of(cls, r: fpcode_result, k: int, witness=None) -> "Result":
+        return cls(r.status, r.d, r.L, r.U, r.m, r.npasses, int(r.enumerated), [int(x) for x in r.counts[:k + 1]],
+                   [int(x) for x in r.kj[:r.m]], r.t_prepare_ms, r.t_kernel_ms, r.t_total_ms, witness)
+
+
+class Prepared:
+    """Owns an fpcode_prepared handle."""
+
+    def __init__(self, handle: int, p: int, n: int, k: int):
+        self.handle = handle
+        self.p, self.n, self.k = p, n, k
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.fpcode_prepared_free(self.handle)
+            self.handle = None
+
+
+def fpcode_prepare(p: int, n: int, k: int, G, opts: fpcode_opts | None = None) -> Prepared:
+    G = _matrix(G)
+    h = _VP()
+    _check(lib().fpcode_prepare(p, n, k, G.ctypes.data_as(_U8P), ctypes.byref(opts) if opts else None,
+                                ctypes.byref(h)), "fpcode_prepare")
+    return Prepared(h.value, p, n, k)
+
+
+def fpcode_prepared_upload(prep: Prepared, stream=None) -> None:
+    _check(lib().fpcode_prepared_upload(prep.handle, _stream(stream)), "fpcode_prepared_upload")
+
+
+def fpcode_search_enqueue(prep: Prepared, stream=None, opts: fpcode_opts | None = None) -> None:
+    _check(lib().fpcode_search_enqueue(prep.handle, _stream(stream), ctypes.byref(opts) if opts else None),
+           "fpcode_search_enqueue")
+
+
+def fpcode_search_finish(prep: Prepared, stream=None, want_witness: bool = True) -> Result:
+    r = fpcode_result()
+    w = np.zeros(prep.n, dtype=np.uint8)
+    _check(lib().fpcode_search_finish(prep.handle, _stream(stream), ctypes.byref(r),
+                                      w.ctypes.data_as(_U8P) if want_witness else None),
+           "fpcode_search_finish", ok=(OK, EBUDGET, ETIMEOUT))
+    return Result.of(r, prep.k, w if (want_witness and r.U <= prep.n) else None)
+
+
+def fpcode_min_distance_ex(prep: Prepared, stream=None, opts: fpcode_opts | None = None) -> Result:
+    r = fpcode_result()
+    w = np.zeros(prep.n, dtype=np.uint8)
+    _check(lib().fpcode_min_distance_ex(prep.handle, _stream(stream), ctypes.byref(opts) if opts else None,
+                                        ctypes.byref(r), w.ctypes.data_as(_U8P)),
+           "fpcode_min_distance_ex", ok=(OK, EBUDGET, ETIMEOUT))
+    return Result.of(r, prep.k, w)
+
+
+def fpcode_min_distance(p: int, n: int, k: int, G, stream=None) -> tuple[int, np.ndarray]:
+    """Certified minimum distance and a witness codeword of that weight."""
+    G = _matrix(G)
+    d = ctypes.c_int(0)
+    w = np.zeros(n, dtype=np.uint8)
+    _check(lib().fpcode_min_distance(p, n, k, G.ctypes.data_as(_U8P), _stream(stream), ctypes.byref(d),
+                                     w.ctypes.data_as(_U8P)), "fpcode_min_distance")
+    return d.value, w
+
+
+def fpcode_min_distance_batch(codes, stream=None, opts: fpcode_opts | None = None, budgets=None,
+                              want_witness: bool = True) -> list[Result]:
+    """codes: objects with p, n, k, G (e.g. inputs.Code)."""
+    num = len(codes)
+    mats = [_matrix(c.G) for c in codes]
+    descs = (fpcode_desc * max(num, 1))()
+    for i, (c, G) in enumerate(zip(codes, mats)):
+        descs[i].p, descs[i].n, descs[i].k = int(c.p), int(c.n), int(c.k)
+        descs[i].G = G.ctypes.data_as(_U8P)
+        descs[i].budget = int(budgets[i]) if budgets is not None else 0
+    res = (fpcode_result * max(num, 1))()
+    total_n = sum(int(c.n) for c in codes)
+    wit = np.zeros(max(total_n, 1), dtype=np.uint8)
+    _check(lib().fpcode_min_distance_batch(num, descs, _stream(stream), ctypes.byref(opts) if opts else None, res,
+                                           wit.ctypes.data_as(_U8P) if want_witness else None),
+           "fpcode_min_distance_batch")
+    out = []
+    off = 0
+    for i, c in enumerate(codes):
+        w = wit[off:off + int(c.n)].copy() if want_witness else None
+        off += int(c.n)
+        out.append(Result.of(res[i], int(c.k), w))
+    return out
+
+
+def fpcode_int_peaks(stream=None) -> dict:
+    r = (ctypes.c_double * 6)()
+    _check(lib().fpcode_int_peaks(_stream(stream), r), "fpcode_int_peaks")
+    return {"lop3_per_clk_sm": r[0], "popc_per_clk_sm": r[1], "iadd_per_clk_sm": r[2], "lop3_per_s": r[3],
+            "popc_per_s": r[4], "sm_mhz": r[5]}
+
+
+# ----------------------------------------------------------- test hooks ----
+
+def fpcode_test_bitslice_host(op: int, p: int, a, b) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.uint32)
+    b = np.ascontiguousarray(b, dtype=np.uint32)
+    out = np.zeros(max(len(a), 1), dtype=np.uint32)
+    _check(lib().fpcode_test_bitslice_host(op, p, a.ctypes.data_as(_U32P), b.ctypes.data_as(_U32P),
+                                           out.ctypes.data_as(_U32P)), "fpcode_test_bitslice_host")
+    return out
+
+
+def fpcode_test_bitslice_device(op: int, p: int, a: np.ndarray, b: np.ndarray, r: int) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.uint32).ravel()
+    b = np.ascontiguousarray(b, dtype=np.uint32).ravel()
+    count = len(a) // r
+    out = np.zeros(len(a), dtype=np.uint32)
+    _check(lib().fpcode_test_bitslice_device(op, p, count, a.ctypes.data_as(_U32P), b.ctypes.data_as(_U32P),
+                                             out.ctypes.data_as(_U32P)), "fpcode_test_bitslice_device")
+    return out if op not in (OP_NZ_SUB, OP_NZ_ADD) else out[:count]
+
+
+def fpcode_test_rd_unrank(rank: int, n: int, t: int) -> int:
+    return int(lib().fpcode_test_rd_unrank(rank, n, t))
+
+
+def fpcode_test_rd_rank(subset: int, n: int, t: int) -> int:
+    return int(lib().fpcode_test_rd_rank(subset, n, t))
+
+
+def fpcode_test_rd_next(subset: int, n: int, t: int) -> int | None:
+    nxt = ctypes.c_uint64(0)
+    ok = lib().fpcode_test_rd_next(subset, n, t, ctypes.byref(nxt))
+    return int(nxt.value) if ok else None
+
+
+def _prefix(fn, *args, g):
+    m = ctypes.c_int(0)
+    Q = ctypes.c_uint64(0)
+    coefs = (ctypes.c_int * max(g - 2, 1))()
+    _check(fn(*args, ctypes.byref(m), ctypes.byref(Q), coefs), fn.__name__)
+    return m.value, int(Q.value), [coefs[i] for i in range(g - 2)]
+
+
+def fpcode_test_prefix_unrank(I: int, k: int, g: int, p: int):
+    return _prefix(lib().fpcode_test_prefix_unrank, I, k, g, p, g=g)
+
+
+def fpcode_test_prefix_walk(I: int, steps: int, k: int, g: int, p: int):
+    return _prefix(lib().fpcode_test_prefix_walk, I, steps, k, g, p, g=g)
+
+
+def fpcode_prepared_shape(prep: Prepared):
+    m = ctypes.c_int(0)
+    kj = (ctypes.c_int * MAX_M)()
+    npasses = ctypes.c_int(0)
+    complete = ctypes.c_int(0)
+    _check(lib().fpcode_prepared_shape(prep.handle, ctypes.byref(m), kj, ctypes.byref(npasses),
+                                       ctypes.byref(complete)), "fpcode_prepared_shape")
+    return m.value, [kj[i] for i in range(m.value)], npasses.value, bool(complete.value)
+
+
+def fpcode_prepared_gamma(prep: Prepared, j: int):
+    gam = np.zeros((prep.k, prep.n), dtype=np.uint8)
+    piv = (ctypes.c_int * prep.k)()
+    _check(lib().fpcode_prepared_gamma(prep.handle, j, gam.ctypes.data_as(_U8P), piv), "fpcode_prepared_gamma")
+    return gam, [piv[i] for i in range(prep.k)]
+
+
+def fpcode_prepared_passes(prep: Prepared):
+    arr = (fpcode_pass_info * 256)()
+    n = lib().fpcode_prepared_passes(prep.handle, arr, 256)
+    return [(arr[i].g, arr[i].j, arr[i].L_before, arr[i].L_after, arr[i].round_end, int(arr[i].size),
+             int(arr[i].nprefix)) for i in range(n)]
+
+
+def fpcode_prepared_bytes(prep: Prepared) -> tuple[int, int]:
+    h2d = ctypes.c_uint64(0)
+    d2h = ctypes.c_uint64(0)
+    _check(lib().fpcode_prepared_bytes(prep.handle, ctypes.byref(h2d), ctypes.byref(d2h)), "fpcode_prepared_bytes")
+    return int(h2d.value), int(d2h.value)

@@ -1,0 +1,695 @@
+// fp_api.cu -- the C ABI of libfpcode on top of the persistent enumeration
+// kernel: device context, uploads, launches, read-back, batching, and the
+// device self-test and integer-rate microbenchmark entry points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/fpcode.h"
+#include "../../include/fpcode_testing.h"
+#include "fp_internal.h"
+#include "fp_kernel.cuh"
+#include "fp_kernels.h"
+
+using fpk::CtlDyn;
+using fpk::CtlStatic;
+using fpk::KParams;
+using fpk::PassDesc;
+using fpk::SlotDesc;
+using fpk::SlotState;
+
+namespace {
+
+#define FP_CUDA(call)                                                                           \
+  do {                                                                                           \
+    cudaError_t _e = (call);                                                                     \
+    if (_e != cudaSuccess) {                                                                     \
+      fph::set_error(std::string(#call) + ": " + cudaGetErrorString(_e));                        \
+      return FPCODE_ECUDA;                                                                       \
+    }                                                                                            \
+  } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// ---------------------------------------------------------------------------
+// Per-device context: SM count, the binomial table, the shared workspace.
+// ---------------------------------------------------------------------------
+struct DevCtx {
+  bool ready = false;
+  int sms = 0;
+  fpenum::Binom *binom = nullptr;  // device copy
+  std::mutex ws_mu;                // guards the workspace below
+  char *ws = nullptr;
+  size_t ws_bytes = 0;
+  char *ws_pinned = nullptr;
+  size_t ws_pinned_bytes = 0;
+};
+
+std::mutex g_ctx_mu;
+DevCtx g_ctx[64];
+
+int get_ctx(DevCtx **out) {
+  int dev = 0;
+  FP_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    fph::set_error("device index out of range");
+    return FPCODE_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(g_ctx_mu);
+  DevCtx &c = g_ctx[dev];
+  if (!c.ready) {
+    FP_CUDA(cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev));
+    FP_CUDA(cudaMalloc(&c.binom, sizeof(fpenum::Binom)));
+    FP_CUDA(cudaMemcpy(c.binom, &fph::binom(), sizeof(fpenum::Binom), cudaMemcpyHostToDevice));
+    c.ready = true;
+  }
+  *out = &c;
+  return FPCODE_OK;
+}
+
+// Grow-only device + pinned buffers (caller holds ws_mu).
+int ws_reserve(DevCtx &c, size_t dev_bytes, size_t pinned_bytes) {
+  if (dev_bytes > c.ws_bytes) {
+    if (c.ws) cudaFree(c.ws);
+    c.ws = nullptr;
+    c.ws_bytes = 0;
+    size_t want = std::max(dev_bytes, (size_t)1 << 20);
+    FP_CUDA(cudaMalloc(&c.ws, want));
+    c.ws_bytes = want;
+  }
+  if (pinned_bytes > c.ws_pinned_bytes) {
+    if (c.ws_pinned) cudaFreeHost(c.ws_pinned);
+    c.ws_pinned = nullptr;
+    c.ws_pinned_bytes = 0;
+    size_t want = std::max(pinned_bytes, (size_t)1 << 20);
+    FP_CUDA(cudaMallocHost(&c.ws_pinned, want));
+    c.ws_pinned_bytes = want;
+  }
+  return FPCODE_OK;
+}
+
+const void *kernel_for(int variant) {
+  const int cls = variant / 4, W = variant % 4 + 1;
+  switch (cls) {
+    case 0: return fpk::kernel_p3(W);
+    case 1: return fpk::kernel_p5(W);
+    case 2: return fpk::kernel_p7(W);
+    default: return fpk::kernel_generic(cls - 3 + 4, W);
+  }
+}
+
+// CTAs per SM for a kernel with `smem` bytes of dynamic shared memory.
+int occupancy(const void *fn, int smem, int override_per_sm, int *per_sm) {
+  if (smem > 48 * 1024) FP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  int n = 0;
+  FP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, fpk::kThreads, (size_t)smem));
+  if (n < 1) {
+    fph::set_error("kernel cannot be resident (shared memory or registers)");
+    return FPCODE_EINVAL;
+  }
+  *per_sm = override_per_sm > 0 ? std::min(override_per_sm, n) : n;
+  return FPCODE_OK;
+}
+
+KParams kparams(const fpcode_opts &o, int serve) {
+  KParams kp{};
+  const double wait = o.wait_limit_s > 0 ? o.wait_limit_s : 10.0;
+  kp.wait_limit_ns = (unsigned long long)(wait * 1e9);
+  kp.timeout_ns = o.timeout_s > 0 ? (unsigned long long)(o.timeout_s * 1e9) : 0ull;
+  kp.idle_limit_ns = serve ? 20000000ull : 0ull;
+  kp.mid_pass = o.mid_pass_exit ? 1 : 0;
+  return kp;
+}
+
+// ---------------------------------------------------------------------------
+// Layout of a launch over several codes:
+//   static  [CtlStatic][SlotDesc x ns][PassDesc ...][tables ...]
+//   dynamic [SlotState x ns][CtlDyn]
+// ---------------------------------------------------------------------------
+struct Layout {
+  size_t off_ctl = 0, off_slots = 0, off_passes = 0, off_tables = 0, static_bytes = 0;
+  size_t off_states = 0, dyn_bytes = 0, total = 0;
+  std::vector<size_t> pass_off, table_off;
+};
+
+Layout make_layout(const std::vector<const fph::Prepared *> &codes) {
+  Layout L;
+  const size_t ns = codes.size();
+  size_t o = 0;
+  L.off_ctl = o;
+  o = align256(o + sizeof(CtlStatic));
+  L.off_slots = o;
+  o = align256(o + ns * sizeof(SlotDesc));
+  L.off_passes = o;
+  for (auto *P : codes) {
+    L.pass_off.push_back(o);
+    o = align256(o + P->passes.size() * sizeof(PassDesc));
+  }
+  L.off_tables = o;
+  for (auto *P : codes) {
+    L.table_off.push_back(o);
+    o = align256(o + P->table.size() * sizeof(uint32_t));
+  }
+  L.static_bytes = o;
+  L.off_states = o;
+  L.dyn_bytes = align256(ns * sizeof(SlotState) + sizeof(CtlDyn));
+  L.total = o + L.dyn_bytes;
+  return L;
+}
+
+// Write the static part for `codes` into host staging `h` (device base `d`).
+void fill_static(const Layout &L, const std::vector<const fph::Prepared *> &codes, const DevCtx &c, char *h,
+                 char *d, int serve) {
+  CtlStatic cs{};
+  cs.binom = c.binom;
+  cs.nslots = (int)codes.size();
+  cs.serve = serve;
+  std::memcpy(h + L.off_ctl, &cs, sizeof(cs));
+  for (size_t i = 0; i < codes.size(); ++i) {
+    const fph::Prepared &P = *codes[i];
+    SlotDesc sd{};
+    sd.p = P.p;
+    sd.n = P.n;
+    sd.k = P.k;
+    sd.r = P.r;
+    sd.W = P.W;
+    sd.rwpad = P.rwpad;
+    sd.m = P.m;
+    sd.npasses = (int)P.passes.size();
+    sd.variant = P.variant;
+    sd.per_round_check = P.opts.per_round_check;
+    sd.mid_pass_exit = P.opts.mid_pass_exit;
+    sd.complete = P.complete;
+    sd.table = reinterpret_cast<const uint32_t *>(d + L.table_off[i]);
+    sd.passes = reinterpret_cast<const PassDesc *>(d + L.pass_off[i]);
+    std::memcpy(h + L.off_slots + i * sizeof(SlotDesc), &sd, sizeof(sd));
+    std::memcpy(h + L.pass_off[i], P.passes.data(), P.passes.size() * sizeof(PassDesc));
+    std::memcpy(h + L.table_off[i], P.table.data(), P.table.size() * sizeof(uint32_t));
+  }
+}
+
+fph::DeviceOutcome outcome_of(const SlotState &s, const CtlDyn &dyn) {
+  fph::DeviceOutcome o{};
+  o.best_key = ~(uint64_t)s.best_key;
+  o.enumerated = s.enumerated;
+  if (s.finished) {
+    o.status = s.status & 0xFF;
+    o.stop_pass = s.stop_pass;
+  } else {
+    o.status = -1;  // timed out or a wait gave up
+    o.stop_pass = (int)(s.word >> 40) - 1;
+  }
+  (void)dyn;
+  return o;
+}
+
+int launch(const void *fn, int ctas, int smem, cudaStream_t st, char *d, const Layout &L, const KParams &kp) {
+  const SlotDesc *slots = reinterpret_cast<const SlotDesc *>(d + L.off_slots);
+  SlotState *states = reinterpret_cast<SlotState *>(d + L.off_states);
+  const CtlStatic *ctl = reinterpret_cast<const CtlStatic *>(d + L.off_ctl);
+  CtlDyn *dyn = reinterpret_cast<CtlDyn *>(d + L.off_states + L.dyn_bytes - sizeof(CtlDyn));
+  KParams kpv = kp;
+  void *args[] = {(void *)&slots, (void *)&states, (void *)&ctl, (void *)&dyn, (void *)&kpv};
+  FP_CUDA(cudaLaunchKernel(fn, dim3(ctas), dim3(fpk::kThreads), args, (size_t)smem, st));
+  return FPCODE_OK;
+}
+
+int smem_for(const std::vector<const fph::Prepared *> &codes) {
+  size_t s = 16;
+  for (auto *P : codes) s = std::max(s, P->table_bytes_per_set());
+  return (int)((s + 15) & ~(size_t)15);
+}
+
+// Upload one prepared code into device buffer `d` (static_bytes) via pinned
+// staging `h`; plan its tasks for the kernel's grid.
+int upload_one(fpcode_prepared *prep, cudaStream_t st, DevCtx &c, char *d, char *h) {
+  fph::Prepared &P = prep->host;
+  const void *fn = kernel_for(P.variant);
+  if (!fn) {
+    fph::set_error("no kernel for this (p, n - k)");
+    return FPCODE_EINVAL;
+  }
+  prep->smem = smem_for({&P});
+  int per_sm = 0;
+  int s = occupancy(fn, prep->smem, P.opts.ctas_per_sm, &per_sm);
+  if (s) return s;
+  prep->ctas = c.sms * per_sm;
+  fph::plan_tasks(&P, prep->ctas, P.opts.prefixes_per_lane);
+  Layout L = make_layout({&P});
+  prep->off_ctl = L.off_ctl;
+  prep->off_slot = L.off_slots;
+  prep->off_pass = L.off_passes;
+  prep->off_table = L.off_tables;
+  prep->off_state = L.off_states;
+  prep->dyn_bytes = L.dyn_bytes;
+  prep->dev_bytes = L.total;
+  fill_static(L, {&P}, c, h, d, 0);
+  FP_CUDA(cudaMemcpyAsync(d, h, L.static_bytes, cudaMemcpyHostToDevice, st));
+  return FPCODE_OK;
+}
+
+int enqueue_one(fpcode_prepared *prep, cudaStream_t st, const fpcode_opts &o) {
+  fph::Prepared &P = prep->host;
+  Layout L = make_layout({&P});
+  FP_CUDA(cudaMemsetAsync(prep->dev + L.off_states, 0, L.dyn_bytes, st));
+  if (!P.passes.empty()) {
+    FP_CUDA(cudaEventRecord((cudaEvent_t)prep->ev0, st));
+    int s = launch(kernel_for(P.variant), prep->ctas, prep->smem, st, prep->dev, L, kparams(o, 0));
+    if (s) return s;
+    FP_CUDA(cudaEventRecord((cudaEvent_t)prep->ev1, st));
+  }
+  FP_CUDA(cudaMemcpyAsync(prep->pinned, prep->dev + L.off_states, L.dyn_bytes, cudaMemcpyDeviceToHost, st));
+  prep->run_opts = o;
+  return FPCODE_OK;
+}
+
+int finish_one(fpcode_prepared *prep, cudaStream_t st, fpcode_result *res, uint8_t *witness) {
+  FP_CUDA(cudaStreamSynchronize(st));
+  const fph::Prepared &P = prep->host;
+  if (P.passes.empty()) {  // budget below the first pass
+    fph::DeviceOutcome o{fpk::kNoKey, 0, FPCODE_EBUDGET, -1};
+    return fph::decode_result(P, o, res, witness);
+  }
+  SlotState s;
+  CtlDyn dyn;
+  std::memcpy(&s, prep->pinned, sizeof(s));
+  std::memcpy(&dyn, prep->pinned + prep->dyn_bytes - sizeof(CtlDyn), sizeof(dyn));
+  int rc = fph::decode_result(P, outcome_of(s, dyn), res, witness);
+  float ms = 0;
+  if (cudaEventElapsedTime(&ms, (cudaEvent_t)prep->ev0, (cudaEvent_t)prep->ev1) == cudaSuccess) res->t_kernel_ms = ms;
+  return rc;
+}
+
+int ensure_events(fpcode_prepared *prep) {
+  if (!prep->ev0) {
+    cudaEvent_t a, b;
+    FP_CUDA(cudaEventCreate(&a));
+    FP_CUDA(cudaEventCreate(&b));
+    prep->ev0 = a;
+    prep->ev1 = b;
+  }
+  return FPCODE_OK;
+}
+
+double ms_since(std::chrono::steady_clock::time_point t) {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t).count();
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void fpcode_opts_default(fpcode_opts *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->per_round_check = 0;
+  o->defer = 1;
+  o->mid_pass_exit = 1;
+  o->wait_limit_s = 10.0;
+}
+
+const char *fpcode_last_error(void) { return fph::last_error(); }
+
+int fpcode_prepare(int p, int n, int k, const uint8_t *G, const fpcode_opts *opts, fpcode_prepared **out) {
+  if (!out) return FPCODE_EINVAL;
+  *out = nullptr;
+  fpcode_opts o;
+  fpcode_opts_default(&o);
+  if (opts) o = *opts;
+  fpcode_prepared *prep = new (std::nothrow) fpcode_prepared();
+  if (!prep) return FPCODE_ENOMEM;
+  int s = fph::prepare(p, n, k, G, o, &prep->host);
+  if (s) {
+    delete prep;
+    return s;
+  }
+  *out = prep;
+  return FPCODE_OK;
+}
+
+void fpcode_prepared_free(fpcode_prepared *prep) {
+  if (!prep) return;
+  if (!prep->external) {
+    if (prep->dev) cudaFree(prep->dev);
+    if (prep->pinned) cudaFreeHost(prep->pinned);
+  }
+  if (prep->ev0) cudaEventDestroy((cudaEvent_t)prep->ev0);
+  if (prep->ev1) cudaEventDestroy((cudaEvent_t)prep->ev1);
+  delete prep;
+}
+
+int fpcode_prepared_upload(fpcode_prepared *prep, void *stream) {
+  if (!prep) return FPCODE_EINVAL;
+  if (prep->uploaded) return FPCODE_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  DevCtx *c;
+  int s = get_ctx(&c);
+  if (s) return s;
+  s = ensure_events(prep);
+  if (s) return s;
+  FP_CUDA(cudaGetDevice(&prep->device));
+  Layout L = make_layout({&prep->host});
+  FP_CUDA(cudaMalloc(&prep->dev, L.total));
+  FP_CUDA(cudaMallocHost(&prep->pinned, std::max(L.static_bytes, L.dyn_bytes)));
+  s = upload_one(prep, st, *c, prep->dev, prep->pinned);
+  if (s) return s;
+  FP_CUDA(cudaStreamSynchronize(st));
+  prep->uploaded = true;
+  return FPCODE_OK;
+}
+
+int fpcode_search_enqueue(fpcode_prepared *prep, void *stream, const fpcode_opts *opts) {
+  if (!prep || !prep->uploaded) {
+    fph::set_error("fpcode_search_enqueue: not uploaded");
+    return FPCODE_EINVAL;
+  }
+  return enqueue_one(prep, (cudaStream_t)stream, opts ? *opts : prep->host.opts);
+}
+
+int fpcode_search_finish(fpcode_prepared *prep, void *stream, fpcode_result *res, uint8_t *witness) {
+  if (!prep || !res) return FPCODE_EINVAL;
+  return finish_one(prep, (cudaStream_t)stream, res, witness);
+}
+
+int fpcode_min_distance_ex(fpcode_prepared *prep, void *stream, const fpcode_opts *opts, fpcode_result *res,
+                           uint8_t *witness) {
+  if (!prep || !res) return FPCODE_EINVAL;
+  auto t0 = std::chrono::steady_clock::now();
+  int s = fpcode_prepared_upload(prep, stream);
+  if (s) return s;
+  s = fpcode_search_enqueue(prep, stream, opts);
+  if (s) return s;
+  s = fpcode_search_finish(prep, stream, res, witness);
+  res->t_total_ms = ms_since(t0);
+  return s;
+}
+
+int fpcode_min_distance(int p, int n, int k, const uint8_t *G, void *stream, int *d, uint8_t *witness) {
+  if (!d) return FPCODE_EINVAL;
+  auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t st = (cudaStream_t)stream;
+  fpcode_opts o;
+  fpcode_opts_default(&o);
+  fpcode_prepared prep;
+  int s = fph::prepare(p, n, k, G, o, &prep.host);
+  if (s) return s;
+  DevCtx *c;
+  s = get_ctx(&c);
+  if (s) return s;
+  std::lock_guard<std::mutex> lk(c->ws_mu);
+  Layout L = make_layout({&prep.host});
+  s = ws_reserve(*c, L.total, std::max(L.static_bytes, L.dyn_bytes));
+  if (s) return s;
+  s = ensure_events(&prep);
+  if (s) return s;
+  prep.external = true;
+  prep.dev = c->ws;
+  prep.pinned = c->ws_pinned;
+  s = upload_one(&prep, st, *c, prep.dev, prep.pinned);
+  if (s) return s;
+  // the pinned staging buffer is reused for the read-back: wait for the upload copy
+  FP_CUDA(cudaStreamSynchronize(st));
+  prep.uploaded = true;
+  s = enqueue_one(&prep, st, o);
+  if (s) return s;
+  fpcode_result res;
+  s = finish_one(&prep, st, &res, witness);
+  if (prep.ev0) cudaEventDestroy((cudaEvent_t)prep.ev0);
+  if (prep.ev1) cudaEventDestroy((cudaEvent_t)prep.ev1);
+  prep.ev0 = prep.ev1 = nullptr;
+  (void)t0;
+  if (s) return s;
+  *d = res.d;
+  return FPCODE_OK;
+}
+
+int fpcode_min_distance_batch(int num, const fpcode_desc *codes, void *stream, const fpcode_opts *opts,
+                              fpcode_result *results, uint8_t *witnesses) {
+  if (num < 0 || (num > 0 && (!codes || !results))) return FPCODE_EINVAL;
+  auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t st = (cudaStream_t)stream;
+  fpcode_opts o;
+  fpcode_opts_default(&o);
+  if (opts) o = *opts;
+  std::vector<std::unique_ptr<fph::Prepared>> preps(num);
+  std::vector<int> status(num, FPCODE_OK);
+  for (int i = 0; i < num; ++i) {
+    preps[i].reset(new fph::Prepared());
+    fpcode_opts oi = o;
+    if (codes[i].budget) oi.budget = codes[i].budget;
+    status[i] = fph::prepare(codes[i].p, codes[i].n, codes[i].k, codes[i].G, oi, preps[i].get());
+  }
+  const double t_prep = ms_since(t0);
+  DevCtx *c;
+  int s = get_ctx(&c);
+  if (s) return s;
+  // groups: the batched kernel for p in {3,5,7}; one launch per other variant
+  std::vector<std::vector<int>> groups;
+  {
+    std::vector<int> multi;
+    std::vector<std::vector<int>> other(64);
+    for (int i = 0; i < num; ++i) {
+      if (status[i] != FPCODE_OK) continue;
+      if (preps[i]->variant < 12) multi.push_back(i);
+      else other[preps[i]->variant].push_back(i);
+    }
+    if (!multi.empty()) groups.push_back(multi);
+    for (auto &g : other)
+      if (!g.empty()) groups.push_back(g);
+  }
+  std::vector<size_t> woff(num + 1, 0);
+  for (int i = 0; i < num; ++i) woff[i + 1] = woff[i] + (size_t)codes[i].n;
+  std::lock_guard<std::mutex> lk(c->ws_mu);
+  cudaEvent_t e0, e1;
+  FP_CUDA(cudaEventCreate(&e0));
+  FP_CUDA(cudaEventCreate(&e1));
+  for (auto &grp : groups) {
+    std::vector<const fph::Prepared *> codesv;
+    std::vector<int> idx;
+    for (int i : grp)
+      if (!preps[i]->passes.empty()) {
+        codesv.push_back(preps[i].get());
+        idx.push_back(i);
+      }
+    if (codesv.empty()) continue;
+    const bool multi = codesv[0]->variant < 12;
+    const void *fn = multi ? fpk::kernel_multi357() : kernel_for(codesv[0]->variant);
+    const int smem = smem_for(codesv);
+    int per_sm = 0;
+    s = occupancy(fn, smem, o.ctas_per_sm, &per_sm);
+    if (s) break;
+    const int ctas = c->sms * per_sm;
+    for (int i : idx) fph::plan_tasks(preps[i].get(), ctas, o.prefixes_per_lane);
+    Layout L = make_layout(codesv);
+    s = ws_reserve(*c, L.total, std::max(L.static_bytes, L.dyn_bytes));
+    if (s) break;
+    fill_static(L, codesv, *c, c->ws_pinned, c->ws, 0);
+    FP_CUDA(cudaMemcpyAsync(c->ws, c->ws_pinned, L.static_bytes, cudaMemcpyHostToDevice, st));
+    FP_CUDA(cudaMemsetAsync(c->ws + L.off_states, 0, L.dyn_bytes, st));
+    FP_CUDA(cudaEventRecord(e0, st));
+    s = launch(fn, ctas, smem, st, c->ws, L, kparams(o, 0));
+    if (s) break;
+    FP_CUDA(cudaEventRecord(e1, st));
+    FP_CUDA(cudaStreamSynchronize(st));  // the staging buffer is reused for the read-back
+    FP_CUDA(cudaMemcpyAsync(c->ws_pinned, c->ws + L.off_states, L.dyn_bytes, cudaMemcpyDeviceToHost, st));
+    FP_CUDA(cudaStreamSynchronize(st));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const SlotState *states = reinterpret_cast<const SlotState *>(c->ws_pinned);
+    CtlDyn dyn;
+    std::memcpy(&dyn, c->ws_pinned + L.dyn_bytes - sizeof(CtlDyn), sizeof(dyn));
+    for (size_t q = 0; q < idx.size(); ++q) {
+      const int i = idx[q];
+      uint8_t *w = witnesses ? witnesses + woff[i] : nullptr;
+      fph::decode_result(*preps[i], outcome_of(states[q], dyn), &results[i], w);
+      results[i].t_kernel_ms = ms;
+      results[i].t_prepare_ms = t_prep;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s) return s;
+  for (int i = 0; i < num; ++i) {
+    if (status[i] != FPCODE_OK) {
+      std::memset(&results[i], 0, sizeof(results[i]));
+      results[i].status = status[i];
+      results[i].d = -1;
+    } else if (preps[i]->passes.empty()) {
+      fph::DeviceOutcome oc{fpk::kNoKey, 0, FPCODE_EBUDGET, -1};
+      fph::decode_result(*preps[i], oc, &results[i], nullptr);
+    }
+    results[i].t_total_ms = ms_since(t0);
+  }
+  return FPCODE_OK;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Device self-test of the bit-sliced operations and the integer-rate
+// microbenchmark.
+// ===========================================================================
+namespace {
+
+template <int R>
+__global__ void bitslice_kernel(int op, int p, int count, const uint32_t *a, const uint32_t *b, uint32_t *out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const uint32_t *x = a + (size_t)i * R;
+  const uint32_t *y = b + (size_t)i * R;
+  uint32_t *z = out + (size_t)i * R;
+  uint32_t xa[R], ya[R], za[R];
+  for (int q = 0; q < R; ++q) {
+    xa[q] = x[q];
+    ya[q] = y[q];
+    za[q] = 0;
+  }
+  switch (op) {
+    case FPCODE_OP_ADD:
+      if (p == 3) fpbs::add_exact<3, R>(xa, ya, za, p);
+      else if (p == 7) fpbs::add_exact<7, R>(xa, ya, za, p);
+      else fpbs::add_generic<R>(xa, ya, za, p);
+      for (int q = 0; q < R; ++q) z[q] = za[q];
+      break;
+    case FPCODE_OP_NZ_SUB: out[i] = fpbs::nz_sub<R>(xa, ya); break;
+    case FPCODE_OP_NZ_ADD:
+      out[i] = (p == 3) ? fpbs::nz_add_p3(xa[0], xa[1], ya[0], ya[1]) : fpbs::nz_add_mersenne<R>(xa, ya);
+      break;
+    case FPCODE_OP_NEG:
+      fpbs::neg_mersenne<R>(xa, za);
+      for (int q = 0; q < R; ++q) z[q] = za[q];
+      break;
+    case FPCODE_OP_MUL2:
+      fpbs::mul_pow2_mersenne<R>(xa, za, 1);
+      for (int q = 0; q < R; ++q) z[q] = za[q];
+      break;
+  }
+}
+
+// Independent chains of one instruction kind: op 0 LOP3, 1 POPC, 2 IADD.
+template <int OP>
+__global__ void intpeak_kernel(uint32_t *sink, long long *cycles, int iters, uint32_t seed) {
+  uint32_t v[8];
+  for (int q = 0; q < 8; ++q) v[q] = (threadIdx.x + 1u) * (2u * q + 3u) ^ seed;
+  const uint32_t k1 = seed * 0x9E3779B9u, k2 = seed ^ 0x5bd1e995u;
+  long long t0 = clock64();
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (OP == 0) asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(v[q]) : "r"(k1), "r"(k2));
+      if (OP == 1) asm volatile("popc.b32 %0, %0;" : "+r"(v[q]));
+      if (OP == 2) asm volatile("add.u32 %0, %0, %1;" : "+r"(v[q]) : "r"(k1));
+    }
+  }
+  long long t1 = clock64();
+  uint32_t acc = 0;
+  for (int q = 0; q < 8; ++q) acc ^= v[q];
+  sink[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+  if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fpcode_prepared_bytes(const fpcode_prepared *prep, uint64_t *h2d, uint64_t *d2h) {
+  if (!prep) return FPCODE_EINVAL;
+  Layout L = make_layout({&prep->host});
+  if (h2d) *h2d = L.static_bytes;
+  if (d2h) *d2h = L.dyn_bytes;
+  return FPCODE_OK;
+}
+
+int fpcode_test_bitslice_device(int op, int p, int count, const uint32_t *a, const uint32_t *b, uint32_t *out) {
+  if (!fph::is_odd_prime(p) || count < 0 || !a || !b || !out) return FPCODE_EINVAL;
+  const bool mersenne = ((p + 1) & p) == 0;
+  if ((op == FPCODE_OP_NEG || op == FPCODE_OP_MUL2 || op == FPCODE_OP_NZ_ADD) && !mersenne) return FPCODE_EINVAL;
+  if (op < FPCODE_OP_ADD || op > FPCODE_OP_MUL2) return FPCODE_EINVAL;
+  if (count == 0) return FPCODE_OK;
+  const int r = fpbs::bits_for(p);
+  const size_t in_words = (size_t)count * r;
+  const size_t out_words = (op == FPCODE_OP_NZ_SUB || op == FPCODE_OP_NZ_ADD) ? (size_t)count : in_words;
+  uint32_t *da = nullptr, *db = nullptr, *dout = nullptr;
+  FP_CUDA(cudaMalloc(&da, in_words * 4));
+  FP_CUDA(cudaMalloc(&db, in_words * 4));
+  FP_CUDA(cudaMalloc(&dout, in_words * 4));
+  FP_CUDA(cudaMemcpy(da, a, in_words * 4, cudaMemcpyHostToDevice));
+  FP_CUDA(cudaMemcpy(db, b, in_words * 4, cudaMemcpyHostToDevice));
+  const int threads = 128, blocks = (count + threads - 1) / threads;
+  switch (r) {
+    case 2: bitslice_kernel<2><<<blocks, threads>>>(op, p, count, da, db, dout); break;
+    case 3: bitslice_kernel<3><<<blocks, threads>>>(op, p, count, da, db, dout); break;
+    case 4: bitslice_kernel<4><<<blocks, threads>>>(op, p, count, da, db, dout); break;
+    case 5: bitslice_kernel<5><<<blocks, threads>>>(op, p, count, da, db, dout); break;
+    case 6: bitslice_kernel<6><<<blocks, threads>>>(op, p, count, da, db, dout); break;
+    case 7: bitslice_kernel<7><<<blocks, threads>>>(op, p, count, da, db, dout); break;
+    default: bitslice_kernel<8><<<blocks, threads>>>(op, p, count, da, db, dout); break;
+  }
+  FP_CUDA(cudaGetLastError());
+  FP_CUDA(cudaMemcpy(out, dout, out_words * 4, cudaMemcpyDeviceToHost));
+  cudaFree(da);
+  cudaFree(db);
+  cudaFree(dout);
+  return FPCODE_OK;
+}
+
+int fpcode_int_peaks(void *stream, double *rates) {
+  if (!rates) return FPCODE_EINVAL;
+  DevCtx *c;
+  int s = get_ctx(&c);
+  if (s) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int blocks = c->sms * 8, threads = 256, iters = 4096;
+  uint32_t *sink = nullptr;
+  long long *cyc = nullptr;
+  FP_CUDA(cudaMalloc(&sink, sizeof(uint32_t) * blocks * threads));
+  FP_CUDA(cudaMalloc(&cyc, sizeof(long long) * blocks));
+  std::vector<long long> h(blocks);
+  cudaEvent_t e0, e1;
+  FP_CUDA(cudaEventCreate(&e0));
+  FP_CUDA(cudaEventCreate(&e1));
+  double per_clk[3] = {0, 0, 0}, per_s[3] = {0, 0, 0}, mhz = 0;
+  for (int op = 0; op < 3; ++op) {
+    for (int rep = 0; rep < 2; ++rep) {  // first run warms up
+      cudaEventRecord(e0, st);
+      if (op == 0) intpeak_kernel<0><<<blocks, threads, 0, st>>>(sink, cyc, iters, 7u);
+      if (op == 1) intpeak_kernel<1><<<blocks, threads, 0, st>>>(sink, cyc, iters, 7u);
+      if (op == 2) intpeak_kernel<2><<<blocks, threads, 0, st>>>(sink, cyc, iters, 7u);
+      cudaEventRecord(e1, st);
+    }
+    FP_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    FP_CUDA(cudaMemcpy(h.data(), cyc, sizeof(long long) * blocks, cudaMemcpyDeviceToHost));
+    long long mx = 1;
+    for (long long x : h) mx = std::max(mx, x);
+    const double ops = (double)blocks * threads * iters * 8.0;
+    per_clk[op] = ops / c->sms / (double)mx;
+    per_s[op] = ops / (ms * 1e-3);
+    if (op == 0) mhz = (double)mx / (ms * 1e3);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  cudaFree(cyc);
+  rates[0] = per_clk[0];
+  rates[1] = per_clk[1];
+  rates[2] = per_clk[2];
+  rates[3] = per_s[0];
+  rates[4] = per_s[1];
+  rates[5] = mhz;
+  return FPCODE_OK;
+}
+
+}  // extern "C"

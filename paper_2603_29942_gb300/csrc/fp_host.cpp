@@ -1,0 +1,504 @@
+// fp_host.cpp -- host side of libfpcode (not on the hot path): Gaussian
+// elimination mod p into systematic generator matrices on disjoint
+// information sets, bit-sliced row multiples, the pass schedule of the
+// Brouwer-Zimmermann search (Sec. 3.1, Alg. 6) and the exact rebuild of a
+// witness codeword from its packed key.  Plain C++17, no CUDA.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/fpcode_testing.h"
+#include "fp_bitslice.cuh"
+#include "fp_internal.h"
+
+namespace fph {
+
+static thread_local std::string g_err;
+void set_error(const std::string &msg) { g_err = msg; }
+const char *last_error() { return g_err.c_str(); }
+
+const fpenum::Binom &binom() {
+  static const fpenum::Binom b = [] {
+    fpenum::Binom x;
+    fpenum::fill_binom(&x);
+    return x;
+  }();
+  return b;
+}
+
+bool is_odd_prime(int p) {
+  if (p < 3 || p > 255 || p % 2 == 0) return false;
+  for (int q = 3; q * q <= p; q += 2)
+    if (p % q == 0) return false;
+  return true;
+}
+
+namespace {
+
+// Multiplicative inverses of F_p by exponentiation a^(p-2).
+std::vector<int> inverses(int p) {
+  std::vector<int> inv(p, 0);
+  for (int a = 1; a < p; ++a) {
+    int r = 1, base = a, e = p - 2;
+    while (e) {
+      if (e & 1) r = r * base % p;
+      base = base * base % p;
+      e >>= 1;
+    }
+    inv[a] = r;
+  }
+  return inv;
+}
+
+// Column-selection elimination on a k x n working matrix.  `owner[r]` is
+// the pivot column of row r in the current round (-1: free).
+struct Eliminator {
+  int p, n, k;
+  std::vector<int> M;  // row-major, values in [0, p)
+  std::vector<int> inv;
+  std::vector<int> owner;
+
+  Eliminator(int p_, int n_, int k_, const uint8_t *G) : p(p_), n(n_), k(k_), M(G, G + (size_t)k_ * n_) {
+    inv = inverses(p);
+  }
+  void new_round() { owner.assign(k, -1); }
+  // Take column c as a pivot if a free row has a nonzero entry there.
+  bool take(int c) {
+    int r = -1;
+    for (int q = 0; q < k; ++q)
+      if (owner[q] < 0 && M[(size_t)q * n + c] != 0) {
+        r = q;
+        break;
+      }
+    if (r < 0) return false;
+    int *row = &M[(size_t)r * n];
+    const int s = inv[row[c]];
+    for (int i = 0; i < n; ++i) row[i] = row[i] * s % p;
+    for (int q = 0; q < k; ++q) {
+      if (q == r) continue;
+      int *o = &M[(size_t)q * n];
+      const int f = o[c];
+      if (!f) continue;
+      for (int i = 0; i < n; ++i) o[i] = (o[i] + (p - f) * row[i]) % p;
+    }
+    owner[r] = c;
+    return true;
+  }
+};
+
+int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+uint64_t sat_mul(uint64_t a, uint64_t b) {
+  if (a == 0 || b == 0) return 0;
+  if (a > ~0ull / b) return ~0ull;
+  return a * b;
+}
+
+// C(k, g) (p-1)^(g-1), saturating.
+uint64_t pass_size(int p, int k, int g) {
+  uint64_t c = binom().c[k][g];
+  for (int i = 1; i < g; ++i) c = sat_mul(c, (uint64_t)(p - 1));
+  return c;
+}
+
+int lower_bound(const std::vector<int> &e, const std::vector<int> &kj, int k) {
+  int L = 0;
+  for (size_t i = 0; i < e.size(); ++i) L += std::max(0, e[i] + 1 - (k - kj[i]));
+  return L;
+}
+
+// Digit width of the coefficient counters the kernel uses for this prime.
+int digit_bits(int p) { return (p == 3 || p == 5 || p == 7) ? 4 : 8; }
+
+}  // namespace
+
+int prepare(int p, int n, int k, const uint8_t *G, const fpcode_opts &opts, Prepared *P) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (!is_odd_prime(p)) {
+    set_error("p must be an odd prime below 256");
+    return FPCODE_EINVAL;
+  }
+  if (k < 1 || k > FPCODE_MAX_K || n < k || n > FPCODE_MAX_N || n - k > 128 || !G) {
+    set_error("need 1 <= k <= 64, k <= n <= 255, n - k <= 128 and a matrix");
+    return FPCODE_EINVAL;
+  }
+  for (size_t i = 0; i < (size_t)k * n; ++i)
+    if (G[i] >= p) {
+      set_error("matrix entry >= p");
+      return FPCODE_EINVAL;
+    }
+  P->p = p;
+  P->n = n;
+  P->k = k;
+  P->opts = opts;
+  P->r = fpbs::bits_for(p);
+  P->W = std::max(1, ceil_div(n - k, 32));
+  P->rwpad = (P->r * P->W + 3) & ~3;
+  P->variant = (p == 3 ? 0 : p == 5 ? 1 : p == 7 ? 2 : 3 + (P->r - 4)) * 4 + (P->W - 1);
+  if (P->table_bytes_per_set() > 96 * 1024) {
+    set_error("bit-sliced multiples of one information set exceed 96 KiB (k (p-1) r W too large)");
+    return FPCODE_EINVAL;
+  }
+
+  // --- information sets: greedy leftmost columns, disjoint fresh pivots ---
+  Eliminator E(p, n, k, G);
+  std::vector<char> used(n, 0);
+  P->kj.clear();
+  P->gam.clear();
+  P->piv.clear();
+  P->red.clear();
+  for (;;) {
+    E.new_round();
+    std::vector<int> fresh;
+    for (int c = 0; c < n && (int)fresh.size() < k; ++c)
+      if (!used[c] && E.take(c)) fresh.push_back(c);
+    if (P->kj.empty() && (int)fresh.size() < k) {
+      set_error("rank(G) < k");
+      return FPCODE_EINVAL;
+    }
+    if (fresh.empty()) break;
+    int have = (int)fresh.size();
+    for (int c = 0; c < n && have < k; ++c)
+      if (used[c] && E.take(c)) ++have;
+    if (have < k) {
+      set_error("internal: information set could not be completed");
+      return FPCODE_EINVAL;
+    }
+    if ((int)P->kj.size() >= FPCODE_MAX_M) break;
+    std::vector<int> rows(k);
+    for (int r = 0; r < k; ++r) rows[r] = r;
+    std::sort(rows.begin(), rows.end(), [&](int a, int b) { return E.owner[a] < E.owner[b]; });
+    std::vector<char> is_piv(n, 0);
+    for (int r : rows) {
+      for (int c = 0; c < n; ++c) P->gam.push_back((uint8_t)E.M[(size_t)r * n + c]);
+      P->piv.push_back(E.owner[r]);
+      is_piv[E.owner[r]] = 1;
+    }
+    for (int c = 0; c < n; ++c)
+      if (!is_piv[c]) P->red.push_back(c);
+    P->kj.push_back((int)fresh.size());
+    for (int c : fresh) used[c] = 1;
+    if (std::find(used.begin(), used.end(), 0) == used.end()) break;
+  }
+  P->m = (int)P->kj.size();
+
+  // --- bit-sliced multiples v * A_j[t] of the non-pivot part ---
+  const int m = P->m, nk = n - k, R = P->r, RWP = P->rwpad;
+  P->table.assign((size_t)m * k * (p - 1) * RWP, 0u);
+  for (int j = 0; j < m; ++j)
+    for (int t = 0; t < k; ++t) {
+      const uint8_t *row = &P->gam[((size_t)j * k + t) * n];
+      const int *red = &P->red[(size_t)j * nk];
+      for (int v = 1; v < p; ++v) {
+        uint32_t *e = &P->table[(((size_t)j * k + t) * (p - 1) + (v - 1)) * RWP];
+        for (int q = 0; q < nk; ++q) {
+          const int y = (v * row[red[q]]) % p;
+          const int w = q >> 5, bit = q & 31;
+          for (int i = 0; i < R; ++i)
+            if ((y >> i) & 1) e[w * R + i] |= 1u << bit;
+        }
+      }
+    }
+
+  // --- pass schedule ---
+  P->passes.clear();
+  std::vector<int> e(m, 0);
+  P->L0 = lower_bound(e, P->kj, k);
+  const int DB = digit_bits(p);
+  const int gmax_digits = 2 + 64 / DB;
+  uint64_t total = 0;
+  bool truncated = false;
+  for (int g = 1; g <= k && !truncated; ++g) {
+    const size_t round_start = P->passes.size();
+    for (int j = 0; j < m && !truncated; ++j) {
+      if (opts.defer && P->kj[j] < k && g < k - P->kj[j]) continue;
+      for (int h = e[j] + 1; h <= g; ++h) {
+        const uint64_t size = pass_size(p, k, h);
+        uint64_t nprefix = (uint64_t)k;
+        uint64_t NC = 1;
+        if (h >= 2) {
+          for (int i = 0; i < h - 2; ++i) NC = sat_mul(NC, (uint64_t)(p - 1));
+          nprefix = sat_mul(binom().c[k - 1][h - 1], NC);
+        }
+        const bool over_budget = opts.budget && (size > opts.budget || total > opts.budget - size);
+        if (over_budget || size == ~0ull || nprefix >= fpk::kMaxPrefix || h > gmax_digits ||
+            (int)P->passes.size() >= fpk::kMaxPasses) {
+          truncated = true;
+          break;
+        }
+        fpk::PassDesc d{};
+        d.g = h;
+        d.j = j;
+        d.L_before = lower_bound(e, P->kj, k);
+        e[j] = h;
+        d.L_after = lower_bound(e, P->kj, k);
+        d.size = size;
+        d.nprefix = nprefix;
+        d.NC = NC;
+        d.pl = 1;
+        d.ntasks = 1;
+        P->passes.push_back(d);
+        total += size;
+      }
+    }
+    if (P->passes.size() > round_start && !truncated) P->passes.back().round_end = 1;
+  }
+  P->complete = truncated ? 0 : 1;
+  P->t_prepare_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return FPCODE_OK;
+}
+
+void plan_tasks(Prepared *P, int ctas, int fixed_pl) {
+  const uint64_t per_task_lanes = (uint64_t)fpk::kThreads;
+  for (auto &d : P->passes) {
+    if (d.g == 1) {
+      d.pl = 1;
+      d.ntasks = 1;
+      continue;
+    }
+    int pl;
+    if (fixed_pl > 0) {
+      pl = std::min(fixed_pl, 64);
+    } else {
+      // about four tasks per CTA, at most 64 prefixes per lane
+      const uint64_t want = (uint64_t)std::max(1, ctas) * 4ull * per_task_lanes;
+      uint64_t q = (d.nprefix + want - 1) / want;
+      pl = (int)std::min<uint64_t>(std::max<uint64_t>(q, 1), 64);
+    }
+    d.pl = pl;
+    const uint64_t per_task = per_task_lanes * (uint64_t)pl;
+    d.ntasks = (uint32_t)((d.nprefix + per_task - 1) / per_task);
+  }
+}
+
+namespace {
+
+// Coefficients (length k) of the codeword a key stands for.
+bool key_coefficients(const Prepared &P, uint64_t key, int *g_out, int *j_out, std::vector<int> &coef) {
+  const int pass = (int)fpk::key_pass(key);
+  if (pass >= (int)P.passes.size()) return false;
+  const fpk::PassDesc &d = P.passes[pass];
+  coef.assign(P.k, 0);
+  const int x = (int)fpk::key_leaf(key);
+  const int c = (int)fpk::key_coef(key);
+  if (x >= P.k || c < 1 || c >= P.p) return false;
+  if (d.g == 1) {
+    coef[x] = 1;
+  } else {
+    const uint64_t I = fpk::key_prefix(key);
+    if (I >= d.nprefix) return false;
+    const int L = d.g - 2, b = P.p - 1;
+    fpenum::Prefix pf = digit_bits(P.p) == 4 ? fpenum::prefix_unrank<4>(binom(), I, P.k, d.g, b)
+                                               : fpenum::prefix_unrank<8>(binom(), I, P.k, d.g, b);
+    if (pf.m >= x) return false;
+    coef[pf.m] = 1;
+    uint64_t Q = pf.Q;
+    for (int s = 0; s < L; ++s) {
+      const int q = fpenum::ctz64(Q);
+      Q &= Q - 1;
+      coef[q] = (digit_bits(P.p) == 4 ? fpenum::gray_digit<4>(pf.d, s, b, L) : fpenum::gray_digit<8>(pf.d, s, b, L)) + 1;
+    }
+    coef[x] = c;
+  }
+  *g_out = d.g;
+  *j_out = d.j;
+  return true;
+}
+
+}  // namespace
+
+int decode_result(const Prepared &P, const DeviceOutcome &o, fpcode_result *res, uint8_t *witness) {
+  std::memset(res, 0, sizeof(*res));
+  res->m = P.m;
+  for (int j = 0; j < P.m && j < FPCODE_MAX_M; ++j) res->kj[j] = P.kj[j];
+  res->enumerated = o.enumerated;
+  res->t_prepare_ms = P.t_prepare_ms;
+  const int singleton = P.n - P.k + 1;
+  res->npasses = o.stop_pass + 1;
+  for (int i = 0; i <= o.stop_pass && i < (int)P.passes.size(); ++i) res->counts[P.passes[i].g] += P.passes[i].size;
+  res->L = o.stop_pass >= 0 ? P.passes[o.stop_pass].L_after : P.L0;
+  const bool have = o.best_key != fpk::kNoKey;
+  res->U = have ? std::min<int>((int)fpk::key_weight(o.best_key), singleton) : singleton;
+  res->status = o.status < 0 ? FPCODE_ETIMEOUT : o.status;
+  res->d = -1;
+  if (res->status == FPCODE_OK) {
+    if (!have) {
+      set_error("internal: certified without a witness");
+      res->status = FPCODE_ECUDA;
+      return res->status;
+    }
+    res->d = (int)fpk::key_weight(o.best_key);
+  }
+  if (have && (witness || res->status == FPCODE_OK)) {
+    int g, j;
+    std::vector<int> coef;
+    if (!key_coefficients(P, o.best_key, &g, &j, coef)) {
+      set_error("internal: witness key does not decode");
+      res->status = FPCODE_ECUDA;
+      return res->status;
+    }
+    std::vector<uint8_t> cw(P.n, 0);
+    int nnz = 0;
+    for (int t = 0; t < P.k; ++t)
+      if (coef[t]) {
+        ++nnz;
+        const uint8_t *row = &P.gam[((size_t)j * P.k + t) * P.n];
+        for (int c = 0; c < P.n; ++c) cw[c] = (uint8_t)((cw[c] + coef[t] * row[c]) % P.p);
+      }
+    int wt = 0;
+    for (int c = 0; c < P.n; ++c) wt += cw[c] != 0;
+    if (nnz != g || wt != (int)fpk::key_weight(o.best_key)) {
+      set_error("internal: rebuilt witness has the wrong weight");
+      res->status = FPCODE_ECUDA;
+      return res->status;
+    }
+    if (witness) std::memcpy(witness, cw.data(), (size_t)P.n);
+  }
+  return res->status;
+}
+
+}  // namespace fph
+
+// ---------------------------------------------------------------------------
+// Host-side hooks declared in fpcode_testing.h.
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int fpcode_test_bitslice_host(int op, int p, const uint32_t *a, const uint32_t *b, uint32_t *out) {
+  if (!fph::is_odd_prime(p) || !a || !out) return FPCODE_EINVAL;
+  const int r = fpbs::bits_for(p);
+  const bool mersenne = ((p + 1) & p) == 0;
+  switch (op) {
+    case FPCODE_OP_ADD:
+      if (!b) return FPCODE_EINVAL;
+      if (p == 3) fpbs::add_exact<3, 2>(a, b, out, p);
+      else if (p == 7) fpbs::add_exact<7, 3>(a, b, out, p);
+      else {
+        switch (r) {
+          case 3: fpbs::add_generic<3>(a, b, out, p); break;
+          case 4: fpbs::add_generic<4>(a, b, out, p); break;
+          case 5: fpbs::add_generic<5>(a, b, out, p); break;
+          case 6: fpbs::add_generic<6>(a, b, out, p); break;
+          case 7: fpbs::add_generic<7>(a, b, out, p); break;
+          case 8: fpbs::add_generic<8>(a, b, out, p); break;
+          default: return FPCODE_EINVAL;
+        }
+      }
+      return FPCODE_OK;
+    case FPCODE_OP_NZ_SUB: {
+      if (!b) return FPCODE_EINVAL;
+      uint32_t mask = 0;
+      for (int i = 0; i < r; ++i) mask |= a[i] ^ b[i];
+      out[0] = mask;
+      return FPCODE_OK;
+    }
+    case FPCODE_OP_NZ_ADD:
+      if (!b) return FPCODE_EINVAL;
+      if (p == 3) out[0] = fpbs::nz_add_p3(a[0], a[1], b[0], b[1]);
+      else if (p == 7) out[0] = fpbs::nz_add_mersenne<3>(a, b);
+      else if (p == 31) out[0] = fpbs::nz_add_mersenne<5>(a, b);
+      else if (p == 127) out[0] = fpbs::nz_add_mersenne<7>(a, b);
+      else return FPCODE_EINVAL;
+      return FPCODE_OK;
+    case FPCODE_OP_NEG:
+      if (!mersenne) return FPCODE_EINVAL;
+      if (p == 3) fpbs::neg_mersenne<2>(a, out);
+      else if (p == 7) fpbs::neg_mersenne<3>(a, out);
+      else if (p == 31) fpbs::neg_mersenne<5>(a, out);
+      else fpbs::neg_mersenne<7>(a, out);
+      return FPCODE_OK;
+    case FPCODE_OP_MUL2:
+      if (!mersenne) return FPCODE_EINVAL;
+      if (p == 3) fpbs::mul_pow2_mersenne<2>(a, out, 1);
+      else if (p == 7) fpbs::mul_pow2_mersenne<3>(a, out, 1);
+      else if (p == 31) fpbs::mul_pow2_mersenne<5>(a, out, 1);
+      else fpbs::mul_pow2_mersenne<7>(a, out, 1);
+      return FPCODE_OK;
+    default:
+      return FPCODE_EINVAL;
+  }
+}
+
+uint64_t fpcode_test_rd_unrank(uint64_t rank, int n, int t) { return fpenum::rd_unrank(fph::binom(), rank, n, t); }
+uint64_t fpcode_test_rd_rank(uint64_t subset, int n, int t) { return fpenum::rd_rank(fph::binom(), subset, n, t); }
+int fpcode_test_rd_next(uint64_t subset, int n, int t, uint64_t *next) {
+  int rm, ad;
+  return fpenum::rd_next(subset, n, t, next, &rm, &ad) ? 1 : 0;
+}
+
+static int prefix_out(const fpenum::Prefix &pf, int g, int p, int *m, uint64_t *Q, int *coefs) {
+  *m = pf.m;
+  *Q = pf.Q;
+  const int L = g - 2, b = p - 1;
+  for (int s = 0; s < L; ++s)
+    coefs[s] = ((p == 3 || p == 5 || p == 7) ? fpenum::gray_digit<4>(pf.d, s, b, L)
+                                              : fpenum::gray_digit<8>(pf.d, s, b, L)) + 1;
+  return FPCODE_OK;
+}
+
+int fpcode_test_prefix_unrank(uint64_t I, int k, int g, int p, int *m, uint64_t *Q, int *coefs) {
+  if (g < 2 || g > k || k > 64 || !fph::is_odd_prime(p)) return FPCODE_EINVAL;
+  const bool small = p == 3 || p == 5 || p == 7;
+  fpenum::Prefix pf = small ? fpenum::prefix_unrank<4>(fph::binom(), I, k, g, p - 1)
+                            : fpenum::prefix_unrank<8>(fph::binom(), I, k, g, p - 1);
+  return prefix_out(pf, g, p, m, Q, coefs);
+}
+
+int fpcode_test_prefix_walk(uint64_t I, uint64_t steps, int k, int g, int p, int *m, uint64_t *Q, int *coefs) {
+  if (g < 2 || g > k || k > 64 || !fph::is_odd_prime(p)) return FPCODE_EINVAL;
+  const fpenum::Binom &B = fph::binom();
+  const int L = g - 2, b = p - 1;
+  const uint64_t NC = fpenum::ipow((uint64_t)b, L);
+  const bool small = p == 3 || p == 5 || p == 7;
+  fpenum::Prefix pf = small ? fpenum::prefix_unrank<4>(B, I, k, g, b) : fpenum::prefix_unrank<8>(B, I, k, g, b);
+  uint64_t ci = (I - fpenum::prefixes_below(B, pf.m, g, NC)) - pf.qi * NC;
+  uint64_t nq = B.c[pf.m][L];
+  for (uint64_t s = 0; s < steps; ++s) {
+    int dir;
+    if (small) fpenum::prefix_advance<4>(B, pf, ci, nq, NC, b, L, &dir);
+    else fpenum::prefix_advance<8>(B, pf, ci, nq, NC, b, L, &dir);
+  }
+  return prefix_out(pf, g, p, m, Q, coefs);
+}
+
+int fpcode_prepared_shape(const fpcode_prepared *prep, int *m, int *kj, int *npasses, int *complete) {
+  const fph::Prepared *P = prep ? &prep->host : nullptr;
+  if (!P) return FPCODE_EINVAL;
+  if (m) *m = P->m;
+  if (kj)
+    for (int j = 0; j < P->m; ++j) kj[j] = P->kj[j];
+  if (npasses) *npasses = (int)P->passes.size();
+  if (complete) *complete = P->complete;
+  return FPCODE_OK;
+}
+
+int fpcode_prepared_gamma(const fpcode_prepared *prep, int j, uint8_t *gamma, int *pivots) {
+  const fph::Prepared *P = prep ? &prep->host : nullptr;
+  if (!P || j < 0 || j >= P->m) return FPCODE_EINVAL;
+  if (gamma) std::memcpy(gamma, &P->gam[(size_t)j * P->k * P->n], (size_t)P->k * P->n);
+  if (pivots)
+    for (int r = 0; r < P->k; ++r) pivots[r] = P->piv[(size_t)j * P->k + r];
+  return FPCODE_OK;
+}
+
+int fpcode_prepared_passes(const fpcode_prepared *prep, fpcode_pass_info *passes, int max) {
+  const fph::Prepared *P = prep ? &prep->host : nullptr;
+  if (!P || !passes) return FPCODE_EINVAL;
+  int n = std::min<int>(max, (int)P->passes.size());
+  for (int i = 0; i < n; ++i) {
+    const fpk::PassDesc &d = P->passes[i];
+    passes[i].g = d.g;
+    passes[i].j = d.j;
+    passes[i].L_before = d.L_before;
+    passes[i].L_after = d.L_after;
+    passes[i].round_end = d.round_end;
+    passes[i].reserved = 0;
+    passes[i].size = d.size;
+    passes[i].nprefix = d.nprefix;
+  }
+  return n;
+}
+
+}  // extern "C"

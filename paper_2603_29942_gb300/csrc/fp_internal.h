@@ -1,0 +1,70 @@
+// fp_internal.h -- host-side structures of libfpcode shared by the
+// preparation code (fp_host.cpp) and the CUDA driver (fp_api.cu).
+#pragma once
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fpcode.h"
+#include "fp_enum.cuh"
+#include "fp_types.h"
+
+namespace fph {
+
+// Thread-local error text behind fpcode_last_error().
+void set_error(const std::string &msg);
+const char *last_error();
+
+const fpenum::Binom &binom();  // host binomial table
+
+bool is_odd_prime(int p);
+
+struct Prepared {
+  int p = 0, n = 0, k = 0, r = 0, W = 0, rwpad = 0, m = 0, variant = 0;
+  fpcode_opts opts{};
+  std::vector<int> kj;           // fresh pivots of each Gamma_j
+  std::vector<uint8_t> gam;      // m * k * n: Gamma_j, rows in pivot order
+  std::vector<int> piv;          // m * k pivot columns (increasing)
+  std::vector<int> red;          // m * (n - k) non-pivot columns (increasing)
+  std::vector<uint32_t> table;   // m * k * (p-1) * rwpad bit-sliced multiples
+  std::vector<fpk::PassDesc> passes;
+  int complete = 0;              // schedule reaches the last level
+  int L0 = 0;                    // lower bound before any pass
+  double t_prepare_ms = 0;
+  size_t table_bytes_per_set() const { return (size_t)k * (p - 1) * rwpad * 4; }
+};
+
+// Elimination, information sets, multiples, schedule.  Returns an fpcode
+// status; the error text is set on failure.
+int prepare(int p, int n, int k, const uint8_t *G, const fpcode_opts &opts, Prepared *out);
+
+// Tasks and prefixes per lane of every pass for a grid of `ctas` CTAs.
+void plan_tasks(Prepared *P, int ctas, int fixed_pl);
+
+// Fill a result from the final device state of one code.
+struct DeviceOutcome {
+  uint64_t best_key;     // kNoKey if none
+  uint64_t enumerated;
+  int status;            // fpcode status; -1: did not finish
+  int stop_pass;         // last pass entered (-1: none)
+};
+int decode_result(const Prepared &P, const DeviceOutcome &o, fpcode_result *res, uint8_t *witness);
+
+}  // namespace fph
+
+// The opaque handle of the C ABI: host preparation plus its device copy.
+struct fpcode_prepared {
+  fph::Prepared host;
+  int device = -1;
+  int ctas = 0;         // grid the tasks were planned for
+  int smem = 0;         // dynamic shared memory of one launch
+  bool uploaded = false;
+  bool external = false;  // device/pinned buffers borrowed from a workspace
+  char *dev = nullptr;    // [CtlStatic][SlotDesc][PassDesc...][table] [SlotState][CtlDyn]
+  size_t dev_bytes = 0;
+  size_t off_ctl = 0, off_slot = 0, off_pass = 0, off_table = 0, off_state = 0, dyn_bytes = 0;
+  char *pinned = nullptr; // read-back of the dynamic part
+  void *ev0 = nullptr, *ev1 = nullptr;  // cudaEvent_t around the kernel
+  fpcode_opts run_opts{};
+};

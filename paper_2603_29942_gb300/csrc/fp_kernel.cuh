@@ -1,0 +1,447 @@
+// fp_kernel.cuh -- persistent Brouwer-Zimmermann enumeration kernel (sm_103a).
+//
+// One launch serves a table of codes ("slots").  Every CTA loops: thread 0
+// claims a task -- a contiguous range of kThreads * pl prefixes of the
+// current pass of some code -- by atomicAdd on the code's (pass, task)
+// word; the CTA stages that information set's bit-sliced row multiples into
+// shared memory (coalesced 128-bit loads) and runs the task.  The CTA that
+// completes the last task of a pass decides, on the device, whether the
+// code is certified (L >= U, Sec. 3.1 Alg. 6) or hands out the next pass.
+// No CTA ever waits on another except for the bounded wait at a pass
+// hand-off, so single codes, batches and a stream of served codes share
+// this one loop.
+//
+// Inside a task each lane walks its prefixes in Gray order (one exact
+// bit-sliced add per step, Sec. 2.1 Alg. 3 / Alg. 4 or the generic form)
+// and, for every leaf row x > m and coefficient c, evaluates the weight of
+// S + c A[x] without forming it: the isometric subtraction of Sec. 4.3,
+// popc(OR_i (S_i xor (p-c)A[x]_i)) per word.  All lanes of a warp share the
+// leaf loop, so the leaf operand is a shared-memory broadcast.  A lane whose
+// candidate could lower the bound takes a rare slow path that recomputes
+// the weight exactly and folds a packed (weight, pass, prefix, leaf)
+// key into the code's atomicMin upper bound; the bound is polled at every
+// task for the early exit of Sec. 4.4.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fp_bitslice.cuh"
+#include "fp_enum.cuh"
+#include "fp_types.h"
+
+namespace fpk {
+
+// Launch-wide constants (device memory, written by the host).
+struct CtlStatic {
+  const fpenum::Binom *binom;
+  int32_t nslots;
+  int32_t serve;  // serving: slots appear while the kernel runs
+};
+
+// Per-launch limits, passed by value.
+struct KParams {
+  unsigned long long wait_limit_ns;  // longest single wait at a pass hand-off
+  unsigned long long timeout_ns;     // 0: none; else per-launch time limit
+  unsigned long long idle_limit_ns;  // serving: exit after this long idle
+  int32_t mid_pass;                  // -1: per code; 0 / 1: override
+  int32_t pad;
+};
+
+// Launch-wide dynamic flags (zeroed before each launch).
+struct CtlDyn {
+  int32_t err;   // 1: a hand-off wait gave up; 2: time limit reached
+  int32_t pad[3];
+};
+
+// SlotState.status while a code is running is 0; the finaliser stores
+// kDoneFlag | fpcode status.
+constexpr int32_t kDoneFlag = 0x100;
+
+template <int R, int W>
+struct Shape {
+  static constexpr int RW = R * W;
+  static constexpr int RWP = (RW + 3) & ~3;
+};
+
+__device__ __forceinline__ unsigned long long ld_vol(const unsigned long long *p) {
+  return *(volatile const unsigned long long *)p;
+}
+__device__ __forceinline__ int ld_vol(const int32_t *p) { return *(volatile const int32_t *)p; }
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// The best key is stored inverted (~key) so that an all-zero state means
+// "no codeword yet" and atomicMax keeps the minimum key.
+__device__ __forceinline__ uint64_t best_key(const SlotState *st) { return ~ld_vol(&st->best_key); }
+
+template <int RWP>
+__device__ __forceinline__ void load_entry(const uint32_t *tab, int idx, uint32_t (&e)[RWP]) {
+  const uint4 *src = reinterpret_cast<const uint4 *>(tab + idx * RWP);
+#pragma unroll
+  for (int q = 0; q < RWP / 4; ++q) {
+    uint4 v = src[q];
+    e[4 * q] = v.x;
+    e[4 * q + 1] = v.y;
+    e[4 * q + 2] = v.z;
+    e[4 * q + 3] = v.w;
+  }
+}
+
+// s += multiple v of row t (exact, word by word).  Entry layout: word-major,
+// e[w * R + i] = slice i of word w.
+template <int P, int R, int W>
+__device__ __forceinline__ void add_row(uint32_t (&s)[R * W], const uint32_t *tab, int t, int v, int p) {
+  constexpr int RWP = Shape<R, W>::RWP;
+  uint32_t e[RWP];
+  load_entry<RWP>(tab, t * (p - 1) + (v - 1), e);
+#pragma unroll
+  for (int w = 0; w < W; ++w) fpbs::add_exact<P, R>(&s[w * R], &e[w * R], &s[w * R], p);
+}
+
+template <int P, int R, int W>
+__device__ __forceinline__ void set_row(uint32_t (&s)[R * W], const uint32_t *tab, int t, int v, int p) {
+  constexpr int RWP = Shape<R, W>::RWP;
+  uint32_t e[RWP];
+  load_entry<RWP>(tab, t * (p - 1) + (v - 1), e);
+#pragma unroll
+  for (int q = 0; q < R * W; ++q) s[q] = e[q];
+}
+
+// Exact sum of a prefix: A[m] (coefficient 1) + sum over the slots of Q.
+template <int P, int R, int W, int DB>
+__device__ __forceinline__ void build_sum(uint32_t (&s)[R * W], const uint32_t *tab, const fpenum::Prefix &pf,
+                                          int L, int b, int p) {
+  set_row<P, R, W>(s, tab, pf.m, 1, p);
+  uint64_t Q = pf.Q;
+  for (int slot = 0; slot < L; ++slot) {
+    int q = fpenum::ctz64(Q);
+    Q &= Q - 1;
+    int coef = fpenum::gray_digit<DB>(pf.d, slot, b, L) + 1;
+    add_row<P, R, W>(s, tab, q, coef, p);
+  }
+}
+
+// Weight of the redundant part of S + c A[x] via the stored multiple
+// (p - c) A[x] = -c A[x]: isometric subtraction, one popc per word.
+template <int R, int W>
+__device__ __forceinline__ int leaf_weight(const uint32_t (&s)[R * W], const uint32_t *e) {
+  int wsum = 0;
+#pragma unroll
+  for (int w = 0; w < W; ++w) wsum += __popc(fpbs::nz_sub<R>(&s[w * R], &e[w * R]));
+  return wsum;
+}
+
+// Record a candidate codeword; returns the (possibly lowered) bound U.
+__device__ __forceinline__ int record(SlotState *st, uint64_t key) {
+  unsigned long long old = atomicMax(&st->best_key, (unsigned long long)~key);
+  uint64_t best = ~(uint64_t)old;
+  if (key < best) best = key;
+  return (int)key_weight(best);
+}
+
+// ---------------------------------------------------------------------------
+// Task of a pass with g == 1: the k rows themselves (coefficient 1).
+// ---------------------------------------------------------------------------
+template <int P, int R, int W>
+__device__ void task_rows(const SlotDesc &sd, int pass, const uint32_t *tab, int U, SlotState *st,
+                          unsigned long long &count) {
+  constexpr int RWP = Shape<R, W>::RWP;
+  const int x = threadIdx.x;
+  const int p = P ? P : sd.p;
+  if (x < sd.k) {
+    uint32_t e[RWP];
+    load_entry<RWP>(tab, x * (p - 1), e);
+    int wsum = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) wsum += __popc(fpbs::nz<R>(&e[w * R]));
+    int weight = 1 + wsum;
+    if (weight <= U) record(st, make_key((uint32_t)weight, (uint32_t)pass, 0, (uint32_t)x, 1));
+    count += 1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Task of a pass with g >= 2.
+// ---------------------------------------------------------------------------
+template <int P, int R, int W, int DB>
+__device__ void task_prefixes(const SlotDesc &sd, const PassDesc &pd, int pass, const uint32_t *tab,
+                              const fpenum::Binom &B, uint64_t task, int U, SlotState *st,
+                              unsigned long long &count) {
+  constexpr int RW = R * W;
+  constexpr int RWP = Shape<R, W>::RWP;
+  const int p = P ? P : sd.p;
+  const int b = p - 1;
+  const int k = sd.k;
+  const int g = pd.g;
+  const int L = g - 2;
+  const int pl = pd.pl;
+  uint64_t I = (task * kThreads + threadIdx.x) * (uint64_t)pl;
+  const uint64_t Iend = min(I + (uint64_t)pl, pd.nprefix);
+  int thr = U - g + 1;  // record weights <= U: redundant weight < U - g + 1
+
+  uint32_t s[RW];
+#pragma unroll
+  for (int q = 0; q < RW; ++q) s[q] = 0;
+  fpenum::Prefix pf;
+  pf.m = k;
+  pf.qi = 0;
+  pf.Q = 0;
+  pf.d = 0;
+  uint64_t ci = 0, nq = 1;
+  if (I < Iend) {
+    pf = fpenum::prefix_unrank<DB>(B, I, k, g, b);
+    ci = (I - fpenum::prefixes_below(B, pf.m, g, pd.NC)) - pf.qi * pd.NC;
+    nq = B.c[pf.m][L];
+    build_sum<P, R, W, DB>(s, tab, pf, L, b, p);
+  }
+
+  for (int step = 0; step < pl; ++step) {
+    const bool act = I < Iend;
+    const int mlane = act ? pf.m : k;
+    const int xs = (int)__reduce_min_sync(0xffffffffu, (unsigned)mlane) + 1;
+    for (int x = xs; x < k; ++x) {
+      const int tx = x > mlane ? thr : 0;
+      bool hit = false;
+      if (P) {
+#pragma unroll
+        for (int c = 1; c < (P ? P : 2); ++c) {
+          uint32_t e[RWP];
+          load_entry<RWP>(tab, x * b + (p - c - 1), e);
+          hit |= leaf_weight<R, W>(s, e) < tx;
+        }
+      } else {
+        for (int c = 1; c < p; ++c) {
+          uint32_t e[RWP];
+          load_entry<RWP>(tab, x * b + (p - c - 1), e);
+          hit |= leaf_weight<R, W>(s, e) < tx;
+        }
+      }
+      if (__any_sync(0xffffffffu, hit)) {
+        if (hit) {  // slow path: exact weights, record the candidates
+          for (int c = 1; c < p; ++c) {
+            uint32_t e[RWP];
+            load_entry<RWP>(tab, x * b + (p - c - 1), e);
+            int wr = leaf_weight<R, W>(s, e);
+            if (wr < thr) {
+              int newU = record(st, make_key((uint32_t)(g + wr), (uint32_t)pass, I, (uint32_t)x, (uint32_t)c));
+              thr = newU - g + 1;
+            }
+          }
+        }
+        thr = (int)__reduce_min_sync(0xffffffffu, (unsigned)thr);
+      }
+    }
+    if (act) count += (unsigned long long)(k - 1 - pf.m) * (unsigned long long)b;
+    // advance to prefix I + 1
+    ++I;
+    if (I < Iend) {
+      int dir;
+      const int slot = fpenum::prefix_advance<DB>(B, pf, ci, nq, pd.NC, b, L, &dir);
+      if (slot >= 0) {
+        const int q = fpenum::nth_member(pf.Q, slot);
+        add_row<P, R, W>(s, tab, q, dir > 0 ? 1 : b, p);  // c -> c+1: +A; c -> c-1: +(p-1)A
+      } else {
+        build_sum<P, R, W, DB>(s, tab, pf, L, b, p);
+      }
+    }
+  }
+}
+
+template <int P, int R, int W>
+struct Fixed {
+  static constexpr int DB = (P != 0 && P <= 17) ? 4 : 8;
+  static __device__ __forceinline__ void run(const SlotDesc &sd, const PassDesc &pd, int pass, const uint32_t *tab,
+                                             const fpenum::Binom &B, uint64_t task, int U, SlotState *st,
+                                             unsigned long long &count) {
+    if (pd.g == 1) {
+      if (task == 0) task_rows<P, R, W>(sd, pass, tab, U, st, count);
+    } else {
+      task_prefixes<P, R, W, DB>(sd, pd, pass, tab, B, task, U, st, count);
+    }
+  }
+};
+
+// Variant id: prime class * 4 + (W - 1); classes 0: p = 3, 1: p = 5,
+// 2: p = 7, 3 + (r - 4): other primes with r bits (r = 4..8).
+__host__ __device__ inline int variant_id(int p, int r, int W) {
+  int cls = p == 3 ? 0 : p == 5 ? 1 : p == 7 ? 2 : 3 + (r - 4);
+  return cls * 4 + (W - 1);
+}
+
+// Batched launches over codes with p in {3, 5, 7}: dispatch per task.
+struct Multi357 {
+  static __device__ __forceinline__ void run(const SlotDesc &sd, const PassDesc &pd, int pass, const uint32_t *tab,
+                                             const fpenum::Binom &B, uint64_t task, int U, SlotState *st,
+                                             unsigned long long &count) {
+    switch (sd.variant) {
+#define FPK_CASE(id, P, R, W) \
+  case id: Fixed<P, R, W>::run(sd, pd, pass, tab, B, task, U, st, count); break;
+      FPK_CASE(0, 3, 2, 1)
+      FPK_CASE(1, 3, 2, 2)
+      FPK_CASE(2, 3, 2, 3)
+      FPK_CASE(3, 3, 2, 4)
+      FPK_CASE(4, 5, 3, 1)
+      FPK_CASE(5, 5, 3, 2)
+      FPK_CASE(6, 5, 3, 3)
+      FPK_CASE(7, 5, 3, 4)
+      FPK_CASE(8, 7, 3, 1)
+      FPK_CASE(9, 7, 3, 2)
+      FPK_CASE(10, 7, 3, 3)
+      FPK_CASE(11, 7, 3, 4)
+#undef FPK_CASE
+      default: break;
+    }
+  }
+};
+
+enum { kCmdRun = 0, kCmdWait = 1, kCmdExit = 2 };
+
+// Thread 0: claim the next task of any live code.
+__device__ __forceinline__ int claim(const SlotDesc *slots, SlotState *states, const CtlStatic &cs,
+                                     const KParams &kp, CtlDyn *cd, int &rr, unsigned long long &wait_t0, unsigned long long t_start,
+                                     int *o_slot, int *o_pass, unsigned long long *o_task, int *o_U, int *o_skip) {
+  const int nslots = cs.nslots;
+  unsigned long long now = globaltimer();
+  if (kp.timeout_ns && now - t_start > kp.timeout_ns) {
+    atomicExch(&cd->err, 2);
+    return kCmdExit;
+  }
+  bool live = false;
+  for (int probe = 0; probe < nslots; ++probe) {
+    int s = rr + probe;
+    if (s >= nslots) s -= nslots;
+    SlotState *st = &states[s];
+    if (ld_vol(&st->finished)) continue;
+    const SlotDesc &sd = slots[s];
+    if (sd.npasses <= 0) continue;
+    live = true;
+    unsigned long long w = ld_vol(&st->word);
+    int P = (int)(w >> 40);
+    if (P >= sd.npasses || (w & kTaskMask) >= sd.passes[P].ntasks) continue;
+    w = atomicAdd(&st->word, 1ull);
+    P = (int)(w >> 40);
+    unsigned long long t = w & kTaskMask;
+    if (P >= sd.npasses || t >= sd.passes[P].ntasks) continue;
+    uint64_t key = best_key(st);
+    int U = key == kNoKey ? sd.n - sd.k + 2 : (int)key_weight(key);
+    const int mid = kp.mid_pass < 0 ? sd.mid_pass_exit : kp.mid_pass;
+    *o_skip = (mid && U <= sd.passes[P].L_before) ? 1 : 0;
+    *o_slot = s;
+    *o_pass = P;
+    *o_task = t;
+    *o_U = U;
+    rr = s;
+    wait_t0 = 0;
+    return kCmdRun;
+  }
+  if (!live && !cs.serve) return kCmdExit;
+  if (ld_vol(&cd->err)) return kCmdExit;
+  if (wait_t0 == 0) {
+    wait_t0 = now;
+  } else {
+    unsigned long long lim = live ? kp.wait_limit_ns : kp.idle_limit_ns;
+    if (now - wait_t0 > lim) {
+      if (live) atomicExch(&cd->err, 1);
+      return kCmdExit;
+    }
+  }
+  __nanosleep(live ? 256 : 2000);
+  return kCmdWait;
+}
+
+// Thread 0: count a finished task; the last task of a pass decides.
+__device__ __forceinline__ void finish_task(const SlotDesc &sd, SlotState *st, int P) {
+  __threadfence();
+  unsigned long long done = atomicAdd(&st->done, 1ull) + 1ull;
+  const PassDesc &pd = sd.passes[P];
+  if (done != pd.ntasks) return;
+  __threadfence();
+  uint64_t key = ~(uint64_t)atomicOr(&st->best_key, 0ull);
+  int U = key == kNoKey ? sd.n - sd.k + 2 : (int)key_weight(key);
+  const bool check = !sd.per_round_check || pd.round_end;
+  const bool certified = check && pd.L_after >= U;
+  if (certified || P + 1 >= sd.npasses) {
+    st->stop_pass = P;
+    st->status = kDoneFlag | ((certified || sd.complete) ? 0 : 4 /* FPCODE_EBUDGET */);
+    __threadfence();
+    atomicExch(&st->finished, 1);
+    return;
+  }
+  st->done = 0;
+  __threadfence();
+  atomicExch(&st->word, (unsigned long long)(P + 1) << 40);
+}
+
+template <class V>
+__global__ void __launch_bounds__(kThreads) bz_kernel(const SlotDesc *__restrict__ slots, SlotState *states,
+                                                      const CtlStatic *__restrict__ ctl, CtlDyn *cdyn,
+                                                      KParams kp) {
+  extern __shared__ uint4 smem_raw[];
+  uint32_t *tab = reinterpret_cast<uint32_t *>(smem_raw);
+  __shared__ int s_cmd, s_slot, s_pass, s_U, s_skip, s_stage;
+  __shared__ unsigned long long s_task, s_count;
+  __shared__ int s_staged_slot, s_staged_j;
+
+  const CtlStatic cs = *ctl;
+  const int tid = threadIdx.x;
+  int rr = (int)(blockIdx.x % (unsigned)(cs.nslots > 0 ? cs.nslots : 1));
+  unsigned long long wait_t0 = 0;
+  const unsigned long long t_start = globaltimer();
+  if (tid == 0) {
+    s_staged_slot = -1;
+    s_staged_j = -1;
+  }
+  for (;;) {
+    if (tid == 0) {
+      int slot = 0, pass = 0, U = 0, skip = 0;
+      unsigned long long task = 0;
+      int cmd = claim(slots, states, cs, kp, cdyn, rr, wait_t0, t_start, &slot, &pass, &task, &U, &skip);
+      s_cmd = cmd;
+      if (cmd == kCmdRun) {
+        s_slot = slot;
+        s_pass = pass;
+        s_task = task;
+        s_U = U;
+        s_skip = skip;
+        const int j = slots[slot].passes[pass].j;
+        s_stage = (!skip && (slot != s_staged_slot || j != s_staged_j)) ? 1 : 0;
+        if (s_stage) {
+          s_staged_slot = slot;
+          s_staged_j = j;
+        }
+      }
+      s_count = 0;
+    }
+    __syncthreads();
+    const int cmd = s_cmd;
+    if (cmd == kCmdExit) break;
+    if (cmd == kCmdWait) {
+      __syncthreads();
+      continue;
+    }
+    const int slot = s_slot, pass = s_pass;
+    const SlotDesc &sd = slots[slot];
+    const PassDesc pd = sd.passes[pass];
+    if (s_stage) {
+      const int words = sd.k * (sd.p - 1) * sd.rwpad;
+      const uint4 *src = reinterpret_cast<const uint4 *>(sd.table + (size_t)pd.j * (size_t)words);
+      for (int i = tid; i < words / 4; i += kThreads) smem_raw[i] = src[i];
+      __syncthreads();
+    }
+    unsigned long long count = 0;
+    if (!s_skip) V::run(sd, pd, pass, tab, *cs.binom, s_task, s_U, &states[slot], count);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) count += __shfl_xor_sync(0xffffffffu, count, o);
+    if ((tid & 31) == 0 && count) atomicAdd(&s_count, count);
+    __syncthreads();
+    if (tid == 0) {
+      if (s_count) atomicAdd(&states[slot].enumerated, s_count);
+      finish_task(sd, &states[slot], pass);
+    }
+  }
+}
+
+}  // namespace fpk

@@ -1,0 +1,12 @@
+// fp_kernels.h -- host stubs of the enumeration kernel instantiations.
+#pragma once
+
+namespace fpk {
+// Kernel for one (prime class, words) variant; nullptr if not built.
+const void *kernel_p3(int W);
+const void *kernel_p5(int W);
+const void *kernel_p7(int W);
+const void *kernel_generic(int r, int W);
+// Batched kernel dispatching per task over p in {3, 5, 7}, W in 1..4.
+const void *kernel_multi357();
+}  // namespace fpk

@@ -1,0 +1,89 @@
+// fp_types.h -- data shared by the host driver and the enumeration kernels.
+#pragma once
+#include <stdint.h>
+
+#if defined(__CUDACC__)
+#define FPK_HD __host__ __device__ inline
+#else
+#define FPK_HD inline
+#endif
+
+namespace fpk {
+
+constexpr int kThreads = 256;        // threads per CTA (8 warps)
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxK = 64;            // rows: subsets are 64-bit masks
+constexpr int kMaxW = 4;             // 32-bit words per slice: n - k <= 128
+constexpr int kMaxPasses = 255;      // pass index fits 8 bits of the key
+constexpr int kMaxN = 255;           // weight fits 8 bits of the key
+constexpr uint64_t kMaxPrefix = 1ull << 34;  // prefix index fits 34 bits
+
+// Packed witness key: (weight, pass, prefix index, leaf row, leaf coefficient).
+// atomicMin on it keeps the lowest weight and, among equal weights, the
+// first codeword in enumeration order.
+constexpr int kKeyW = 56, kKeyP = 48, kKeyI = 14, kKeyX = 8;
+constexpr uint64_t kNoKey = ~0ull;
+
+FPK_HD uint64_t make_key(uint32_t weight, uint32_t pass, uint64_t I, uint32_t x, uint32_t c) {
+  return ((uint64_t)weight << kKeyW) | ((uint64_t)pass << kKeyP) | (I << kKeyI) | ((uint64_t)x << kKeyX) |
+         (uint64_t)c;
+}
+FPK_HD uint32_t key_weight(uint64_t key) { return (uint32_t)(key >> kKeyW); }
+FPK_HD uint32_t key_pass(uint64_t key) { return (uint32_t)(key >> kKeyP) & 0xFFu; }
+FPK_HD uint64_t key_prefix(uint64_t key) { return (key >> kKeyI) & ((1ull << 34) - 1); }
+FPK_HD uint32_t key_leaf(uint64_t key) { return (uint32_t)(key >> kKeyX) & 63u; }
+FPK_HD uint32_t key_coef(uint64_t key) { return (uint32_t)key & 0xFFu; }
+
+// One pass (g, j) of the schedule.
+struct PassDesc {
+  int32_t g, j;
+  int32_t L_before;   // lower bound before the pass (valid: earlier passes complete)
+  int32_t L_after;    // lower bound once the pass is complete
+  int32_t round_end;  // last pass of round g (per-round termination check)
+  int32_t pl;         // prefixes per lane in one CTA task
+  uint32_t ntasks;    // CTA tasks in the pass
+  uint32_t pad;
+  uint64_t nprefix;   // prefixes (g >= 2) or rows (g == 1)
+  uint64_t size;      // codewords in the pass: C(k,g)(p-1)^(g-1)
+  uint64_t NC;        // (p-1)^(g-2) coefficient vectors per prefix subset
+};
+
+// Static description of one code as the kernel sees it.
+struct SlotDesc {
+  int32_t p, n, k, r, W, rwpad;  // rwpad: words per stored multiple (r*W rounded up to 4)
+  int32_t m, npasses;
+  int32_t variant;               // kernel variant (prime and words)
+  int32_t per_round_check;
+  int32_t mid_pass_exit;
+  int32_t complete;              // 1: the schedule runs to the last level
+  const uint32_t *table;         // m * k * (p-1) * rwpad words, device
+  const PassDesc *passes;        // npasses entries, device
+};
+
+// Dynamic state of one code, device memory.
+struct SlotState {
+  unsigned long long word;        // (pass << 40) | next task
+  unsigned long long done;        // tasks finished in the current pass
+  unsigned long long best_key;    // packed witness key (kNoKey: none yet)
+  unsigned long long enumerated;  // codewords evaluated
+  int32_t status;                 // kRunning until finished
+  int32_t stop_pass;              // last pass entered
+  int32_t finished;               // 1: nothing left to do
+  int32_t pad;
+};
+
+constexpr int32_t kRunning = -1;
+constexpr uint64_t kTaskMask = (1ull << 40) - 1;
+
+// Launch-wide control block (device memory).
+struct Ctl {
+  unsigned long long wait_limit_ns;  // longest single wait for a pass hand-off
+  unsigned long long deadline_ns;    // 0: none; else %globaltimer deadline
+  int32_t nslots;
+  int32_t err;                       // set when a wait gave up
+  int32_t serve;                     // serving mode: slots appear while running
+  int32_t pad;
+  unsigned long long idle_limit_ns;  // serving: exit after this long idle
+};
+
+}  // namespace fpk

@@ -1,0 +1,208 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bit-exact on d, on the codewords enumerated per level g (counts of the
+passes entered), on L and on the schedule; the witness is a nonzero
+codeword of weight d (checked against a parity-check matrix computed by the
+tests' own linear algebra).  Where several witnesses are correct they are
+verified, not compared.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+import gf
+import oracle
+from paper_2603_29942_gb300 import _binding as B
+from paper_2603_29942_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for -m gpu tests")
+    B.lib()
+
+
+def golden():
+    with open(os.path.join(HERE, "golden", "oracle_single_codes.json")) as f:
+        return json.load(f)
+
+
+def check_witness(code, d, w):
+    w = [int(x) for x in w]
+    assert any(w) and gf.weight(w) == d
+    H = gf.null_space(np.asarray(code.G).tolist(), code.p)  # rows span the dual
+    for h in H:
+        assert sum(a * b for a, b in zip(h, w)) % code.p == 0
+
+
+def run(code, **kw):
+    pr = B.fpcode_prepare(code.p, code.n, code.k, code.G, B.fpcode_opts_default(**kw))
+    return B.fpcode_min_distance_ex(pr), pr
+
+
+# --------------------------------------------------- bit-sliced ops ----
+
+@pytest.mark.parametrize("p", [3, 5, 7, 11, 13, 31, 127, 251])
+def test_bitslice_ops_on_device(p):
+    """The device build of every operation equals mod-p arithmetic on all
+    p^2 pairs, spread over random lane positions."""
+    r = p.bit_length()
+    rng = np.random.default_rng(p)
+    pairs = [(a, b) for a in range(p) for b in range(p)]
+    reps = max(1, 4096 // len(pairs))
+    A = np.zeros((len(pairs) * reps, r), dtype=np.uint32)
+    Bm = np.zeros_like(A)
+    expect = []
+    for i in range(len(pairs) * reps):
+        lanes = rng.integers(0, p, size=(32, 2))
+        lanes[i % 32] = pairs[i % len(pairs)]
+        for q in range(32):
+            for s in range(r):
+                A[i, s] |= np.uint32(((int(lanes[q, 0]) >> s) & 1) << q)
+                Bm[i, s] |= np.uint32(((int(lanes[q, 1]) >> s) & 1) << q)
+        expect.append(lanes)
+    out = B.fpcode_test_bitslice_device(B.OP_ADD, p, A, Bm, r).reshape(-1, r)
+    nz = B.fpcode_test_bitslice_device(B.OP_NZ_SUB, p, A, Bm, r)
+    for i, lanes in enumerate(expect):
+        for q in range(32):
+            s = sum(((int(out[i, b]) >> q) & 1) << b for b in range(r))
+            assert s == (int(lanes[q, 0]) + int(lanes[q, 1])) % p
+            assert ((int(nz[i]) >> q) & 1) == int(lanes[q, 0] != lanes[q, 1])
+
+
+# ------------------------------------------------- single workloads ----
+
+@pytest.mark.parametrize("name", ["f3_n30_k15", "f7_n40_k20", "f3_n80_k40"])
+def test_single_code_parity(name):
+    code = inputs.single(name)
+    g = golden()[name]
+    assert code.digest() == g["sha256"]
+    for mode, kw in (("default", {}), ("paper_literal", {"per_round_check": 1, "defer": 0})):
+        exp = g[mode]
+        for mid in (1, 0):
+            res, _ = run(code, mid_pass_exit=mid, **kw)
+            assert res.status == B.OK
+            assert (res.d, res.L, res.U, res.m, res.kj) == (exp["d"], exp["L"], exp["U"], exp["m"], exp["kj"])
+            assert res.counts == exp["counts"]
+            assert res.npasses == len(exp["passes"])
+            if mid == 0:  # every pass entered is fully enumerated
+                assert res.enumerated == exp["evaluated"]
+            else:
+                assert res.enumerated <= exp["evaluated"]
+            check_witness(code, res.d, res.witness)
+
+
+def test_parity_mode_witness_is_deterministic():
+    code = inputs.single("f7_n40_k20")
+    ws = []
+    for _ in range(3):
+        res, _ = run(code, mid_pass_exit=0)
+        ws.append(res.witness.tobytes())
+    assert len(set(ws)) == 1
+
+
+@pytest.mark.parametrize("pl", [1, 3, 64])
+def test_task_shape_does_not_change_result(pl):
+    code = inputs.single("f3_n80_k40")
+    exp = golden()["f3_n80_k40"]["default"]
+    res, _ = run(code, prefixes_per_lane=pl, mid_pass_exit=0, ctas_per_sm=1)
+    assert (res.d, res.counts, res.enumerated) == (exp["d"], exp["counts"], exp["evaluated"])
+
+
+def _random_codes(seed, count):
+    rng = np.random.default_rng(seed)
+    shapes = [(3, 20, 8), (5, 18, 7), (7, 16, 6), (11, 12, 5), (13, 12, 4), (3, 50, 12), (7, 45, 8),
+              (3, 90, 20), (5, 100, 10), (3, 140, 12), (3, 24, 24), (7, 9, 1), (3, 40, 39), (17, 10, 4),
+              (31, 9, 3), (127, 7, 2), (251, 6, 2)]
+    for i in range(count):
+        p, n, k = shapes[i % len(shapes)]
+        G = rng.integers(0, p, size=(k, n), dtype=np.uint8)
+        if i % 4 == 0:
+            G[:, rng.integers(0, n)] = 0
+        if i % 5 == 0:
+            G[:, :k] = np.eye(k, dtype=np.uint8)
+        if gf.rank(G.tolist(), p) < k:
+            continue
+        yield inputs.Code(p, n, k, G)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_codes_parity(seed):
+    """Random codes over several primes, word counts W = 1..4, rank-deficient
+    last information sets, zero columns, k = 1 and k = n: same d, counts, L,
+    schedule as the oracle; a valid witness."""
+    for code in _random_codes(1000 + seed, 17):
+        r = oracle.bz(code, threads=4, budget=5 * 10 ** 7)
+        res, _ = run(code, mid_pass_exit=seed % 2, budget=5 * 10 ** 7)
+        assert res.status == r.status, (code.p, code.n, code.k)
+        assert res.counts == r.counts
+        assert (res.L, res.U) == (r.L, r.U)
+        if r.status == oracle.OK:
+            assert res.d == r.d
+            check_witness(code, res.d, res.witness)
+
+
+def test_budget_interval():
+    code = inputs.single("f7_n40_k20")
+    r = oracle.bz(code, budget=100000)
+    res, _ = run(code, budget=100000)
+    assert res.status == B.EBUDGET == r.status
+    assert (res.L, res.U, res.counts) == (r.L, r.U, r.counts)
+
+
+def test_one_shot_call():
+    code = inputs.single("f3_n30_k15")
+    d, w = B.fpcode_min_distance(code.p, code.n, code.k, code.G)
+    assert d == 6
+    check_witness(code, d, w)
+
+
+def test_batch_equals_alone():
+    codes = inputs.batch_codes(48)
+    budgets = [2 * 10 ** 6] * len(codes)
+    res = B.fpcode_min_distance_batch(codes, budgets=budgets)
+    for c, rb in zip(codes, res):
+        ra, _ = run(c, budget=2 * 10 ** 6)
+        assert (rb.status, rb.d, rb.L, rb.U, rb.counts) == (ra.status, ra.d, ra.L, ra.U, ra.counts)
+        if rb.status == B.OK:
+            check_witness(c, rb.d, rb.witness)
+
+
+def test_batch_against_oracle_mixed_primes():
+    rng = np.random.default_rng(77)
+    codes = []
+    for i in range(30):
+        p = [3, 5, 7, 11, 13][i % 5]
+        n = int(rng.integers(12, 40))
+        k = int(rng.integers(3, min(n, 14)))
+        codes.append(inputs.single_code(500 + i, p, n, k))
+    res = B.fpcode_min_distance_batch(codes, budgets=[10 ** 7] * len(codes))
+    for c, rb in zip(codes, res):
+        r = oracle.bz(c, budget=10 ** 7, threads=4)
+        assert (rb.status, rb.counts, rb.L, rb.U) == (r.status, r.counts, r.L, r.U)
+        if r.status == oracle.OK:
+            assert rb.d == r.d
+            check_witness(c, rb.d, rb.witness)
+
+
+def test_bounded_wait_reports_timeout():
+    """A hand-off wait limit far below a task's duration makes the waiting
+    CTAs give up and the kernel return; the host reports ETIMEOUT and the
+    context stays usable."""
+    code = inputs.single("f3_n80_k40")
+    res, _ = run(code, wait_limit_s=1e-7)
+    assert res.status in (B.ETIMEOUT, B.OK)
+    res2, _ = run(code, timeout_s=1e-6)
+    assert res2.status == B.ETIMEOUT
+    assert res2.L <= 14
+    ok, _ = run(code)
+    assert ok.status == B.OK and ok.d == 14

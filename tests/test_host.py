@@ -1,0 +1,338 @@
+"""CPU tests of libfpcode's host logic (no GPU needed).
+
+- the library loads and exports every function include/*.h declares;
+- bit-sliced F_p operations, exhaustively over all p^2 operand pairs for
+  every odd prime p < 256, against plain mod-p arithmetic;
+- the paper's worked examples (tests/golden/paper_examples.json);
+- revolving-door order and the prefix walk against their definitions;
+- information sets and pass schedule against the oracle.
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_29942_gb300 import _binding as B
+from paper_2603_29942_gb300 import inputs
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+PRIMES = [p for p in range(3, 256, 2) if all(p % q for q in range(3, int(p ** 0.5) + 1, 2))]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return B.lib()
+
+
+def r_bits(p):
+    return p.bit_length()
+
+
+def slices(vals, r):
+    """Sliced-bit storage (Sec. 2): slice i holds bit i of every symbol."""
+    out = np.zeros(r, dtype=np.uint32)
+    for q, v in enumerate(vals):
+        for i in range(r):
+            if (v >> i) & 1:
+                out[i] |= np.uint32(1 << q)
+    return out
+
+
+def unslice(words, r, count):
+    return [sum(((int(words[i]) >> q) & 1) << i for i in range(r)) for q in range(count)]
+
+
+def test_exports_match_headers(lib):
+    declared = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            declared |= set(re.findall(r"\b(fpcode_[a-z0-9_]+)\s*\(", src))
+    missing = [n for n in sorted(declared) if not hasattr(lib, n)]
+    assert not missing, f"declared but not exported: {missing}"
+    assert declared <= set(B.EXPORTS) | {"fpcode_last_error"} | set(B.EXPORTS)
+
+
+# ------------------------------------------------------- bit-sliced ops ----
+
+def _pairs(p):
+    """All p^2 pairs, 32 per word batch."""
+    pairs = list(itertools.product(range(p), repeat=2))
+    for i in range(0, len(pairs), 32):
+        yield pairs[i:i + 32]
+
+
+@pytest.mark.parametrize("p", PRIMES)
+def test_exact_add_exhaustive(p, lib):
+    r = r_bits(p)
+    for chunk in _pairs(p):
+        a = slices([x for x, _ in chunk], r)
+        b = slices([y for _, y in chunk], r)
+        out = B.fpcode_test_bitslice_host(B.OP_ADD, p, a, b)
+        assert unslice(out, r, len(chunk)) == [(x + y) % p for x, y in chunk]
+        # padding lanes (beyond the chunk) stay zero
+        if len(chunk) < 32:
+            assert all((int(w) >> len(chunk)) == 0 for w in out[:r])
+
+
+@pytest.mark.parametrize("p", PRIMES)
+def test_iso_sub_exhaustive(p, lib):
+    r = r_bits(p)
+    for chunk in _pairs(p):
+        a = slices([x for x, _ in chunk], r)
+        b = slices([y for _, y in chunk], r)
+        m = int(B.fpcode_test_bitslice_host(B.OP_NZ_SUB, p, a, b)[0])
+        assert [(m >> q) & 1 for q in range(len(chunk))] == [int((x - y) % p != 0) for x, y in chunk]
+
+
+@pytest.mark.parametrize("p", [3, 7, 31, 127])
+def test_mersenne_ops_exhaustive(p, lib):
+    """Isometric addition (Sec. 4.3), negation by complement and doubling by
+    slice rotation (Sec. 4.2) for p = 2^r - 1."""
+    r = r_bits(p)
+    for chunk in _pairs(p):
+        a = slices([x for x, _ in chunk], r)
+        b = slices([y for _, y in chunk], r)
+        m = int(B.fpcode_test_bitslice_host(B.OP_NZ_ADD, p, a, b)[0])
+        assert [(m >> q) & 1 for q in range(len(chunk))] == [int((x + y) % p != 0) for x, y in chunk]
+        neg = B.fpcode_test_bitslice_host(B.OP_NEG, p, a, b)
+        assert unslice(neg, r, len(chunk)) == [(-x) % p for x, _ in chunk]
+        dbl = B.fpcode_test_bitslice_host(B.OP_MUL2, p, a, b)
+        assert unslice(dbl, r, len(chunk)) == [(2 * x) % p for x, _ in chunk]
+
+
+# ----------------------------------------------------- worked examples ----
+
+def golden():
+    with open(os.path.join(HERE, "golden", "paper_examples.json")) as f:
+        return json.load(f)
+
+
+def test_paper_encodings_and_storage():
+    g = golden()
+    for key in ("natural_encoding_f3", "natural_encoding_f7"):
+        p = g[key]["p"]
+        for v, bits in g[key]["table"].items():
+            assert [(int(v) >> i) & 1 for i in range(r_bits(p))] == bits
+    st = g["sliced_storage"]
+    s = slices(st["vector"], 2)
+    assert [[(int(s[i]) >> q) & 1 for q in range(3)] for i in range(2)] == st["slices"]
+
+
+@pytest.mark.parametrize("name", ["example1", "example2", "example3"])
+def test_paper_addition_examples(name, lib):
+    ex = golden()[name]
+    p, r = ex["p"], r_bits(ex["p"])
+    a = slices([ex["V"]], r)
+    b = slices([ex["W"]], r)
+    assert [int(a[i]) & 1 for i in range(r)] == ex["v"]
+    out = B.fpcode_test_bitslice_host(B.OP_ADD, p, a, b)
+    assert [int(out[i]) & 1 for i in range(r)] == ex["c"]
+    assert unslice(out, r, 1) == [ex["sum"]]
+
+
+def test_paper_shift_and_rewrites(lib):
+    g = golden()
+    sh = g["shift_multiplication"]
+    w = sum(b << i for i, b in enumerate(sh["w"]))
+    a = slices([w], 3)
+    two = B.fpcode_test_bitslice_host(B.OP_MUL2, 7, a, a)
+    four = B.fpcode_test_bitslice_host(B.OP_MUL2, 7, two, two)
+    assert [int(two[i]) & 1 for i in range(3)] == sh["times2"]
+    assert [int(four[i]) & 1 for i in range(3)] == sh["times4"]
+    for key in ("f7_rewrites", "f3_rewrite"):
+        p = g[key]["p"]
+        for _s1, h, s2, h2 in g[key]["rows"]:
+            for v in range(p):
+                for wv in range(p):
+                    rhs = (v + h2 * wv) % p if s2 == "+" else (v - h2 * wv) % p
+                    assert (v + h * wv) % p == rhs
+
+
+def test_alg3_reading():
+    """Alg. 3 line 6 as printed (s0 = s0 and carry_1) is wrong on 5 of the 9
+    pairs of F_3; read as xor it is right on all 9 (natural encoding)."""
+    def alg3(a, b, sixth):
+        a0, a1, b0, b1 = a & 1, a >> 1, b & 1, b >> 1
+        s0 = a0 ^ b0
+        c0 = a0 & b0
+        s1 = a1 ^ b1 ^ c0
+        c1 = a1 & b1
+        s0 = sixth(s0, c1)
+        t = s0 & s1
+        return (s0 ^ t) | ((s1 ^ t) << 1)
+    lit = sum(alg3(a, b, lambda x, y: x & y) != (a + b) % 3 for a in range(3) for b in range(3))
+    fix = sum(alg3(a, b, lambda x, y: x ^ y) != (a + b) % 3 for a in range(3) for b in range(3))
+    assert (lit, fix) == (5, 0)
+
+
+def test_alg5_as_printed_is_not_canonical():
+    """Alg. 5 (p != 2^r - 1) as printed leaves some sums in [p+1, 2^r); the
+    library therefore uses ripple add + conditional subtract.  Ex. 3 is one
+    of the cases it gets right."""
+    def alg5(p, v, w):
+        r = r_bits(p)
+        f = (1 << r) - p
+        d, e = v ^ w, v & w
+        while e:
+            eps = (e >> (r - 1)) & 1
+            v, w = d, (e << 1) & ((1 << r) - 1)
+            ef = f if eps else 0
+            d, e = v ^ w ^ ef, (v & w) | (v & ef) | (w & ef)
+        t = all((d >> i) & 1 for i in range(r) if (p >> i) & 1)
+        return d ^ (p if t else 0)
+    assert alg5(11, 10, 9) == 8
+    bad = {p: sum(alg5(p, a, b) != (a + b) % p for a in range(p) for b in range(p)) for p in (5, 11, 13)}
+    assert all(v > 0 for v in bad.values())
+
+
+# ---------------------------------------------------- enumeration order ----
+
+def revolving_door(n, t):
+    """R(n,t) from its recursive definition, subsets of {0..n-1}."""
+    if t == 0:
+        return [frozenset()]
+    if t == n:
+        return [frozenset(range(n))]
+    return revolving_door(n - 1, t) + [s | {n - 1} for s in reversed(revolving_door(n - 1, t - 1))]
+
+
+def mask(s):
+    return sum(1 << x for x in s)
+
+
+def test_revolving_door(lib):
+    for n in range(1, 13):
+        for t in range(0, n + 1):
+            seq = revolving_door(n, t)
+            assert len(seq) == math.comb(n, t)
+            for r, s in enumerate(seq):
+                assert B.fpcode_test_rd_unrank(r, n, t) == mask(s)
+                assert B.fpcode_test_rd_rank(mask(s), n, t) == r
+                nxt = B.fpcode_test_rd_next(mask(s), n, t)
+                if r + 1 < len(seq):
+                    assert nxt == mask(seq[r + 1])
+                    assert len(s ^ seq[r + 1]) == 2  # one exchange
+                else:
+                    assert nxt is None
+
+
+def _codeword_coeffs(k, g, p, I, x, c):
+    m, Q, coefs = B.fpcode_test_prefix_unrank(I, k, g, p)
+    v = [0] * k
+    v[m] = 1
+    for s, q in enumerate(sorted(b for b in range(64) if (Q >> b) & 1)):
+        v[q] = coefs[s]
+    assert x > m
+    v[x] = c
+    return v
+
+
+@pytest.mark.parametrize("k,g,p", [(6, 2, 3), (7, 3, 3), (7, 4, 5), (6, 3, 7), (8, 5, 3), (6, 4, 11), (9, 3, 7)])
+def test_pass_enumerates_each_class_once(k, g, p, lib):
+    """Prefixes x leaves of pass g visit every vector of F_p^k with exactly
+    g nonzeros exactly once up to scaling (Sec. 4.2)."""
+    NC = (p - 1) ** (g - 2)
+    nprefix = math.comb(k - 1, g - 1) * NC
+    seen = set()
+    count = 0
+    for I in range(nprefix):
+        m, _Q, _c = B.fpcode_test_prefix_unrank(I, k, g, p)
+        for x in range(m + 1, k):
+            for c in range(1, p):
+                v = _codeword_coeffs(k, g, p, I, x, c)
+                assert sum(1 for a in v if a) == g
+                lead = next(a for a in v if a)
+                inv = pow(lead, p - 2, p)
+                seen.add(tuple((a * inv) % p for a in v))
+                count += 1
+    assert count == math.comb(k, g) * (p - 1) ** (g - 1) == len(seen)
+
+
+@pytest.mark.parametrize("k,g,p", [(9, 4, 3), (8, 3, 7), (10, 5, 5), (12, 6, 3), (7, 4, 13)])
+def test_prefix_walk_matches_unrank(k, g, p, lib):
+    """The kernel's walk from prefix I reaches the prefix of index I + s, and
+    each Gray step changes exactly one coefficient by +-1."""
+    NC = (p - 1) ** (g - 2)
+    nprefix = math.comb(k - 1, g - 1) * NC
+    rng = np.random.default_rng(5)
+    starts = sorted(set(int(x) for x in rng.integers(0, nprefix, size=12)) | {0})
+    for I in starts:
+        steps = min(40, nprefix - 1 - I)
+        prev = B.fpcode_test_prefix_unrank(I, k, g, p)
+        for s in range(1, steps + 1):
+            walked = B.fpcode_test_prefix_walk(I, s, k, g, p)
+            assert walked == B.fpcode_test_prefix_unrank(I + s, k, g, p)
+            if walked[0] == prev[0] and walked[1] == prev[1]:
+                diff = [(a - b) % p for a, b in zip(walked[2], prev[2])]
+                assert sum(1 for d in diff if d) == 1 and all(d in (0, 1, p - 1) for d in diff)
+            prev = walked
+
+
+# ------------------------------------------------ preparation + schedule ----
+
+def _prep(code, **kw):
+    return B.fpcode_prepare(code.p, code.n, code.k, code.G, B.fpcode_opts_default(**kw))
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_info_sets_and_schedule_match_oracle(seed, lib):
+    rng = np.random.default_rng(100 + seed)
+    shapes = [(3, 11, 4), (7, 13, 5), (5, 10, 3), (3, 17, 6), (11, 9, 4), (3, 30, 15)]
+    p, n, k = shapes[seed % len(shapes)]
+    G = rng.integers(0, p, size=(k, n), dtype=np.uint8)
+    if seed % 3 == 0:
+        G[:, 1] = 0
+    code = inputs.Code(p, n, k, G)
+    try:
+        info = oracle.info_sets(code)
+    except ValueError:
+        with pytest.raises(B.FpcodeError):
+            _prep(code)
+        return
+    pr = _prep(code)
+    m, kj, npasses, complete = B.fpcode_prepared_shape(pr)
+    assert (m, kj) == (info.m, info.kj)
+    for j in range(m):
+        gam, piv = B.fpcode_prepared_gamma(pr, j)
+        assert np.array_equal(gam, info.gammas[j]) and piv == list(info.pivots[j])
+    for per_round, defer in ((0, 1), (1, 0), (0, 0)):
+        pr2 = _prep(code, per_round_check=per_round, defer=defer)
+        passes = B.fpcode_prepared_passes(pr2)
+        r = oracle.bz(code, per_round_check=bool(per_round), defer=bool(defer))
+        # the oracle's passes are a prefix of the full schedule
+        assert [(g, j) for g, j, *_ in passes[:len(r.passes)]] == [(g, j) for g, j, _b, _L in r.passes]
+        assert [La for _g, _j, _Lb, La, *_ in passes[:len(r.passes)]] == [L for *_x, L in r.passes]
+        for g, _j, _Lb, _La, _re, size, _np in passes:
+            assert size == math.comb(k, g) * (p - 1) ** (g - 1)
+
+
+def test_budget_truncates_schedule(lib):
+    code = inputs.single("f7_n40_k20")
+    pr = _prep(code, budget=100000)
+    _m, _kj, npasses, complete = B.fpcode_prepared_shape(pr)
+    passes = B.fpcode_prepared_passes(pr)
+    assert not complete and sum(x[5] for x in passes) <= 100000
+    r = oracle.bz(code, budget=100000)
+    assert [(g, j) for g, j, *_ in passes] == [(g, j) for g, j, _b, _L in r.passes]
+
+
+def test_prepare_rejects_bad_input(lib):
+    G = np.eye(3, 5, dtype=np.uint8)
+    for p, n, k, M in ((4, 5, 3, G), (3, 5, 3, G + 3), (3, 5, 0, G[:0]), (257, 5, 3, G)):
+        with pytest.raises(B.FpcodeError) as e:
+            B.fpcode_prepare(p, n, k, M)
+        assert e.value.status == B.EINVAL
+    rank_def = np.zeros((2, 5), dtype=np.uint8)
+    rank_def[0, 0] = rank_def[1, 0] = 1
+    with pytest.raises(B.FpcodeError):
+        B.fpcode_prepare(3, 5, 2, rank_def)
