@@ -44,6 +44,11 @@ def check_witness(code, d, w):
         assert sum(a * b for a, b in zip(h, w)) % code.p == 0
 
 
+def status_of_oracle(st):
+    """The oracle's status numbering mapped onto the library's."""
+    return {oracle.OK: B.OK, oracle.EBUDGET: B.EBUDGET}[st]
+
+
 def run(code, **kw):
     pr = B.fpcode_prepare(code.p, code.n, code.k, code.G, B.fpcode_opts_default(**kw))
     return B.fpcode_min_distance_ex(pr), pr
@@ -143,7 +148,7 @@ def test_random_codes_parity(seed):
     for code in _random_codes(1000 + seed, 17):
         r = oracle.bz(code, threads=4, budget=5 * 10 ** 7)
         res, _ = run(code, mid_pass_exit=seed % 2, budget=5 * 10 ** 7)
-        assert res.status == r.status, (code.p, code.n, code.k)
+        assert res.status == status_of_oracle(r.status), (code.p, code.n, code.k)
         assert res.counts == r.counts
         assert (res.L, res.U) == (r.L, r.U)
         if r.status == oracle.OK:
@@ -155,7 +160,7 @@ def test_budget_interval():
     code = inputs.single("f7_n40_k20")
     r = oracle.bz(code, budget=100000)
     res, _ = run(code, budget=100000)
-    assert res.status == B.EBUDGET == r.status
+    assert res.status == B.EBUDGET == status_of_oracle(r.status)
     assert (res.L, res.U, res.counts) == (r.L, r.U, r.counts)
 
 
@@ -188,7 +193,7 @@ def test_batch_against_oracle_mixed_primes():
     res = B.fpcode_min_distance_batch(codes, budgets=[10 ** 7] * len(codes))
     for c, rb in zip(codes, res):
         r = oracle.bz(c, budget=10 ** 7, threads=4)
-        assert (rb.status, rb.counts, rb.L, rb.U) == (r.status, r.counts, r.L, r.U)
+        assert (rb.status, rb.counts, rb.L, rb.U) == (status_of_oracle(r.status), r.counts, r.L, r.U)
         if r.status == oracle.OK:
             assert rb.d == r.d
             check_witness(c, rb.d, rb.witness)
