@@ -150,6 +150,23 @@ int fpcode_min_distance_ex(fpcode_prepared *prep, void *stream, const fpcode_opt
  * (no budget). */
 int fpcode_min_distance(int p, int n, int k, const uint8_t *G, void *stream, int *d, uint8_t *witness);
 
+/* fpcode_min_distance without any allocation, for callers that cannot call
+ * cudaMalloc (code running where the CUDA allocator is off limits, such as
+ * a host callback or a component whose device memory is fixed at start-up).
+ * The paper has no counterpart: this is a deployment variant of
+ * fpcode_min_distance.  It allocates no device memory and no pinned host
+ * memory (no cudaMalloc, cudaMallocHost, cudaFree or allocating library
+ * routine); host-side preparation uses the ordinary C++ heap.  All device
+ * state lives in one fixed 512 KiB array inside the library that every GPU
+ * loading the library keeps until exit; a code whose tables, schedule and
+ * state need more than that is rejected with FPCODE_EINVAL (message in
+ * fpcode_last_error) -- use fpcode_min_distance for it.  The first call on
+ * a device looks up the array's device address (make it before any stream
+ * capture).  Calls share the array: calls that overlap on the GPU race, and
+ * calls from this process are serialised on the host.  Same arguments and
+ * results as fpcode_min_distance. */
+int fpcode_min_distance_noalloc(int p, int n, int k, const uint8_t *G, void *stream, int *d, uint8_t *witness);
+
 /* One code of a batch or a served request. */
 typedef struct fpcode_desc {
   int p, n, k;

@@ -118,6 +118,8 @@ def _declare(lib):
         "fpcode_min_distance_ex": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(fpcode_opts),
                                                   ctypes.POINTER(fpcode_result), _U8P]),
         "fpcode_min_distance": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _U8P, _VP, _IP, _U8P]),
+        "fpcode_min_distance_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _U8P, _VP, _IP,
+                                                       _U8P]),
         "fpcode_min_distance_batch": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(fpcode_desc), _VP,
                                                      ctypes.POINTER(fpcode_opts), ctypes.POINTER(fpcode_result),
                                                      _U8P]),
@@ -287,6 +289,16 @@ def fpcode_min_distance(p: int, n: int, k: int, G, stream=None) -> tuple[int, np
     w = np.zeros(n, dtype=np.uint8)
     _check(lib().fpcode_min_distance(p, n, k, G.ctypes.data_as(_U8P), _stream(stream), ctypes.byref(d),
                                      w.ctypes.data_as(_U8P)), "fpcode_min_distance")
+    return d.value, w
+
+
+def fpcode_min_distance_noalloc(p: int, n: int, k: int, G, stream=None) -> tuple[int, np.ndarray]:
+    """fpcode_min_distance without device allocation (fixed in-library scratch)."""
+    G = _matrix(G)
+    d = ctypes.c_int(0)
+    w = np.zeros(n, dtype=np.uint8)
+    _check(lib().fpcode_min_distance_noalloc(p, n, k, G.ctypes.data_as(_U8P), _stream(stream), ctypes.byref(d),
+                                             w.ctypes.data_as(_U8P)), "fpcode_min_distance_noalloc")
     return d.value, w
 
 

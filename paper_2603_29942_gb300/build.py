@@ -13,7 +13,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfpcode.so")
 
-CU_SOURCES = ["fp_api.cu", "fp_k_p3.cu", "fp_k_p5.cu", "fp_k_p7.cu", "fp_k_generic.cu", "fp_k_multi.cu"]
+CU_SOURCES = ["fp_api.cu", "fp_k_p3.cu", "fp_k_p5.cu", "fp_k_p7.cu", "fp_k_generic.cu", "fp_k_multi.cu",
+              "fp_noalloc.cu"]
 CPP_SOURCES = ["fp_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

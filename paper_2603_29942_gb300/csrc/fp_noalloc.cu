@@ -1,0 +1,184 @@
+// fp_noalloc.cu -- fpcode_min_distance_noalloc: the certified-distance
+// search without any device or pinned-host allocation.
+//
+// Who needs it: code that runs where cudaMalloc is not available or not
+// allowed -- inside a host callback or a library that must not touch the
+// CUDA allocator, or under a memory budget fixed at start-up -- can still
+// certify a distance.  The search state, the pass schedule, the bit-sliced
+// row multiples and the binomial table live in one file-scope device array
+// (g_noalloc_scratch, kNoallocScratchBytes = 512 KiB) that every GPU loading
+// this library holds until the process exits.
+//
+// Host code never uses the array's name as an address: on the first call
+// on a device (with that device current) the address is fetched once with
+// cudaGetSymbolAddress and cached per device; that first call should
+// therefore come before any stream capture.  Every call shares the array
+// and it keeps the last call's contents, so calls that overlap on the GPU
+// (different streams or threads on the same device) race; a mutex
+// serialises calls from this process on the host side.  The state words the
+// kernel expects to start at zero are cleared by every call.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/fpcode.h"
+#include "fp_internal.h"
+#include "fp_kernel.cuh"
+#include "fp_kernels.h"
+
+namespace {
+
+constexpr size_t kNoallocScratchBytes = 512 * 1024;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;               // one call at a time (they share the array)
+bool g_noalloc_ready[kMaxDevices];
+unsigned char *g_noalloc_ptr[kMaxDevices];  // device address of the array, per device
+
+size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+#define NA_CUDA(call)                                                           \
+  do {                                                                          \
+    cudaError_t _e = (call);                                                    \
+    if (_e != cudaSuccess) {                                                    \
+      fph::set_error(std::string(#call) + ": " + cudaGetErrorString(_e));       \
+      return FPCODE_ECUDA;                                                      \
+    }                                                                           \
+  } while (0)
+
+// Once per device, with the device current: fetch the array's device
+// address and write the binomial table at its start.
+int noalloc_setup(int dev, unsigned char **out) {
+  if (!g_noalloc_ready[dev]) {
+    void *ptr = nullptr;
+    NA_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+    NA_CUDA(cudaMemcpy(ptr, &fph::binom(), sizeof(fpenum::Binom), cudaMemcpyHostToDevice));
+    g_noalloc_ptr[dev] = static_cast<unsigned char *>(ptr);
+    g_noalloc_ready[dev] = true;
+  }
+  *out = g_noalloc_ptr[dev];
+  return FPCODE_OK;
+}
+
+const void *kernel_of(int variant) {
+  const int cls = variant / 4, W = variant % 4 + 1;
+  switch (cls) {
+    case 0: return fpk::kernel_p3(W);
+    case 1: return fpk::kernel_p5(W);
+    case 2: return fpk::kernel_p7(W);
+    default: return fpk::kernel_generic(cls - 3 + 4, W);
+  }
+}
+
+}  // namespace
+
+extern "C" int fpcode_min_distance_noalloc(int p, int n, int k, const uint8_t *G, void *stream, int *d,
+                                           uint8_t *witness) {
+  if (!d) return FPCODE_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  fpcode_opts o;
+  fpcode_opts_default(&o);
+  fph::Prepared P;
+  int s = fph::prepare(p, n, k, G, o, &P);
+  if (s) return s;
+
+  // layout inside the array: [binom][CtlStatic][SlotDesc][passes][table][state][dyn]
+  const size_t off_ctl = a256(sizeof(fpenum::Binom));
+  const size_t off_slot = a256(off_ctl + sizeof(fpk::CtlStatic));
+  const size_t off_pass = a256(off_slot + sizeof(fpk::SlotDesc));
+  const size_t off_table = a256(off_pass + P.passes.size() * sizeof(fpk::PassDesc));
+  const size_t off_state = a256(off_table + P.table.size() * sizeof(uint32_t));
+  const size_t dyn_bytes = a256(sizeof(fpk::SlotState) + sizeof(fpk::CtlDyn));
+  if (off_state + dyn_bytes > kNoallocScratchBytes) {
+    fph::set_error("fpcode_min_distance_noalloc: the code needs " + std::to_string(off_state + dyn_bytes) +
+                   " bytes of device scratch, above the fixed 524288; use fpcode_min_distance");
+    return FPCODE_EINVAL;
+  }
+
+  int dev = 0;
+  NA_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return FPCODE_EINVAL;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  unsigned char *base = nullptr;
+  s = noalloc_setup(dev, &base);
+  if (s) return s;
+
+  const void *fn = kernel_of(P.variant);
+  if (!fn) return FPCODE_EINVAL;
+  const int smem = (int)((std::max<size_t>(16, P.table_bytes_per_set()) + 15) & ~(size_t)15);
+  if (smem > 48 * 1024) NA_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  int per_sm = 0, sms = 0;
+  NA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, fpk::kThreads, (size_t)smem));
+  NA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (per_sm < 1) return FPCODE_EINVAL;
+  const int ctas = sms * per_sm;
+  fph::plan_tasks(&P, ctas, 0);
+
+  // host image of the static part (starting at off_ctl)
+  std::vector<unsigned char> img(off_state - off_ctl, 0);
+  fpk::CtlStatic cs{};
+  cs.binom = reinterpret_cast<const fpenum::Binom *>(base);
+  cs.nslots = 1;
+  cs.serve = 0;
+  std::memcpy(&img[0], &cs, sizeof(cs));
+  fpk::SlotDesc sd{};
+  sd.p = P.p;
+  sd.n = P.n;
+  sd.k = P.k;
+  sd.r = P.r;
+  sd.W = P.W;
+  sd.rwpad = P.rwpad;
+  sd.m = P.m;
+  sd.npasses = (int)P.passes.size();
+  sd.variant = P.variant;
+  sd.per_round_check = P.opts.per_round_check;
+  sd.mid_pass_exit = P.opts.mid_pass_exit;
+  sd.complete = P.complete;
+  sd.table = reinterpret_cast<const uint32_t *>(base + off_table);
+  sd.passes = reinterpret_cast<const fpk::PassDesc *>(base + off_pass);
+  std::memcpy(&img[off_slot - off_ctl], &sd, sizeof(sd));
+  std::memcpy(&img[off_pass - off_ctl], P.passes.data(), P.passes.size() * sizeof(fpk::PassDesc));
+  std::memcpy(&img[off_table - off_ctl], P.table.data(), P.table.size() * sizeof(uint32_t));
+
+  NA_CUDA(cudaMemcpyAsync(base + off_ctl, img.data(), img.size(), cudaMemcpyHostToDevice, st));
+  NA_CUDA(cudaMemsetAsync(base + off_state, 0, dyn_bytes, st));  // state starts at zero
+  if (!P.passes.empty()) {
+    const fpk::SlotDesc *slots = reinterpret_cast<const fpk::SlotDesc *>(base + off_slot);
+    fpk::SlotState *states = reinterpret_cast<fpk::SlotState *>(base + off_state);
+    const fpk::CtlStatic *ctl = reinterpret_cast<const fpk::CtlStatic *>(base + off_ctl);
+    fpk::CtlDyn *dyn = reinterpret_cast<fpk::CtlDyn *>(base + off_state + dyn_bytes - sizeof(fpk::CtlDyn));
+    fpk::KParams kp{};
+    kp.wait_limit_ns = (unsigned long long)(o.wait_limit_s * 1e9);
+    kp.mid_pass = o.mid_pass_exit ? 1 : 0;
+    void *args[] = {(void *)&slots, (void *)&states, (void *)&ctl, (void *)&dyn, (void *)&kp};
+    NA_CUDA(cudaLaunchKernel(fn, dim3(ctas), dim3(fpk::kThreads), args, (size_t)smem, st));
+  }
+  fpk::SlotState state{};
+  NA_CUDA(cudaMemcpyAsync(&state, base + off_state, sizeof(state), cudaMemcpyDeviceToHost, st));
+  NA_CUDA(cudaStreamSynchronize(st));
+
+  fph::DeviceOutcome oc{};
+  oc.best_key = ~(uint64_t)state.best_key;
+  oc.enumerated = state.enumerated;
+  if (P.passes.empty()) {
+    oc.best_key = fpk::kNoKey;
+    oc.status = FPCODE_EBUDGET;
+    oc.stop_pass = -1;
+  } else if (state.finished) {
+    oc.status = state.status & 0xFF;
+    oc.stop_pass = state.stop_pass;
+  } else {
+    oc.status = -1;
+    oc.stop_pass = (int)(state.word >> 40) - 1;
+  }
+  fpcode_result res;
+  s = fph::decode_result(P, oc, &res, witness);
+  if (s) return s;
+  *d = res.d;
+  return FPCODE_OK;
+}
