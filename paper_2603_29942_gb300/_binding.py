@@ -414,3 +414,76 @@ def fpcode_prepared_bytes(prep: Prepared) -> tuple[int, int]:
     d2h = ctypes.c_uint64(0)
     _check(lib().fpcode_prepared_bytes(prep.handle, ctypes.byref(h2d), ctypes.byref(d2h)), "fpcode_prepared_bytes")
     return int(h2d.value), int(d2h.value)
+
+
+# --------------------------------------------------------------- serving ----
+
+def fpcode_serve_opts_default(**over) -> fpcode_serve_opts:
+    o = fpcode_serve_opts()
+    lib().fpcode_serve_opts_default(ctypes.byref(o))
+    for k, v in over.items():
+        if k == "search":
+            o.search = v
+        else:
+            setattr(o, k, v)
+    return o
+
+
+class Server:
+    """Owns an fpcode_server handle (fpcode_serve_*)."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+        self.ks: dict[int, int] = {}
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.fpcode_serve_destroy(self.handle)
+            self.handle = None
+
+
+def fpcode_serve_create(opts: fpcode_serve_opts | None = None, stream=None) -> Server:
+    h = _VP()
+    _check(lib().fpcode_serve_create(ctypes.byref(opts) if opts else None, _stream(stream), ctypes.byref(h)),
+           "fpcode_serve_create")
+    return Server(h.value)
+
+
+def fpcode_serve_submit(server: Server, code, budget: int = 0) -> int | None:
+    """Ticket, or None if the server is busy (no slot or memory free)."""
+    G = _matrix(code.G)
+    desc = fpcode_desc(int(code.p), int(code.n), int(code.k), 0, G.ctypes.data_as(_U8P), int(budget))
+    t = ctypes.c_uint64(0)
+    st = lib().fpcode_serve_submit(server.handle, ctypes.byref(desc), ctypes.byref(t))
+    if st == EBUSY:
+        return None
+    _check(st, "fpcode_serve_submit")
+    server.ks[int(t.value)] = int(code.k)
+    return int(t.value)
+
+
+def fpcode_serve_poll(server: Server, max_results: int = 256, want_witness: bool = True):
+    """List of (ticket, Result) for codes that finished since the last poll."""
+    res = (fpcode_result * max_results)()
+    tickets = (ctypes.c_uint64 * max_results)()
+    wit = np.zeros(max_results * MAX_N, dtype=np.uint8) if want_witness else None
+    n = ctypes.c_int(0)
+    _check(lib().fpcode_serve_poll(server.handle, res, tickets, wit.ctypes.data_as(_U8P) if want_witness else None,
+                                   max_results, ctypes.byref(n)), "fpcode_serve_poll")
+    out = []
+    for i in range(n.value):
+        t = int(tickets[i])
+        k = server.ks.pop(t, MAX_K)
+        w = wit[i * MAX_N:(i + 1) * MAX_N].copy() if want_witness else None
+        out.append((t, Result.of(res[i], k, w)))
+    return out
+
+
+def fpcode_serve_drain(server: Server, timeout_ms: int = 60000) -> None:
+    _check(lib().fpcode_serve_drain(server.handle, timeout_ms), "fpcode_serve_drain")
+
+
+def fpcode_serve_destroy(server: Server) -> None:
+    if server.handle:
+        lib().fpcode_serve_destroy(server.handle)
+        server.handle = None

@@ -18,6 +18,7 @@
 #include "fp_internal.h"
 #include "fp_kernel.cuh"
 #include "fp_kernels.h"
+#include "fp_driver.h"
 
 using fpk::CtlDyn;
 using fpk::CtlStatic;
@@ -26,7 +27,7 @@ using fpk::PassDesc;
 using fpk::SlotDesc;
 using fpk::SlotState;
 
-namespace {
+using fpd::DevCtx;
 
 #define FP_CUDA(call)                                                                           \
   do {                                                                                           \
@@ -37,21 +38,7 @@ namespace {
     }                                                                                            \
   } while (0)
 
-size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-
-// ---------------------------------------------------------------------------
-// Per-device context: SM count, the binomial table, the shared workspace.
-// ---------------------------------------------------------------------------
-struct DevCtx {
-  bool ready = false;
-  int sms = 0;
-  fpenum::Binom *binom = nullptr;  // device copy
-  std::mutex ws_mu;                // guards the workspace below
-  char *ws = nullptr;
-  size_t ws_bytes = 0;
-  char *ws_pinned = nullptr;
-  size_t ws_pinned_bytes = 0;
-};
+namespace fpd {
 
 std::mutex g_ctx_mu;
 DevCtx g_ctx[64];
@@ -129,6 +116,18 @@ KParams kparams(const fpcode_opts &o, int serve) {
   return kp;
 }
 
+}  // namespace fpd
+
+namespace {
+
+using fpd::get_ctx;
+using fpd::kernel_for;
+using fpd::kparams;
+using fpd::occupancy;
+using fpd::ws_reserve;
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
 // ---------------------------------------------------------------------------
 // Layout of a launch over several codes:
 //   static  [CtlStatic][SlotDesc x ns][PassDesc ...][tables ...]
@@ -205,7 +204,7 @@ fph::DeviceOutcome outcome_of(const SlotState &s, const CtlDyn &dyn) {
     o.stop_pass = s.stop_pass;
   } else {
     o.status = -1;  // timed out or a wait gave up
-    o.stop_pass = (int)(s.word >> 40) - 1;
+    o.stop_pass = (int)((s.word >> 40) & 0xFF) - 1;
   }
   (void)dyn;
   return o;

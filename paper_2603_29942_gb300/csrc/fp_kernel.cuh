@@ -34,8 +34,9 @@ namespace fpk {
 // Launch-wide constants (device memory, written by the host).
 struct CtlStatic {
   const fpenum::Binom *binom;
+  Completion *done_host;  // serving: host-mapped completion records (else null)
   int32_t nslots;
-  int32_t serve;  // serving: slots appear while the kernel runs
+  int32_t serve;          // serving: slots appear while the kernel runs
 };
 
 // Per-launch limits, passed by value.
@@ -71,6 +72,19 @@ __device__ __forceinline__ unsigned long long globaltimer() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
+}
+
+// Coherent (L2) copy of a descriptor: slots are rewritten by the host while
+// a serving kernel runs, so descriptors never come from L1.
+template <class T>
+__device__ __forceinline__ T load_cg(const T *p) {
+  static_assert(sizeof(T) % 16 == 0, "16-byte multiple");
+  T out;
+  const uint4 *src = reinterpret_cast<const uint4 *>(p);
+  uint4 *dst = reinterpret_cast<uint4 *>(&out);
+#pragma unroll
+  for (int i = 0; i < (int)(sizeof(T) / 16); ++i) dst[i] = __ldcg(src + i);
+  return out;
 }
 
 // The best key is stored inverted (~key) so that an all-zero state means
@@ -299,10 +313,13 @@ struct Multi357 {
 
 enum { kCmdRun = 0, kCmdWait = 1, kCmdExit = 2 };
 
-// Thread 0: claim the next task of any live code.
+// Thread 0: claim the next task of any live code.  On success the code's
+// descriptor and the pass descriptor are copied (coherently) to *o_sd, *o_pd.
 __device__ __forceinline__ int claim(const SlotDesc *slots, SlotState *states, const CtlStatic &cs,
-                                     const KParams &kp, CtlDyn *cd, int &rr, unsigned long long &wait_t0, unsigned long long t_start,
-                                     int *o_slot, int *o_pass, unsigned long long *o_task, int *o_U, int *o_skip) {
+                                     const KParams &kp, CtlDyn *cd, int &rr, unsigned long long &wait_t0,
+                                     unsigned long long t_start, int *o_slot, int *o_pass,
+                                     unsigned long long *o_task, int *o_U, int *o_skip, SlotDesc *o_sd,
+                                     PassDesc *o_pd) {
   const int nslots = cs.nslots;
   unsigned long long now = globaltimer();
   if (kp.timeout_ns && now - t_start > kp.timeout_ns) {
@@ -315,24 +332,40 @@ __device__ __forceinline__ int claim(const SlotDesc *slots, SlotState *states, c
     if (s >= nslots) s -= nslots;
     SlotState *st = &states[s];
     if (ld_vol(&st->finished)) continue;
-    const SlotDesc &sd = slots[s];
+    __threadfence();  // the descriptor was written before the state was reset
+    SlotDesc sd = load_cg(&slots[s]);
     if (sd.npasses <= 0) continue;
     live = true;
+    const unsigned long long gen = sd.seq & kGenMask;
     unsigned long long w = ld_vol(&st->word);
-    int P = (int)(w >> 40);
-    if (P >= sd.npasses || (w & kTaskMask) >= sd.passes[P].ntasks) continue;
+    if ((w >> kGenShift) != gen) continue;  // slot in transition between two codes
+    int P = (int)((w >> 40) & 0xFF);
+    if (P >= sd.npasses) continue;
+    PassDesc pd = load_cg(&sd.passes[P]);
+    if ((w & kTaskMask) >= pd.ntasks) continue;
     w = atomicAdd(&st->word, 1ull);
-    P = (int)(w >> 40);
-    unsigned long long t = w & kTaskMask;
-    if (P >= sd.npasses || t >= sd.passes[P].ntasks) continue;
+    const int P2 = (int)((w >> 40) & 0xFF);
+    const unsigned long long t = w & kTaskMask;
+    if ((w >> kGenShift) != gen) {
+      // the slot now holds a newer code; its descriptor was written before
+      // its state, so re-reading it gives the code this task belongs to
+      sd = load_cg(&slots[s]);
+      if ((sd.seq & kGenMask) != (w >> kGenShift)) continue;
+      P = -1;
+    }
+    if (P2 >= sd.npasses) continue;
+    if (P2 != P) pd = load_cg(&sd.passes[P2]);
+    if (t >= pd.ntasks) continue;
     uint64_t key = best_key(st);
     int U = key == kNoKey ? sd.n - sd.k + 2 : (int)key_weight(key);
     const int mid = kp.mid_pass < 0 ? sd.mid_pass_exit : kp.mid_pass;
-    *o_skip = (mid && U <= sd.passes[P].L_before) ? 1 : 0;
+    *o_skip = (mid && U <= pd.L_before) ? 1 : 0;
     *o_slot = s;
-    *o_pass = P;
+    *o_pass = P2;
     *o_task = t;
     *o_U = U;
+    *o_sd = sd;
+    *o_pd = pd;
     rr = s;
     wait_t0 = 0;
     return kCmdRun;
@@ -353,10 +386,10 @@ __device__ __forceinline__ int claim(const SlotDesc *slots, SlotState *states, c
 }
 
 // Thread 0: count a finished task; the last task of a pass decides.
-__device__ __forceinline__ void finish_task(const SlotDesc &sd, SlotState *st, int P) {
+__device__ __forceinline__ void finish_task(const CtlStatic &cs, const SlotDesc &sd, const PassDesc &pd,
+                                            SlotState *st, int slot, int P) {
   __threadfence();
   unsigned long long done = atomicAdd(&st->done, 1ull) + 1ull;
-  const PassDesc &pd = sd.passes[P];
   if (done != pd.ntasks) return;
   __threadfence();
   uint64_t key = ~(uint64_t)atomicOr(&st->best_key, 0ull);
@@ -364,15 +397,26 @@ __device__ __forceinline__ void finish_task(const SlotDesc &sd, SlotState *st, i
   const bool check = !sd.per_round_check || pd.round_end;
   const bool certified = check && pd.L_after >= U;
   if (certified || P + 1 >= sd.npasses) {
+    const int status = (certified || sd.complete) ? 0 : 4 /* FPCODE_EBUDGET */;
     st->stop_pass = P;
-    st->status = kDoneFlag | ((certified || sd.complete) ? 0 : 4 /* FPCODE_EBUDGET */);
+    st->status = kDoneFlag | status;
+    const unsigned long long enumerated = atomicAdd(&st->enumerated, 0ull);
     __threadfence();
     atomicExch(&st->finished, 1);
+    if (cs.done_host) {  // serving: post the outcome; the host may reuse the slot after seq
+      Completion *c = cs.done_host + slot;
+      c->best_key = key;
+      c->enumerated = enumerated;
+      c->status = status;
+      c->stop_pass = P;
+      __threadfence_system();
+      *(volatile unsigned long long *)&c->seq = sd.seq;
+    }
     return;
   }
   st->done = 0;
   __threadfence();
-  atomicExch(&st->word, (unsigned long long)(P + 1) << 40);
+  atomicExch(&st->word, ((sd.seq & kGenMask) << kGenShift) | ((unsigned long long)(P + 1) << 40));
 }
 
 template <class V>
@@ -381,8 +425,10 @@ __global__ void __launch_bounds__(kThreads) bz_kernel(const SlotDesc *__restrict
                                                       KParams kp) {
   extern __shared__ uint4 smem_raw[];
   uint32_t *tab = reinterpret_cast<uint32_t *>(smem_raw);
+  __shared__ SlotDesc s_sd;
+  __shared__ PassDesc s_pd;
   __shared__ int s_cmd, s_slot, s_pass, s_U, s_skip, s_stage;
-  __shared__ unsigned long long s_task, s_count;
+  __shared__ unsigned long long s_task, s_count, s_staged_seq;
   __shared__ int s_staged_slot, s_staged_j;
 
   const CtlStatic cs = *ctl;
@@ -393,24 +439,29 @@ __global__ void __launch_bounds__(kThreads) bz_kernel(const SlotDesc *__restrict
   if (tid == 0) {
     s_staged_slot = -1;
     s_staged_j = -1;
+    s_staged_seq = 0;
   }
   for (;;) {
     if (tid == 0) {
       int slot = 0, pass = 0, U = 0, skip = 0;
       unsigned long long task = 0;
-      int cmd = claim(slots, states, cs, kp, cdyn, rr, wait_t0, t_start, &slot, &pass, &task, &U, &skip);
+      SlotDesc sd;
+      PassDesc pd;
+      int cmd = claim(slots, states, cs, kp, cdyn, rr, wait_t0, t_start, &slot, &pass, &task, &U, &skip, &sd, &pd);
       s_cmd = cmd;
       if (cmd == kCmdRun) {
+        s_sd = sd;
+        s_pd = pd;
         s_slot = slot;
         s_pass = pass;
         s_task = task;
         s_U = U;
         s_skip = skip;
-        const int j = slots[slot].passes[pass].j;
-        s_stage = (!skip && (slot != s_staged_slot || j != s_staged_j)) ? 1 : 0;
+        s_stage = (!skip && (slot != s_staged_slot || pd.j != s_staged_j || sd.seq != s_staged_seq)) ? 1 : 0;
         if (s_stage) {
           s_staged_slot = slot;
-          s_staged_j = j;
+          s_staged_j = pd.j;
+          s_staged_seq = sd.seq;
         }
       }
       s_count = 0;
@@ -423,23 +474,21 @@ __global__ void __launch_bounds__(kThreads) bz_kernel(const SlotDesc *__restrict
       continue;
     }
     const int slot = s_slot, pass = s_pass;
-    const SlotDesc &sd = slots[slot];
-    const PassDesc pd = sd.passes[pass];
     if (s_stage) {
-      const int words = sd.k * (sd.p - 1) * sd.rwpad;
-      const uint4 *src = reinterpret_cast<const uint4 *>(sd.table + (size_t)pd.j * (size_t)words);
-      for (int i = tid; i < words / 4; i += kThreads) smem_raw[i] = src[i];
+      const int words = s_sd.k * (s_sd.p - 1) * s_sd.rwpad;
+      const uint4 *src = reinterpret_cast<const uint4 *>(s_sd.table + (size_t)s_pd.j * (size_t)words);
+      for (int i = tid; i < words / 4; i += kThreads) smem_raw[i] = __ldcg(src + i);
       __syncthreads();
     }
     unsigned long long count = 0;
-    if (!s_skip) V::run(sd, pd, pass, tab, *cs.binom, s_task, s_U, &states[slot], count);
+    if (!s_skip) V::run(s_sd, s_pd, pass, tab, *cs.binom, s_task, s_U, &states[slot], count);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) count += __shfl_xor_sync(0xffffffffu, count, o);
     if ((tid & 31) == 0 && count) atomicAdd(&s_count, count);
     __syncthreads();
     if (tid == 0) {
       if (s_count) atomicAdd(&states[slot].enumerated, s_count);
-      finish_task(sd, &states[slot], pass);
+      finish_task(cs, s_sd, s_pd, &states[slot], slot, pass);
     }
   }
 }

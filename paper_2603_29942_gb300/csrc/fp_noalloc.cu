@@ -174,7 +174,7 @@ extern "C" int fpcode_min_distance_noalloc(int p, int n, int k, const uint8_t *G
     oc.stop_pass = state.stop_pass;
   } else {
     oc.status = -1;
-    oc.stop_pass = (int)(state.word >> 40) - 1;
+    oc.stop_pass = (int)((state.word >> 40) & 0xFF) - 1;
   }
   fpcode_result res;
   s = fph::decode_result(P, oc, &res, witness);

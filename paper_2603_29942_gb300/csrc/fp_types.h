@@ -46,7 +46,9 @@ struct PassDesc {
   uint64_t nprefix;   // prefixes (g >= 2) or rows (g == 1)
   uint64_t size;      // codewords in the pass: C(k,g)(p-1)^(g-1)
   uint64_t NC;        // (p-1)^(g-2) coefficient vectors per prefix subset
+  uint64_t pad2;      // 64 bytes: read with 16-byte coherent loads
 };
+static_assert(sizeof(PassDesc) == 64, "PassDesc layout");
 
 // Static description of one code as the kernel sees it.
 struct SlotDesc {
@@ -58,11 +60,14 @@ struct SlotDesc {
   int32_t complete;              // 1: the schedule runs to the last level
   const uint32_t *table;         // m * k * (p-1) * rwpad words, device
   const PassDesc *passes;        // npasses entries, device
+  uint64_t seq;                  // serving: ticket of the code in this slot
+  uint64_t pad;
 };
+static_assert(sizeof(SlotDesc) == 80, "SlotDesc layout");
 
 // Dynamic state of one code, device memory.
 struct SlotState {
-  unsigned long long word;        // (pass << 40) | next task
+  unsigned long long word;        // (generation << 48) | (pass << 40) | next task
   unsigned long long done;        // tasks finished in the current pass
   unsigned long long best_key;    // packed witness key (kNoKey: none yet)
   unsigned long long enumerated;  // codewords evaluated
@@ -72,18 +77,21 @@ struct SlotState {
   int32_t pad;
 };
 
-constexpr int32_t kRunning = -1;
-constexpr uint64_t kTaskMask = (1ull << 40) - 1;
-
-// Launch-wide control block (device memory).
-struct Ctl {
-  unsigned long long wait_limit_ns;  // longest single wait for a pass hand-off
-  unsigned long long deadline_ns;    // 0: none; else %globaltimer deadline
-  int32_t nslots;
-  int32_t err;                       // set when a wait gave up
-  int32_t serve;                     // serving mode: slots appear while running
-  int32_t pad;
-  unsigned long long idle_limit_ns;  // serving: exit after this long idle
+// Serving: the finaliser of a code posts its outcome to host-mapped memory
+// (seq written last, after a system-scope fence).
+struct Completion {
+  unsigned long long seq;
+  unsigned long long best_key;   // packed key (kNoKey: none)
+  unsigned long long enumerated;
+  int32_t status;                // fpcode status
+  int32_t stop_pass;
 };
+
+constexpr int32_t kRunning = -1;
+// SlotState.word = (generation << 48) | (pass << 40) | next task; the
+// generation is the low 16 bits of SlotDesc.seq (0 outside serving).
+constexpr uint64_t kTaskMask = (1ull << 40) - 1;
+constexpr int kGenShift = 48;
+constexpr uint64_t kGenMask = 0xFFFFull;
 
 }  // namespace fpk

@@ -1,0 +1,107 @@
+"""Serving on the GPU: continuous batching over the persistent kernel.
+
+Each result is the same alone and in the mix: codes submitted while others
+run (and into slots that earlier codes have left) give exactly the status,
+d, [L, U] and per-level counts of the same code searched on its own, and a
+valid witness.  Admission by device memory: a server with a tiny table
+arena turns requests away (EBUSY) until earlier codes finish.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import gf
+from paper_2603_29942_gb300 import _binding as B
+from paper_2603_29942_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for -m gpu tests")
+    B.lib()
+
+
+def _alone(code, budget):
+    pr = B.fpcode_prepare(code.p, code.n, code.k, code.G, B.fpcode_opts_default(budget=budget))
+    return B.fpcode_min_distance_ex(pr)
+
+
+def _check(code, r, ref):
+    assert (r.status, r.d, r.L, r.U, r.counts[:code.k + 1]) == (ref.status, ref.d, ref.L, ref.U, ref.counts)
+    if r.status == B.OK:
+        w = [int(x) for x in r.witness[:code.n]]
+        assert gf.weight(w) == r.d
+        for h in gf.null_space(code.G.tolist(), code.p):
+            assert sum(a * b for a, b in zip(h, w)) % code.p == 0
+
+
+def test_serve_alone_equals_mix():
+    codes, _ = inputs.serve_codes(count=120)
+    budget = 2 * 10 ** 6
+    srv = B.fpcode_serve_create(B.fpcode_serve_opts_default(slots=16))
+    pending = list(range(len(codes)))
+    tickets = {}
+    results = {}
+    t0 = time.time()
+    while (pending or len(results) < len(codes)) and time.time() - t0 < 120:
+        while pending:
+            i = pending[0]
+            t = B.fpcode_serve_submit(srv, codes[i], budget=budget)
+            if t is None:
+                break
+            tickets[t] = i
+            pending.pop(0)
+        for t, r in B.fpcode_serve_poll(srv):
+            results[tickets[t]] = r
+    B.fpcode_serve_drain(srv)
+    for t, r in B.fpcode_serve_poll(srv):
+        results[tickets[t]] = r
+    assert len(results) == len(codes)
+    for i, c in enumerate(codes):
+        _check(c, results[i], _alone(c, budget))
+    B.fpcode_serve_destroy(srv)
+
+
+def test_serve_admission_by_memory():
+    """With room for about one code's tables, later requests wait (EBUSY)
+    and are admitted once earlier codes finish."""
+    codes = [inputs.single_code(40 + i, 7, 40, 20) for i in range(4)]
+    tb = 2 * 20 * 6 * 4 * 4  # bytes of one code's bit-sliced multiples
+    srv = B.fpcode_serve_create(B.fpcode_serve_opts_default(slots=8, device_bytes=tb + 256))
+    first = B.fpcode_serve_submit(srv, codes[0], budget=10 ** 5)
+    assert first is not None
+    assert B.fpcode_serve_submit(srv, codes[1], budget=10 ** 5) is None  # busy: no memory
+    done = {}
+    for i in range(1, 4):
+        t = None
+        t0 = time.time()
+        while t is None and time.time() - t0 < 30:
+            for tk, r in B.fpcode_serve_poll(srv):
+                done[tk] = r
+            t = B.fpcode_serve_submit(srv, codes[i], budget=10 ** 5)
+        assert t is not None
+    B.fpcode_serve_drain(srv)
+    for tk, r in B.fpcode_serve_poll(srv):
+        done[tk] = r
+    assert len(done) == 4
+    for r in done.values():
+        assert r.status in (B.OK, B.EBUDGET)
+    B.fpcode_serve_destroy(srv)
+
+
+def test_serve_relaunch_after_idle():
+    """The kernel exits after its idle period; a later request relaunches it."""
+    srv = B.fpcode_serve_create(B.fpcode_serve_opts_default(slots=4, idle_exit_s=0.005))
+    code = inputs.single("f3_n30_k15")
+    for _ in range(3):
+        t = B.fpcode_serve_submit(srv, code)
+        B.fpcode_serve_drain(srv)
+        out = dict(B.fpcode_serve_poll(srv))
+        assert out[t].status == B.OK and out[t].d == 6
+        time.sleep(0.05)  # longer than the idle period: the kernel has exited
+    B.fpcode_serve_destroy(srv)
