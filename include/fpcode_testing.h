@@ -57,6 +57,15 @@ int fpcode_prepared_shape(const fpcode_prepared *prep, int *m, int *kj, int *npa
 /* Gamma_j (k x n) and its pivot columns (k). */
 int fpcode_prepared_gamma(const fpcode_prepared *prep, int j, uint8_t *gamma, int *pivots);
 int fpcode_prepared_passes(const fpcode_prepared *prep, fpcode_pass_info *passes, int max);
+/* The CTA task ranges [lo, hi) of pass `pass` when planned for `ctas` CTAs
+ * (fixed_pl > 0: fixed tasks of 256 * fixed_pl prefixes; 0: guided).
+ * Returns the number of tasks (at most max written). */
+int fpcode_test_task_ranges(fpcode_prepared *prep, int pass, int ctas, int fixed_pl, uint64_t *lo, uint64_t *hi,
+                            int max);
+/* Microseconds from the start of the last search on `prep` to the end of
+ * each of its passes (-1: not reached), for up to max passes.  Returns the
+ * number of passes written, or -1. */
+int fpcode_test_pass_times(fpcode_prepared *prep, void *stream, double *us, int max);
 /* Bytes one search moves: host-to-device (tables, schedule, descriptors)
  * and device-to-host (final state). */
 int fpcode_prepared_bytes(const fpcode_prepared *prep, uint64_t *h2d, uint64_t *d2h);

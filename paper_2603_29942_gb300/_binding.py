@@ -145,6 +145,10 @@ def _declare(lib):
         "fpcode_prepared_shape": (ctypes.c_int, [_VP, _IP, _IP, _IP, _IP]),
         "fpcode_prepared_gamma": (ctypes.c_int, [_VP, ctypes.c_int, _U8P, _IP]),
         "fpcode_prepared_passes": (ctypes.c_int, [_VP, ctypes.POINTER(fpcode_pass_info), ctypes.c_int]),
+        "fpcode_test_task_ranges": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                   ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                                   ctypes.c_int]),
+        "fpcode_test_pass_times": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
         "fpcode_prepared_bytes": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
     }
     found = []
@@ -487,3 +491,22 @@ def fpcode_serve_destroy(server: Server) -> None:
     if server.handle:
         lib().fpcode_serve_destroy(server.handle)
         server.handle = None
+
+
+def fpcode_test_task_ranges(prep: Prepared, pass_index: int, ctas: int, fixed_pl: int = 0):
+    cap = 1 << 16
+    lo = (ctypes.c_uint64 * cap)()
+    hi = (ctypes.c_uint64 * cap)()
+    n = lib().fpcode_test_task_ranges(prep.handle, pass_index, ctas, fixed_pl, lo, hi, cap)
+    if n < 0:
+        raise FpcodeError(EINVAL, "fpcode_test_task_ranges")
+    return [(int(lo[i]), int(hi[i])) for i in range(min(n, cap))]
+
+
+def fpcode_test_pass_times(prep: Prepared, stream=None) -> list[float]:
+    """Microseconds from the last search's start to the end of each pass."""
+    us = (ctypes.c_double * 256)()
+    n = lib().fpcode_test_pass_times(prep.handle, _stream(stream), us, 256)
+    if n < 0:
+        raise FpcodeError(EINVAL, "fpcode_test_pass_times")
+    return [us[i] for i in range(n)]

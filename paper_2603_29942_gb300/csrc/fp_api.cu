@@ -135,7 +135,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // ---------------------------------------------------------------------------
 struct Layout {
   size_t off_ctl = 0, off_slots = 0, off_passes = 0, off_tables = 0, static_bytes = 0;
-  size_t off_states = 0, dyn_bytes = 0, total = 0;
+  size_t off_states = 0, dyn_bytes = 0, off_times = 0, total = 0;
   std::vector<size_t> pass_off, table_off;
 };
 
@@ -160,7 +160,8 @@ Layout make_layout(const std::vector<const fph::Prepared *> &codes) {
   L.static_bytes = o;
   L.off_states = o;
   L.dyn_bytes = align256(ns * sizeof(SlotState) + sizeof(CtlDyn));
-  L.total = o + L.dyn_bytes;
+  L.off_times = o + L.dyn_bytes;  // per-pass end times of a single code (diagnostics)
+  L.total = L.off_times + (fpk::kMaxPasses + 1) * sizeof(unsigned long long);
   return L;
 }
 
@@ -221,10 +222,12 @@ int launch(const void *fn, int ctas, int smem, cudaStream_t st, char *d, const L
   return FPCODE_OK;
 }
 
+// Dynamic shared memory of a launch: binomial columns + the largest table
+// of one information set.
 int smem_for(const std::vector<const fph::Prepared *> &codes) {
   size_t s = 16;
   for (auto *P : codes) s = std::max(s, P->table_bytes_per_set());
-  return (int)((s + 15) & ~(size_t)15);
+  return (int)(((s + 15) & ~(size_t)15) + fpk::kBinomBytes);
 }
 
 // Upload one prepared code into device buffer `d` (static_bytes) via pinned
@@ -251,6 +254,8 @@ int upload_one(fpcode_prepared *prep, cudaStream_t st, DevCtx &c, char *d, char 
   prep->dyn_bytes = L.dyn_bytes;
   prep->dev_bytes = L.total;
   fill_static(L, {&P}, c, h, d, 0);
+  SlotDesc *sd = reinterpret_cast<SlotDesc *>(h + L.off_slots);
+  sd->pass_times = reinterpret_cast<unsigned long long *>(d + L.off_times);
   FP_CUDA(cudaMemcpyAsync(d, h, L.static_bytes, cudaMemcpyHostToDevice, st));
   return FPCODE_OK;
 }
@@ -601,6 +606,18 @@ __global__ void intpeak_kernel(uint32_t *sink, long long *cycles, int iters, uin
 }  // namespace
 
 extern "C" {
+
+int fpcode_test_pass_times(fpcode_prepared *prep, void *stream, double *us, int max) {
+  if (!prep || !prep->uploaded || !us) return -1;
+  Layout L = make_layout({&prep->host});
+  std::vector<unsigned long long> t(fpk::kMaxPasses + 1);
+  FP_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  FP_CUDA(cudaMemcpy(t.data(), prep->dev + L.off_times, t.size() * sizeof(unsigned long long),
+                     cudaMemcpyDeviceToHost));
+  const int n = std::min<int>(max, (int)prep->host.passes.size());
+  for (int i = 0; i < n; ++i) us[i] = t[i] >= t[fpk::kMaxPasses] ? (double)(t[i] - t[fpk::kMaxPasses]) * 1e-3 : -1.0;
+  return n;
+}
 
 int fpcode_prepared_bytes(const fpcode_prepared *prep, uint64_t *h2d, uint64_t *d2h) {
   if (!prep) return FPCODE_EINVAL;

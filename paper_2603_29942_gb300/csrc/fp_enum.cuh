@@ -39,9 +39,17 @@ namespace fpenum {
 
 constexpr int kMaxK = 64;
 
-// Binomial table C(n, t), 0 <= t <= n <= 64 (C(64,32) < 2^63).
+// Binomial table C(n, t), 0 <= t <= n <= 64 (C(64,32) < 2^63).  The
+// enumeration functions take any accessor B with B(n, t) = C(n, t).
 struct Binom {
   uint64_t c[kMaxK + 1][kMaxK + 1];
+  FP_HD uint64_t operator()(int n, int t) const { return c[n][t]; }
+};
+
+// Columns t < T of the table, stored t-major (shared memory on the GPU).
+struct BinomCols {
+  const uint64_t *p;  // p[t * (kMaxK + 1) + n]
+  FP_HD uint64_t operator()(int n, int t) const { return p[t * (kMaxK + 1) + n]; }
 };
 
 inline void fill_binom(Binom *b) {
@@ -72,17 +80,18 @@ FP_HD int popc64(uint64_t x) {
 FP_HD uint64_t low_mask(int n) { return n >= 64 ? ~0ull : ((1ull << n) - 1ull); }
 
 // Subset of rank r in R(n, t), as a bit mask over {0..n-1}.
-FP_HD uint64_t rd_unrank(const Binom &B, uint64_t r, int n, int t) {
+template <class BT>
+FP_HD uint64_t rd_unrank(const BT &B, uint64_t r, int n, int t) {
   uint64_t mask = 0;
   while (t > 0) {
     if (t == n) {
       mask |= low_mask(n);
       break;
     }
-    uint64_t c = B.c[n - 1][t];
+    uint64_t c = B(n - 1, t);
     if (r >= c) {  // n-1 is in the subset; the tail part is reversed
       mask |= 1ull << (n - 1);
-      r = B.c[n][t] - 1 - r;
+      r = B(n, t) - 1 - r;
       --t;
     }
     --n;
@@ -91,7 +100,8 @@ FP_HD uint64_t rd_unrank(const Binom &B, uint64_t r, int n, int t) {
 }
 
 // Rank of subset T (|T| = t) in R(n, t).
-FP_HD uint64_t rd_rank(const Binom &B, uint64_t T, int n, int t) {
+template <class BT>
+FP_HD uint64_t rd_rank(const BT &B, uint64_t T, int n, int t) {
   // Walk from the top; each member n-1 reflects the rank of the rest.
   int flip = 0;  // parity of reflections so far
   uint64_t off = 0;
@@ -99,7 +109,7 @@ FP_HD uint64_t rd_rank(const Binom &B, uint64_t T, int n, int t) {
   // unrolled as an affine map r = off + (flip ? -1 : 1) * r_rest
   while (t > 0 && t < n) {
     if (T >> (n - 1) & 1ull) {
-      uint64_t base = B.c[n][t] - 1;
+      uint64_t base = B(n, t) - 1;
       // r = base - r_rest, composed with the current map
       if (!flip) off = off + base; else off = off - base;
       flip ^= 1;
@@ -207,7 +217,8 @@ FP_HD uint64_t ipow(uint64_t b, int e) {
 
 // Number of prefixes of pass g >= 2 whose largest row is below m:
 // sum_{m' < m} C(m', g-2) NC = C(m, g-1) NC, NC = (p-1)^(g-2).
-FP_HD uint64_t prefixes_below(const Binom &B, int m, int g, uint64_t NC) { return B.c[m][g - 1] * NC; }
+template <class BT>
+FP_HD uint64_t prefixes_below(const BT &B, int m, int g, uint64_t NC) { return B(m, g - 1) * NC; }
 
 struct Prefix {
   int m;        // largest row of the prefix (coefficient 1)
@@ -216,8 +227,8 @@ struct Prefix {
   uint64_t d;   // counter digits of the coefficient vector of Q (slot order)
 };
 
-template <int DB>
-FP_HD Prefix prefix_unrank(const Binom &B, uint64_t I, int k, int g, int b) {
+template <int DB, class BT>
+FP_HD Prefix prefix_unrank(const BT &B, uint64_t I, int k, int g, int b) {
   const int L = g - 2;
   const uint64_t NC = ipow((uint64_t)b, L);
   // largest m in [g-2, k-2] with C(m, g-1) NC <= I (binary search)
@@ -241,8 +252,8 @@ FP_HD Prefix prefix_unrank(const Binom &B, uint64_t I, int k, int g, int b) {
 // of subsets C(m, g-2).  Returns the slot whose coefficient changed (by
 // *dir = +1 or -1), or -1 if Q or m changed and the prefix sum must be
 // rebuilt (all coefficients back to 1).
-template <int DB>
-FP_HD int prefix_advance(const Binom &B, Prefix &pf, uint64_t &ci, uint64_t &nq, uint64_t NC, int b, int L,
+template <int DB, class BT>
+FP_HD int prefix_advance(const BT &B, Prefix &pf, uint64_t &ci, uint64_t &nq, uint64_t NC, int b, int L,
                          int *dir) {
   if (ci + 1 < NC) {
     int s = gray_step<DB>(&pf.d, b, L, dir);
@@ -261,7 +272,7 @@ FP_HD int prefix_advance(const Binom &B, Prefix &pf, uint64_t &ci, uint64_t &nq,
     ++pf.m;
     pf.qi = 0;
     pf.Q = low_mask(L);
-    nq = B.c[pf.m][L];
+    nq = B(pf.m, L);
   }
   return -1;
 }

@@ -103,14 +103,19 @@ uint64_t pass_size(int p, int k, int g) {
   return c;
 }
 
+}  // namespace
+
+int digit_bits_of(int p) { return p == 3 ? 1 : (p == 5 || p == 7) ? 4 : 8; }
+
+namespace {
+
 int lower_bound(const std::vector<int> &e, const std::vector<int> &kj, int k) {
   int L = 0;
   for (size_t i = 0; i < e.size(); ++i) L += std::max(0, e[i] + 1 - (k - kj[i]));
   return L;
 }
 
-// Digit width of the coefficient counters the kernel uses for this prime.
-int digit_bits(int p) { return (p == 3 || p == 5 || p == 7) ? 4 : 8; }
+int digit_bits(int p) { return digit_bits_of(p); }
 
 }  // namespace
 
@@ -184,20 +189,36 @@ int prepare(int p, int n, int k, const uint8_t *G, const fpcode_opts &opts, Prep
   }
   P->m = (int)P->kj.size();
 
-  // --- bit-sliced multiples v * A_j[t] of the non-pivot part ---
-  const int m = P->m, nk = n - k, R = P->r, RWP = P->rwpad;
-  P->table.assign((size_t)m * k * (p - 1) * RWP, 0u);
+  // --- bit-sliced multiples v * A_j[t] of the non-pivot part, then the
+  //     pair signatures (Mersenne p) ---
+  const int m = P->m, nk = n - k, R = P->r, RWP = P->rwpad, W = P->W;
+  const int SIG = fpk::sig_words(p, R, W);
+  const size_t set_words = (size_t)k * ((size_t)(p - 1) * RWP + SIG);
+  P->table.assign((size_t)m * set_words, 0u);
   for (int j = 0; j < m; ++j)
     for (int t = 0; t < k; ++t) {
       const uint8_t *row = &P->gam[((size_t)j * k + t) * n];
       const int *red = &P->red[(size_t)j * nk];
       for (int v = 1; v < p; ++v) {
-        uint32_t *e = &P->table[(((size_t)j * k + t) * (p - 1) + (v - 1)) * RWP];
+        uint32_t *e = &P->table[(size_t)j * set_words + ((size_t)t * (p - 1) + (v - 1)) * RWP];
         for (int q = 0; q < nk; ++q) {
           const int y = (v * row[red[q]]) % p;
           const int w = q >> 5, bit = q & 31;
           for (int i = 0; i < R; ++i)
             if ((y >> i) & 1) e[w * R + i] |= 1u << bit;
+        }
+      }
+      if (SIG) {
+        uint32_t *sg = &P->table[(size_t)j * set_words + (size_t)k * (p - 1) * RWP + (size_t)t * SIG];
+        const int npair = (p - 1) / 2;
+        for (int pq = 0; pq < npair; ++pq) {
+          const int c = fpk::pair_rep(p, pq);
+          for (int q = 0; q < nk; ++q) {
+            const int y = (c * row[red[q]]) % p;
+            const int w = q >> 5, bit = q & 31;
+            for (int i = 0; i + 1 < R; ++i)
+              if (((y >> i) ^ (y >> (i + 1))) & 1) sg[(pq * W + w) * (R - 1) + i] |= 1u << bit;
+          }
         }
       }
     }
@@ -251,25 +272,43 @@ int prepare(int p, int n, int k, const uint8_t *G, const fpcode_opts &opts, Prep
 }
 
 void plan_tasks(Prepared *P, int ctas, int fixed_pl) {
-  const uint64_t per_task_lanes = (uint64_t)fpk::kThreads;
+  const uint64_t lanes = (uint64_t)fpk::kThreads;
+  const uint64_t C = (uint64_t)std::max(1, ctas);
+  const uint64_t b = (uint64_t)(P->p - 1);
   for (auto &d : P->passes) {
+    d.phases = 0;
+    d.plan_ctas = (uint32_t)C;
+    d.unit = 1;
     if (d.g == 1) {
       d.pl = 1;
       d.ntasks = 1;
       continue;
     }
-    int pl;
     if (fixed_pl > 0) {
-      pl = std::min(fixed_pl, 64);
-    } else {
-      // about four tasks per CTA, at most 64 prefixes per lane
-      const uint64_t want = (uint64_t)std::max(1, ctas) * 4ull * per_task_lanes;
-      uint64_t q = (d.nprefix + want - 1) / want;
-      pl = (int)std::min<uint64_t>(std::max<uint64_t>(q, 1), 64);
+      d.pl = std::min(fixed_pl, 64);
+      const uint64_t per_task = lanes * (uint64_t)d.pl;
+      d.ntasks = (uint32_t)((d.nprefix + per_task - 1) / per_task);
+      continue;
     }
-    d.pl = pl;
-    const uint64_t per_task = per_task_lanes * (uint64_t)pl;
-    d.ntasks = (uint32_t)((d.nprefix + per_task - 1) / per_task);
+    d.pl = 0;
+    // unit b^t: as many whole low digits as keep two units per lane of the grid
+    uint64_t unit = 1;
+    for (int t = 0; t < d.g - 2; ++t) {
+      if (unit * b > 256 || d.nprefix / (unit * b) < 2 * lanes * C) break;
+      unit *= b;
+    }
+    d.unit = (uint32_t)unit;
+    const uint64_t N = d.nprefix / unit;
+    if (N <= 2 * lanes * C) {  // small pass: one unit per lane
+      d.ntasks = (uint32_t)((N + lanes - 1) / lanes);
+      continue;
+    }
+    // guided: phase h has C tasks over half of what is left, until a task of
+    // the last phase holds about one unit per lane
+    uint32_t H = 1;
+    while (H < 12 && (N >> H) / C >= lanes) ++H;
+    d.phases = H;
+    d.ntasks = (uint32_t)(H * C);
   }
 }
 
@@ -290,15 +329,19 @@ bool key_coefficients(const Prepared &P, uint64_t key, int *g_out, int *j_out, s
     const uint64_t I = fpk::key_prefix(key);
     if (I >= d.nprefix) return false;
     const int L = d.g - 2, b = P.p - 1;
-    fpenum::Prefix pf = digit_bits(P.p) == 4 ? fpenum::prefix_unrank<4>(binom(), I, P.k, d.g, b)
-                                               : fpenum::prefix_unrank<8>(binom(), I, P.k, d.g, b);
+    const int DB = digit_bits(P.p);
+    fpenum::Prefix pf = DB == 1   ? fpenum::prefix_unrank<1>(binom(), I, P.k, d.g, b)
+                        : DB == 4 ? fpenum::prefix_unrank<4>(binom(), I, P.k, d.g, b)
+                                  : fpenum::prefix_unrank<8>(binom(), I, P.k, d.g, b);
     if (pf.m >= x) return false;
     coef[pf.m] = 1;
     uint64_t Q = pf.Q;
     for (int s = 0; s < L; ++s) {
       const int q = fpenum::ctz64(Q);
       Q &= Q - 1;
-      coef[q] = (digit_bits(P.p) == 4 ? fpenum::gray_digit<4>(pf.d, s, b, L) : fpenum::gray_digit<8>(pf.d, s, b, L)) + 1;
+      coef[q] = (DB == 1   ? fpenum::gray_digit<1>(pf.d, s, b, L)
+                 : DB == 4 ? fpenum::gray_digit<4>(pf.d, s, b, L)
+                           : fpenum::gray_digit<8>(pf.d, s, b, L)) + 1;
     }
     coef[x] = c;
   }
@@ -428,39 +471,70 @@ int fpcode_test_rd_next(uint64_t subset, int n, int t, uint64_t *next) {
   return fpenum::rd_next(subset, n, t, next, &rm, &ad) ? 1 : 0;
 }
 
-static int prefix_out(const fpenum::Prefix &pf, int g, int p, int *m, uint64_t *Q, int *coefs) {
+extern "C++" {
+namespace {
+template <int DB>
+int prefix_out(const fpenum::Prefix &pf, int g, int p, int *m, uint64_t *Q, int *coefs) {
   *m = pf.m;
   *Q = pf.Q;
   const int L = g - 2, b = p - 1;
-  for (int s = 0; s < L; ++s)
-    coefs[s] = ((p == 3 || p == 5 || p == 7) ? fpenum::gray_digit<4>(pf.d, s, b, L)
-                                              : fpenum::gray_digit<8>(pf.d, s, b, L)) + 1;
+  for (int s = 0; s < L; ++s) coefs[s] = fpenum::gray_digit<DB>(pf.d, s, b, L) + 1;
   return FPCODE_OK;
 }
 
+template <int DB>
+int prefix_walk(uint64_t I, uint64_t steps, int k, int g, int p, int *m, uint64_t *Q, int *coefs) {
+  const fpenum::Binom &B = fph::binom();
+  const int L = g - 2, b = p - 1;
+  const uint64_t NC = fpenum::ipow((uint64_t)b, L);
+  fpenum::Prefix pf = fpenum::prefix_unrank<DB>(B, I, k, g, b);
+  uint64_t ci = (I - fpenum::prefixes_below(B, pf.m, g, NC)) - pf.qi * NC;
+  uint64_t nq = B(pf.m, L);
+  for (uint64_t s = 0; s < steps; ++s) {
+    int dir;
+    fpenum::prefix_advance<DB>(B, pf, ci, nq, NC, b, L, &dir);
+  }
+  return prefix_out<DB>(pf, g, p, m, Q, coefs);
+}
+}  // namespace
+}  // extern "C++"
+
 int fpcode_test_prefix_unrank(uint64_t I, int k, int g, int p, int *m, uint64_t *Q, int *coefs) {
   if (g < 2 || g > k || k > 64 || !fph::is_odd_prime(p)) return FPCODE_EINVAL;
-  const bool small = p == 3 || p == 5 || p == 7;
-  fpenum::Prefix pf = small ? fpenum::prefix_unrank<4>(fph::binom(), I, k, g, p - 1)
-                            : fpenum::prefix_unrank<8>(fph::binom(), I, k, g, p - 1);
-  return prefix_out(pf, g, p, m, Q, coefs);
+  switch (fph::digit_bits_of(p)) {
+    case 1: return prefix_out<1>(fpenum::prefix_unrank<1>(fph::binom(), I, k, g, p - 1), g, p, m, Q, coefs);
+    case 4: return prefix_out<4>(fpenum::prefix_unrank<4>(fph::binom(), I, k, g, p - 1), g, p, m, Q, coefs);
+    default: return prefix_out<8>(fpenum::prefix_unrank<8>(fph::binom(), I, k, g, p - 1), g, p, m, Q, coefs);
+  }
 }
 
 int fpcode_test_prefix_walk(uint64_t I, uint64_t steps, int k, int g, int p, int *m, uint64_t *Q, int *coefs) {
   if (g < 2 || g > k || k > 64 || !fph::is_odd_prime(p)) return FPCODE_EINVAL;
-  const fpenum::Binom &B = fph::binom();
-  const int L = g - 2, b = p - 1;
-  const uint64_t NC = fpenum::ipow((uint64_t)b, L);
-  const bool small = p == 3 || p == 5 || p == 7;
-  fpenum::Prefix pf = small ? fpenum::prefix_unrank<4>(B, I, k, g, b) : fpenum::prefix_unrank<8>(B, I, k, g, b);
-  uint64_t ci = (I - fpenum::prefixes_below(B, pf.m, g, NC)) - pf.qi * NC;
-  uint64_t nq = B.c[pf.m][L];
-  for (uint64_t s = 0; s < steps; ++s) {
-    int dir;
-    if (small) fpenum::prefix_advance<4>(B, pf, ci, nq, NC, b, L, &dir);
-    else fpenum::prefix_advance<8>(B, pf, ci, nq, NC, b, L, &dir);
+  switch (fph::digit_bits_of(p)) {
+    case 1: return prefix_walk<1>(I, steps, k, g, p, m, Q, coefs);
+    case 4: return prefix_walk<4>(I, steps, k, g, p, m, Q, coefs);
+    default: return prefix_walk<8>(I, steps, k, g, p, m, Q, coefs);
   }
-  return prefix_out(pf, g, p, m, Q, coefs);
+}
+
+int fpcode_test_task_ranges(fpcode_prepared *prep, int pass, int ctas, int fixed_pl, uint64_t *lo, uint64_t *hi,
+                            int max) {
+  if (!prep || pass < 0 || pass >= (int)prep->host.passes.size() || !lo || !hi) return -1;
+  fph::plan_tasks(&prep->host, ctas, fixed_pl);
+  const fpk::PassDesc &d = prep->host.passes[pass];
+  const int n = (int)std::min<uint64_t>(d.ntasks, (uint64_t)max);
+  for (int t = 0; t < n; ++t) {
+    if (d.g == 1) {
+      lo[t] = 0;
+      hi[t] = d.nprefix;
+    } else {
+      fpk::task_range(d, (uint64_t)t, &lo[t], &hi[t]);
+      lo[t] *= d.unit;
+      hi[t] *= d.unit;
+      if (hi[t] > d.nprefix) hi[t] = d.nprefix;
+    }
+  }
+  return (int)d.ntasks;
 }
 
 int fpcode_prepared_shape(const fpcode_prepared *prep, int *m, int *kj, int *npasses, int *complete) {

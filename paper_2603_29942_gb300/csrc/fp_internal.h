@@ -20,6 +20,10 @@ const fpenum::Binom &binom();  // host binomial table
 
 bool is_odd_prime(int p);
 
+// Digit width of the packed coefficient counter for prime p (the kernels
+// use the same: 1 bit for p = 3, 4 for p = 5, 7, 8 otherwise).
+int digit_bits_of(int p);
+
 struct Prepared {
   int p = 0, n = 0, k = 0, r = 0, W = 0, rwpad = 0, m = 0, variant = 0;
   fpcode_opts opts{};
@@ -32,7 +36,8 @@ struct Prepared {
   int complete = 0;              // schedule reaches the last level
   int L0 = 0;                    // lower bound before any pass
   double t_prepare_ms = 0;
-  size_t table_bytes_per_set() const { return (size_t)k * (p - 1) * rwpad * 4; }
+  size_t table_words_per_set() const { return (size_t)k * ((size_t)(p - 1) * rwpad + fpk::sig_words(p, r, W)); }
+  size_t table_bytes_per_set() const { return table_words_per_set() * 4; }
 };
 
 // Elimination, information sets, multiples, schedule.  Returns an fpcode

@@ -54,6 +54,16 @@ struct CtlDyn {
   int32_t pad[3];
 };
 
+// Shared memory: binomial columns C(n, t), t < kBinomCols, then the staged
+// table of one information set.
+constexpr int kBinomCols = 24;
+constexpr int kBinomBytes = kBinomCols * (fpenum::kMaxK + 1) * 8;  // 12480, a multiple of 16
+
+// Words of one information set's table: multiples, then pair signatures.
+__device__ __forceinline__ int table_words(const SlotDesc &sd) {
+  return sd.k * ((sd.p - 1) * sd.rwpad + sig_words(sd.p, sd.r, sd.W));
+}
+
 // SlotState.status while a code is running is 0; the finaliser stores
 // kDoneFlag | fpcode status.
 constexpr int32_t kDoneFlag = 0x100;
@@ -179,26 +189,62 @@ __device__ void task_rows(const SlotDesc &sd, int pass, const uint32_t *tab, int
 
 // ---------------------------------------------------------------------------
 // Task of a pass with g >= 2.
+//
+// Leaf filter.  For a leaf row x and a pair of coefficients {c, p-c}, the
+// positions where BOTH S + cA[x] and S - cA[x] are nonzero give a lower
+// bound on either weight.  For p = 2^r - 1, with y = cA[x] and d = S xor y,
+// S + y = 0 iff d is all ones and S - y = 0 iff d is all zeros (negation is
+// the bitwise complement), so that mask is OR_i (d_i xor d_{i+1}) =
+// OR_i ((S_i xor S_{i+1}) xor (y_i xor y_{i+1})): the prefix keeps its r-1
+// "signature" words, the row table stores the leaf's.  Other primes AND the
+// two isometric subtractions.  One POPC per word covers two codewords (for
+// p = 3 both leaf coefficients); only a pair whose bound is below the
+// current threshold is evaluated exactly (slow path).
 // ---------------------------------------------------------------------------
+template <int P, int R, int W>
+struct LeafFilter {
+  static constexpr bool kMersenne = (P == 3 || P == 7);
+  static constexpr int kSigW = kMersenne ? (((P == 3 ? W * (R - 1) : 3 * W * (R - 1)) + 3) & ~3) : 0;
+  static constexpr int kPrefSig = kMersenne ? W * (R - 1) : 1;
+};
+
+template <int R, int W, int NA>
+__device__ __forceinline__ void prefix_signature(const uint32_t (&s)[R * W], uint32_t (&a)[NA]) {
+  static_assert(NA >= W * (R - 1), "signature size");
+#pragma unroll
+  for (int w = 0; w < W; ++w)
+#pragma unroll
+    for (int i = 0; i + 1 < R; ++i) a[w * (R - 1) + i] = s[w * R + i] ^ s[w * R + i + 1];
+}
+
 template <int P, int R, int W, int DB>
 __device__ void task_prefixes(const SlotDesc &sd, const PassDesc &pd, int pass, const uint32_t *tab,
-                              const fpenum::Binom &B, uint64_t task, int U, SlotState *st,
+                              const fpenum::BinomCols &B, uint64_t task, int U, SlotState *st,
                               unsigned long long &count) {
   constexpr int RW = R * W;
   constexpr int RWP = Shape<R, W>::RWP;
+  using F = LeafFilter<P, R, W>;
   const int p = P ? P : sd.p;
   const int b = p - 1;
   const int k = sd.k;
   const int g = pd.g;
   const int L = g - 2;
-  const int pl = pd.pl;
-  uint64_t I = (task * kThreads + threadIdx.x) * (uint64_t)pl;
-  const uint64_t Iend = min(I + (uint64_t)pl, pd.nprefix);
+  const uint32_t *sig = tab + k * b * RWP;  // pair signatures (Mersenne p)
+  uint64_t ulo, uhi;
+  task_range(pd, task, &ulo, &uhi);
+  const uint64_t pu = (uhi - ulo + kThreads - 1) / kThreads;  // units per lane, same for the CTA
+  const uint64_t unit = pd.unit;
+  const uint64_t pl = pu * unit;                               // prefix steps
+  uint64_t I = (ulo + (uint64_t)threadIdx.x * pu) * unit;
+  const uint64_t Iend = min(I + pl, pd.nprefix < uhi * unit ? pd.nprefix : uhi * unit);
   int thr = U - g + 1;  // record weights <= U: redundant weight < U - g + 1
 
   uint32_t s[RW];
 #pragma unroll
   for (int q = 0; q < RW; ++q) s[q] = 0;
+  uint32_t a[F::kPrefSig];
+#pragma unroll
+  for (int q = 0; q < F::kPrefSig; ++q) a[q] = 0;
   fpenum::Prefix pf;
   pf.m = k;
   pf.qi = 0;
@@ -208,39 +254,56 @@ __device__ void task_prefixes(const SlotDesc &sd, const PassDesc &pd, int pass, 
   if (I < Iend) {
     pf = fpenum::prefix_unrank<DB>(B, I, k, g, b);
     ci = (I - fpenum::prefixes_below(B, pf.m, g, pd.NC)) - pf.qi * pd.NC;
-    nq = B.c[pf.m][L];
+    nq = B(pf.m, L);
     build_sum<P, R, W, DB>(s, tab, pf, L, b, p);
+    if constexpr (F::kMersenne) prefix_signature<R, W>(s, a);
   }
 
-  for (int step = 0; step < pl; ++step) {
+  for (uint64_t step = 0; step < pl; ++step) {
     const bool act = I < Iend;
     const int mlane = act ? pf.m : k;
     const int xs = (int)__reduce_min_sync(0xffffffffu, (unsigned)mlane) + 1;
     for (int x = xs; x < k; ++x) {
       const int tx = x > mlane ? thr : 0;
       bool hit = false;
-      if (P) {
+      if constexpr (F::kMersenne) {
+        uint32_t e[F::kSigW];
+        load_entry<F::kSigW>(sig, x, e);
+        constexpr int NP = (P - 1) / 2;
 #pragma unroll
-        for (int c = 1; c < (P ? P : 2); ++c) {
-          uint32_t e[RWP];
-          load_entry<RWP>(tab, x * b + (p - c - 1), e);
-          hit |= leaf_weight<R, W>(s, e) < tx;
+        for (int q = 0; q < NP; ++q) {
+          int lb = 0;
+#pragma unroll
+          for (int w = 0; w < W; ++w) {
+            uint32_t f = 0;
+#pragma unroll
+            for (int i = 0; i + 1 < R; ++i) f |= a[w * (R - 1) + i] ^ e[(q * W + w) * (R - 1) + i];
+            lb += __popc(f);
+          }
+          hit |= lb < tx;
         }
       } else {
-        for (int c = 1; c < p; ++c) {
-          uint32_t e[RWP];
-          load_entry<RWP>(tab, x * b + (p - c - 1), e);
-          hit |= leaf_weight<R, W>(s, e) < tx;
+        const int np = (p - 1) / 2;
+        for (int q = 0; q < np; ++q) {
+          const int c = q + 1;
+          uint32_t e1[RWP], e2[RWP];
+          load_entry<RWP>(tab, x * b + (p - c - 1), e1);  // (p - c) A = -c A
+          load_entry<RWP>(tab, x * b + (c - 1), e2);      // c A = -(p - c) A
+          int lb = 0;
+#pragma unroll
+          for (int w = 0; w < W; ++w)
+            lb += __popc(fpbs::nz_sub<R>(&s[w * R], &e1[w * R]) & fpbs::nz_sub<R>(&s[w * R], &e2[w * R]));
+          hit |= lb < tx;
         }
       }
       if (__any_sync(0xffffffffu, hit)) {
-        if (hit) {  // slow path: exact weights, record the candidates
+        if (hit) {  // slow path: exact weights of every leaf coefficient
           for (int c = 1; c < p; ++c) {
             uint32_t e[RWP];
             load_entry<RWP>(tab, x * b + (p - c - 1), e);
-            int wr = leaf_weight<R, W>(s, e);
+            const int wr = leaf_weight<R, W>(s, e);
             if (wr < thr) {
-              int newU = record(st, make_key((uint32_t)(g + wr), (uint32_t)pass, I, (uint32_t)x, (uint32_t)c));
+              const int newU = record(st, make_key((uint32_t)(g + wr), (uint32_t)pass, I, (uint32_t)x, (uint32_t)c));
               thr = newU - g + 1;
             }
           }
@@ -260,15 +323,16 @@ __device__ void task_prefixes(const SlotDesc &sd, const PassDesc &pd, int pass, 
       } else {
         build_sum<P, R, W, DB>(s, tab, pf, L, b, p);
       }
+      if constexpr (F::kMersenne) prefix_signature<R, W>(s, a);
     }
   }
 }
 
 template <int P, int R, int W>
 struct Fixed {
-  static constexpr int DB = (P != 0 && P <= 17) ? 4 : 8;
+  static constexpr int DB = P == 3 ? 1 : (P == 5 || P == 7) ? 4 : 8;  // as the host's digit width
   static __device__ __forceinline__ void run(const SlotDesc &sd, const PassDesc &pd, int pass, const uint32_t *tab,
-                                             const fpenum::Binom &B, uint64_t task, int U, SlotState *st,
+                                             const fpenum::BinomCols &B, uint64_t task, int U, SlotState *st,
                                              unsigned long long &count) {
     if (pd.g == 1) {
       if (task == 0) task_rows<P, R, W>(sd, pass, tab, U, st, count);
@@ -288,7 +352,7 @@ __host__ __device__ inline int variant_id(int p, int r, int W) {
 // Batched launches over codes with p in {3, 5, 7}: dispatch per task.
 struct Multi357 {
   static __device__ __forceinline__ void run(const SlotDesc &sd, const PassDesc &pd, int pass, const uint32_t *tab,
-                                             const fpenum::Binom &B, uint64_t task, int U, SlotState *st,
+                                             const fpenum::BinomCols &B, uint64_t task, int U, SlotState *st,
                                              unsigned long long &count) {
     switch (sd.variant) {
 #define FPK_CASE(id, P, R, W) \
@@ -392,6 +456,7 @@ __device__ __forceinline__ void finish_task(const CtlStatic &cs, const SlotDesc 
   unsigned long long done = atomicAdd(&st->done, 1ull) + 1ull;
   if (done != pd.ntasks) return;
   __threadfence();
+  if (sd.pass_times) sd.pass_times[P] = globaltimer();
   uint64_t key = ~(uint64_t)atomicOr(&st->best_key, 0ull);
   int U = key == kNoKey ? sd.n - sd.k + 2 : (int)key_weight(key);
   const bool check = !sd.per_round_check || pd.round_end;
@@ -424,7 +489,9 @@ __global__ void __launch_bounds__(kThreads) bz_kernel(const SlotDesc *__restrict
                                                       const CtlStatic *__restrict__ ctl, CtlDyn *cdyn,
                                                       KParams kp) {
   extern __shared__ uint4 smem_raw[];
-  uint32_t *tab = reinterpret_cast<uint32_t *>(smem_raw);
+  uint64_t *bcols = reinterpret_cast<uint64_t *>(smem_raw);  // binomial columns t < kBinomCols
+  uint4 *tab4 = smem_raw + kBinomBytes / 16;
+  uint32_t *tab = reinterpret_cast<uint32_t *>(tab4);
   __shared__ SlotDesc s_sd;
   __shared__ PassDesc s_pd;
   __shared__ int s_cmd, s_slot, s_pass, s_U, s_skip, s_stage;
@@ -441,6 +508,16 @@ __global__ void __launch_bounds__(kThreads) bz_kernel(const SlotDesc *__restrict
     s_staged_j = -1;
     s_staged_seq = 0;
   }
+  for (int i = tid; i < kBinomCols * (fpenum::kMaxK + 1); i += kThreads) {
+    const int t = i / (fpenum::kMaxK + 1), n = i % (fpenum::kMaxK + 1);
+    bcols[i] = cs.binom->c[n][t];
+  }
+  const fpenum::BinomCols binom{bcols};
+  if (blockIdx.x == 0 && tid == 0 && cs.nslots == 1) {
+    const SlotDesc sd0 = load_cg(&slots[0]);
+    if (sd0.pass_times) sd0.pass_times[kMaxPasses] = t_start;  // launch start
+  }
+  __syncthreads();
   for (;;) {
     if (tid == 0) {
       int slot = 0, pass = 0, U = 0, skip = 0;
@@ -475,13 +552,13 @@ __global__ void __launch_bounds__(kThreads) bz_kernel(const SlotDesc *__restrict
     }
     const int slot = s_slot, pass = s_pass;
     if (s_stage) {
-      const int words = s_sd.k * (s_sd.p - 1) * s_sd.rwpad;
+      const int words = table_words(s_sd);
       const uint4 *src = reinterpret_cast<const uint4 *>(s_sd.table + (size_t)s_pd.j * (size_t)words);
-      for (int i = tid; i < words / 4; i += kThreads) smem_raw[i] = __ldcg(src + i);
+      for (int i = tid; i < words / 4; i += kThreads) tab4[i] = __ldcg(src + i);
       __syncthreads();
     }
     unsigned long long count = 0;
-    if (!s_skip) V::run(s_sd, s_pd, pass, tab, *cs.binom, s_task, s_U, &states[slot], count);
+    if (!s_skip) V::run(s_sd, s_pd, pass, tab, binom, s_task, s_U, &states[slot], count);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) count += __shfl_xor_sync(0xffffffffu, count, o);
     if ((tid & 31) == 0 && count) atomicAdd(&s_count, count);

@@ -110,7 +110,7 @@ extern "C" int fpcode_min_distance_noalloc(int p, int n, int k, const uint8_t *G
 
   const void *fn = kernel_of(P.variant);
   if (!fn) return FPCODE_EINVAL;
-  const int smem = (int)((std::max<size_t>(16, P.table_bytes_per_set()) + 15) & ~(size_t)15);
+  const int smem = (int)(((std::max<size_t>(16, P.table_bytes_per_set()) + 15) & ~(size_t)15) + fpk::kBinomBytes);
   if (smem > 48 * 1024) NA_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   int per_sm = 0, sms = 0;
   NA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, fpk::kThreads, (size_t)smem));

@@ -167,7 +167,7 @@ int fpcode_serve_create(const fpcode_serve_opts *opts, void *stream, fpcode_serv
   int st = fpd::get_ctx(&s->ctx);
   if (st) return st;
   s->fn = fpk::kernel_multi357();
-  s->smem = (int)kServeTableSet;
+  s->smem = (int)kServeTableSet + fpk::kBinomBytes;
   int per_sm = 0;
   st = fpd::occupancy(s->fn, s->smem, o.ctas_per_sm, &per_sm);
   if (st) return st;

@@ -40,14 +40,47 @@ struct PassDesc {
   int32_t L_before;   // lower bound before the pass (valid: earlier passes complete)
   int32_t L_after;    // lower bound once the pass is complete
   int32_t round_end;  // last pass of round g (per-round termination check)
-  int32_t pl;         // prefixes per lane in one CTA task
+  int32_t pl;         // > 0: fixed tasks of kThreads * pl prefixes; 0: guided
   uint32_t ntasks;    // CTA tasks in the pass
-  uint32_t pad;
+  uint32_t phases;    // guided: phases of plan_ctas tasks, each half the last (0: 256-prefix tasks)
   uint64_t nprefix;   // prefixes (g >= 2) or rows (g == 1)
   uint64_t size;      // codewords in the pass: C(k,g)(p-1)^(g-1)
   uint64_t NC;        // (p-1)^(g-2) coefficient vectors per prefix subset
-  uint64_t pad2;      // 64 bytes: read with 16-byte coherent loads
+  uint32_t plan_ctas; // guided: tasks per phase
+  uint32_t unit;      // prefixes per work unit: b^t, aligned to the coefficient counter
 };
+
+// Words per row of the pair-signature table (Mersenne p = 3, 7): for each
+// pair {c, -c} (representatives c = 1 for p = 3; 1, 2, 4 for p = 7) and
+// word w, the r-1 words y_i xor y_{i+1} of y = c * A[row] (0 otherwise).
+FPK_HD int sig_words(int p, int r, int W) {
+  const int raw = p == 3 ? W * (r - 1) : p == 7 ? 3 * W * (r - 1) : 0;
+  return (raw + 3) & ~3;
+}
+FPK_HD int pair_rep(int p, int q) { return p == 7 ? (1 << q) : q + 1; }
+
+// Unit range [lo, hi) of CTA task t of a pass with g >= 2 (a unit is
+// d.unit consecutive prefixes; every unit starts where the lowest digits of
+// the coefficient counter are zero, so all lanes of a warp take the same
+// Gray steps).  Guided tasks: phase h (plan_ctas tasks) covers
+// [N - (N >> h), N - (N >> (h+1))) of the N units, the last phase the rest,
+// so tasks shrink as the pass drains.
+FPK_HD void task_range(const PassDesc &d, uint64_t t, uint64_t *lo, uint64_t *hi) {
+  const uint64_t N = d.nprefix / d.unit;
+  if (d.pl > 0 || d.phases == 0) {
+    const uint64_t chunk = (uint64_t)kThreads * (uint64_t)(d.pl > 0 ? d.pl : 1);
+    *lo = t * chunk;
+    *hi = *lo + chunk < N ? *lo + chunk : N;
+    return;
+  }
+  const uint64_t C = d.plan_ctas;
+  const uint64_t h = t / C, i = t % C;
+  const uint64_t plo = N - (N >> h);
+  const uint64_t phi = (h + 1 == d.phases) ? N : N - (N >> (h + 1));
+  const uint64_t size = phi - plo;
+  *lo = plo + size * i / C;
+  *hi = plo + size * (i + 1) / C;
+}
 static_assert(sizeof(PassDesc) == 64, "PassDesc layout");
 
 // Static description of one code as the kernel sees it.
@@ -61,7 +94,7 @@ struct SlotDesc {
   const uint32_t *table;         // m * k * (p-1) * rwpad words, device
   const PassDesc *passes;        // npasses entries, device
   uint64_t seq;                  // serving: ticket of the code in this slot
-  uint64_t pad;
+  unsigned long long *pass_times;  // optional: %globaltimer at each pass end (device)
 };
 static_assert(sizeof(SlotDesc) == 80, "SlotDesc layout");
 

@@ -71,7 +71,9 @@ def test_serve_admission_by_memory():
     """With room for about one code's tables, later requests wait (EBUSY)
     and are admitted once earlier codes finish."""
     codes = [inputs.single_code(40 + i, 7, 40, 20) for i in range(4)]
-    tb = 2 * 20 * 6 * 4 * 4  # bytes of one code's bit-sliced multiples
+    # one code's table: 2 information sets x 20 rows x (6 multiples x 4 words
+    # + 8 words of pair signatures) x 4 bytes
+    tb = 2 * 20 * (6 * 4 + 8) * 4
     srv = B.fpcode_serve_create(B.fpcode_serve_opts_default(slots=8, device_bytes=tb + 256))
     first = B.fpcode_serve_submit(srv, codes[0], budget=10 ** 5)
     assert first is not None

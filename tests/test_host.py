@@ -336,3 +336,27 @@ def test_prepare_rejects_bad_input(lib):
     rank_def[0, 0] = rank_def[1, 0] = 1
     with pytest.raises(B.FpcodeError):
         B.fpcode_prepare(3, 5, 2, rank_def)
+
+
+@pytest.mark.parametrize("ctas,fixed_pl", [(760, 0), (608, 0), (152, 0), (7, 0), (760, 3), (1, 0)])
+def test_task_ranges_tile_each_pass(ctas, fixed_pl, lib):
+    """Guided (shrinking) and fixed task ranges cover every prefix of a pass
+    exactly once, in order."""
+    code = inputs.single("f3_n80_k40")
+    pr = _prep(code)
+    passes = B.fpcode_prepared_passes(pr)
+    for i, (g, _j, _Lb, _La, _re, _size, nprefix) in enumerate(passes[:14]):
+        if fixed_pl and nprefix > 256 * fixed_pl * 60000:
+            continue  # more tasks than the hook returns
+        ranges = B.fpcode_test_task_ranges(pr, i, ctas, fixed_pl)
+        if g == 1:
+            assert ranges == [(0, nprefix)]
+            continue
+        pos = 0
+        for lo, hi in ranges:
+            assert lo == pos and hi >= lo
+            pos = hi
+        assert pos == nprefix
+        if fixed_pl == 0 and nprefix > 2 * 256 * ctas:
+            sizes = [hi - lo for lo, hi in ranges]
+            assert sizes[0] + 256 >= sizes[-1]  # tasks shrink as the pass drains (up to one unit)
