@@ -69,7 +69,11 @@ typedef struct fpcode_opts {
                           the choice among equal-weight witnesses may vary */
   int ctas_per_sm;     /* 0: from the occupancy calculator */
   int prefixes_per_lane; /* 0: autotuned per pass; else fixed (1..64) */
-  int reserved0;
+  int lookahead;       /* 1 (default): CTAs take tasks of the next passes as
+                          soon as the current pass has none left, instead of
+                          waiting for its last tasks; the termination test
+                          still runs pass by pass in order, so d, L and the
+                          passes entered are the same; 0: one pass at a time */
   uint64_t budget;     /* 0: unlimited; else a pass is not entered if it
                           would take the per-level count total above it */
   double timeout_s;    /* 0: none; else time limit of one device search */
@@ -87,7 +91,9 @@ typedef struct fpcode_result {
   int m;               /* number of information sets */
   int npasses;         /* passes entered (last pass index + 1) */
   int reserved0, reserved1;
-  uint64_t enumerated; /* codewords the GPU evaluated */
+  uint64_t enumerated; /* codewords the GPU evaluated in the passes entered
+                          (work taken ahead past the certifying pass is not
+                          counted) */
   uint64_t counts[FPCODE_MAX_K + 1]; /* per level g: codewords of the passes
                           entered, C(k,g)(p-1)^(g-1) each (equals the
                           enumeration when mid_pass_exit = 0) */

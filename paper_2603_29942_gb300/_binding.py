@@ -34,7 +34,7 @@ class fpcode_opts(ctypes.Structure):
         ("mid_pass_exit", ctypes.c_int),
         ("ctas_per_sm", ctypes.c_int),
         ("prefixes_per_lane", ctypes.c_int),
-        ("reserved0", ctypes.c_int),
+        ("lookahead", ctypes.c_int),
         ("budget", ctypes.c_uint64),
         ("timeout_s", ctypes.c_double),
         ("wait_limit_s", ctypes.c_double),

@@ -113,6 +113,7 @@ KParams kparams(const fpcode_opts &o, int serve) {
   kp.timeout_ns = o.timeout_s > 0 ? (unsigned long long)(o.timeout_s * 1e9) : 0ull;
   kp.idle_limit_ns = serve ? 20000000ull : 0ull;
   kp.mid_pass = o.mid_pass_exit ? 1 : 0;
+  kp.lookahead = o.lookahead ? 1 : 0;
   return kp;
 }
 
@@ -135,7 +136,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // ---------------------------------------------------------------------------
 struct Layout {
   size_t off_ctl = 0, off_slots = 0, off_passes = 0, off_tables = 0, static_bytes = 0;
-  size_t off_states = 0, dyn_bytes = 0, off_times = 0, total = 0;
+  size_t off_states = 0, dyn_bytes = 0, off_aux = 0, aux_bytes = 0, off_times = 0, total = 0;
   std::vector<size_t> pass_off, table_off;
 };
 
@@ -159,8 +160,10 @@ Layout make_layout(const std::vector<const fph::Prepared *> &codes) {
   }
   L.static_bytes = o;
   L.off_states = o;
-  L.dyn_bytes = align256(ns * sizeof(SlotState) + sizeof(CtlDyn));
-  L.off_times = o + L.dyn_bytes;  // per-pass end times of a single code (diagnostics)
+  L.dyn_bytes = align256(ns * sizeof(SlotState) + sizeof(CtlDyn));  // read back after a search
+  L.off_aux = o + L.dyn_bytes;
+  L.aux_bytes = align256(ns * sizeof(fpk::SlotAux));                  // zeroed, never read back
+  L.off_times = L.off_aux + L.aux_bytes;  // per-pass end times of a single code (diagnostics)
   L.total = L.off_times + (fpk::kMaxPasses + 1) * sizeof(unsigned long long);
   return L;
 }
@@ -170,6 +173,7 @@ void fill_static(const Layout &L, const std::vector<const fph::Prepared *> &code
                  char *d, int serve) {
   CtlStatic cs{};
   cs.binom = c.binom;
+  cs.aux = reinterpret_cast<fpk::SlotAux *>(d + L.off_aux);
   cs.nslots = (int)codes.size();
   cs.serve = serve;
   std::memcpy(h + L.off_ctl, &cs, sizeof(cs));
@@ -199,7 +203,7 @@ void fill_static(const Layout &L, const std::vector<const fph::Prepared *> &code
 fph::DeviceOutcome outcome_of(const SlotState &s, const CtlDyn &dyn) {
   fph::DeviceOutcome o{};
   o.best_key = ~(uint64_t)s.best_key;
-  o.enumerated = s.enumerated;
+  o.enumerated = s.finished ? s.entered : s.enumerated;
   if (s.finished) {
     o.status = s.status & 0xFF;
     o.stop_pass = s.stop_pass;
@@ -263,7 +267,7 @@ int upload_one(fpcode_prepared *prep, cudaStream_t st, DevCtx &c, char *d, char 
 int enqueue_one(fpcode_prepared *prep, cudaStream_t st, const fpcode_opts &o) {
   fph::Prepared &P = prep->host;
   Layout L = make_layout({&P});
-  FP_CUDA(cudaMemsetAsync(prep->dev + L.off_states, 0, L.dyn_bytes, st));
+  FP_CUDA(cudaMemsetAsync(prep->dev + L.off_states, 0, L.dyn_bytes + L.aux_bytes, st));
   if (!P.passes.empty()) {
     FP_CUDA(cudaEventRecord((cudaEvent_t)prep->ev0, st));
     int s = launch(kernel_for(P.variant), prep->ctas, prep->smem, st, prep->dev, L, kparams(o, 0));
@@ -320,6 +324,7 @@ void fpcode_opts_default(fpcode_opts *o) {
   o->per_round_check = 0;
   o->defer = 1;
   o->mid_pass_exit = 1;
+  o->lookahead = 1;
   o->wait_limit_s = 10.0;
 }
 
@@ -500,7 +505,7 @@ int fpcode_min_distance_batch(int num, const fpcode_desc *codes, void *stream, c
     if (s) break;
     fill_static(L, codesv, *c, c->ws_pinned, c->ws, 0);
     FP_CUDA(cudaMemcpyAsync(c->ws, c->ws_pinned, L.static_bytes, cudaMemcpyHostToDevice, st));
-    FP_CUDA(cudaMemsetAsync(c->ws + L.off_states, 0, L.dyn_bytes, st));
+    FP_CUDA(cudaMemsetAsync(c->ws + L.off_states, 0, L.dyn_bytes + L.aux_bytes, st));
     FP_CUDA(cudaEventRecord(e0, st));
     s = launch(fn, ctas, smem, st, c->ws, L, kparams(o, 0));
     if (s) break;

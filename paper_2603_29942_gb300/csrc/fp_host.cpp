@@ -310,6 +310,12 @@ void plan_tasks(Prepared *P, int ctas, int fixed_pl) {
     d.phases = H;
     d.ntasks = (uint32_t)(H * C);
   }
+  // one task sequence over all passes
+  uint64_t base = 0;
+  for (auto &d : P->passes) {
+    d.task_base = (uint32_t)base;
+    base += d.ntasks;
+  }
 }
 
 namespace {

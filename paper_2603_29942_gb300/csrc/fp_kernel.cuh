@@ -35,6 +35,7 @@ namespace fpk {
 struct CtlStatic {
   const fpenum::Binom *binom;
   Completion *done_host;  // serving: host-mapped completion records (else null)
+  SlotAux *aux;           // per-slot pass minima and counts (zeroed with the states)
   int32_t nslots;
   int32_t serve;          // serving: slots appear while the kernel runs
 };
@@ -45,7 +46,7 @@ struct KParams {
   unsigned long long timeout_ns;     // 0: none; else per-launch time limit
   unsigned long long idle_limit_ns;  // serving: exit after this long idle
   int32_t mid_pass;                  // -1: per code; 0 / 1: override
-  int32_t pad;
+  int32_t lookahead;                 // 1: take tasks of later passes while earlier ones drain
 };
 
 // Launch-wide dynamic flags (zeroed before each launch).
@@ -158,8 +159,10 @@ __device__ __forceinline__ int leaf_weight(const uint32_t (&s)[R * W], const uin
   return wsum;
 }
 
-// Record a candidate codeword; returns the (possibly lowered) bound U.
-__device__ __forceinline__ int record(SlotState *st, uint64_t key) {
+// Record a candidate codeword: the code's packed best key and the least
+// weight of its pass.  Returns the (possibly lowered) bound U.
+__device__ __forceinline__ int record(SlotState *st, SlotAux *ax, int pass, uint64_t key) {
+  atomicMax(&ax->pass_min[pass], 256 - (int)key_weight(key));
   unsigned long long old = atomicMax(&st->best_key, (unsigned long long)~key);
   uint64_t best = ~(uint64_t)old;
   if (key < best) best = key;
@@ -170,7 +173,7 @@ __device__ __forceinline__ int record(SlotState *st, uint64_t key) {
 // Task of a pass with g == 1: the k rows themselves (coefficient 1).
 // ---------------------------------------------------------------------------
 template <int P, int R, int W>
-__device__ void task_rows(const SlotDesc &sd, int pass, const uint32_t *tab, int U, SlotState *st,
+__device__ void task_rows(const SlotDesc &sd, int pass, const uint32_t *tab, int U, SlotState *st, SlotAux *ax,
                           unsigned long long &count) {
   constexpr int RWP = Shape<R, W>::RWP;
   const int x = threadIdx.x;
@@ -182,7 +185,7 @@ __device__ void task_rows(const SlotDesc &sd, int pass, const uint32_t *tab, int
 #pragma unroll
     for (int w = 0; w < W; ++w) wsum += __popc(fpbs::nz<R>(&e[w * R]));
     int weight = 1 + wsum;
-    if (weight <= U) record(st, make_key((uint32_t)weight, (uint32_t)pass, 0, (uint32_t)x, 1));
+    if (weight <= U) record(st, ax, pass, make_key((uint32_t)weight, (uint32_t)pass, 0, (uint32_t)x, 1));
     count += 1;
   }
 }
@@ -219,7 +222,7 @@ __device__ __forceinline__ void prefix_signature(const uint32_t (&s)[R * W], uin
 
 template <int P, int R, int W, int DB>
 __device__ void task_prefixes(const SlotDesc &sd, const PassDesc &pd, int pass, const uint32_t *tab,
-                              const fpenum::BinomCols &B, uint64_t task, int U, SlotState *st,
+                              const fpenum::BinomCols &B, uint64_t task, int U, SlotState *st, SlotAux *ax,
                               unsigned long long &count) {
   constexpr int RW = R * W;
   constexpr int RWP = Shape<R, W>::RWP;
@@ -260,6 +263,11 @@ __device__ void task_prefixes(const SlotDesc &sd, const PassDesc &pd, int pass, 
   }
 
   for (uint64_t step = 0; step < pl; ++step) {
+    if ((step & 15) == 15) {
+      // a finished code only has tasks of passes past its stop left: drop them
+      int fin = (threadIdx.x & 31) == 0 ? ld_vol(&st->finished) : 0;
+      if (__shfl_sync(0xffffffffu, fin, 0)) break;
+    }
     const bool act = I < Iend;
     const int mlane = act ? pf.m : k;
     const int xs = (int)__reduce_min_sync(0xffffffffu, (unsigned)mlane) + 1;
@@ -303,7 +311,8 @@ __device__ void task_prefixes(const SlotDesc &sd, const PassDesc &pd, int pass, 
             load_entry<RWP>(tab, x * b + (p - c - 1), e);
             const int wr = leaf_weight<R, W>(s, e);
             if (wr < thr) {
-              const int newU = record(st, make_key((uint32_t)(g + wr), (uint32_t)pass, I, (uint32_t)x, (uint32_t)c));
+              const int newU =
+                  record(st, ax, pass, make_key((uint32_t)(g + wr), (uint32_t)pass, I, (uint32_t)x, (uint32_t)c));
               thr = newU - g + 1;
             }
           }
@@ -333,11 +342,11 @@ struct Fixed {
   static constexpr int DB = P == 3 ? 1 : (P == 5 || P == 7) ? 4 : 8;  // as the host's digit width
   static __device__ __forceinline__ void run(const SlotDesc &sd, const PassDesc &pd, int pass, const uint32_t *tab,
                                              const fpenum::BinomCols &B, uint64_t task, int U, SlotState *st,
-                                             unsigned long long &count) {
+                                             SlotAux *ax, unsigned long long &count) {
     if (pd.g == 1) {
-      if (task == 0) task_rows<P, R, W>(sd, pass, tab, U, st, count);
+      if (task == 0) task_rows<P, R, W>(sd, pass, tab, U, st, ax, count);
     } else {
-      task_prefixes<P, R, W, DB>(sd, pd, pass, tab, B, task, U, st, count);
+      task_prefixes<P, R, W, DB>(sd, pd, pass, tab, B, task, U, st, ax, count);
     }
   }
 };
@@ -353,10 +362,10 @@ __host__ __device__ inline int variant_id(int p, int r, int W) {
 struct Multi357 {
   static __device__ __forceinline__ void run(const SlotDesc &sd, const PassDesc &pd, int pass, const uint32_t *tab,
                                              const fpenum::BinomCols &B, uint64_t task, int U, SlotState *st,
-                                             unsigned long long &count) {
+                                             SlotAux *ax, unsigned long long &count) {
     switch (sd.variant) {
 #define FPK_CASE(id, P, R, W) \
-  case id: Fixed<P, R, W>::run(sd, pd, pass, tab, B, task, U, st, count); break;
+  case id: Fixed<P, R, W>::run(sd, pd, pass, tab, B, task, U, st, ax, count); break;
       FPK_CASE(0, 3, 2, 1)
       FPK_CASE(1, 3, 2, 2)
       FPK_CASE(2, 3, 2, 3)
@@ -377,13 +386,43 @@ struct Multi357 {
 
 enum { kCmdRun = 0, kCmdWait = 1, kCmdExit = 2 };
 
-// Thread 0: claim the next task of any live code.  On success the code's
-// descriptor and the pass descriptor are copied (coherently) to *o_sd, *o_pd.
+// What thread 0 hands to its CTA for one task.
+struct Claim {
+  SlotDesc sd;
+  PassDesc pd;              // the task's pass
+  unsigned long long task;  // task index within the pass
+  int slot, pass, U, skip;
+};
+
+// Thread 0's cache of the descriptors it read last (one slot and pass), so
+// that an idle probe costs two loads: the finished flag and the task word.
+struct ClaimCache {
+  int slot;  // -1: empty
+  unsigned long long gen;
+  int P;     // pass whose descriptor is cached (-1: none)
+  SlotDesc sd;
+  PassDesc pd;
+  unsigned int sleep_ns;
+};
+
+// Pass of global task t, searching forward from the cached pass.
+__device__ __forceinline__ bool locate(ClaimCache &cc, unsigned long long t) {
+  if (cc.P < 0 || t < cc.pd.task_base) {
+    cc.P = 0;
+    cc.pd = load_cg(&cc.sd.passes[0]);
+  }
+  while (t >= (unsigned long long)cc.pd.task_base + cc.pd.ntasks) {
+    if (cc.P + 1 >= cc.sd.npasses) return false;
+    ++cc.P;
+    cc.pd = load_cg(&cc.sd.passes[cc.P]);
+  }
+  return true;
+}
+
+// Thread 0: claim the next task of any live code.
 __device__ __forceinline__ int claim(const SlotDesc *slots, SlotState *states, const CtlStatic &cs,
                                      const KParams &kp, CtlDyn *cd, int &rr, unsigned long long &wait_t0,
-                                     unsigned long long t_start, int *o_slot, int *o_pass,
-                                     unsigned long long *o_task, int *o_U, int *o_skip, SlotDesc *o_sd,
-                                     PassDesc *o_pd) {
+                                     unsigned long long t_start, Claim *o, ClaimCache &cc) {
   const int nslots = cs.nslots;
   unsigned long long now = globaltimer();
   if (kp.timeout_ns && now - t_start > kp.timeout_ns) {
@@ -396,42 +435,47 @@ __device__ __forceinline__ int claim(const SlotDesc *slots, SlotState *states, c
     if (s >= nslots) s -= nslots;
     SlotState *st = &states[s];
     if (ld_vol(&st->finished)) continue;
-    __threadfence();  // the descriptor was written before the state was reset
-    SlotDesc sd = load_cg(&slots[s]);
-    if (sd.npasses <= 0) continue;
-    live = true;
-    const unsigned long long gen = sd.seq & kGenMask;
     unsigned long long w = ld_vol(&st->word);
-    if ((w >> kGenShift) != gen) continue;  // slot in transition between two codes
-    int P = (int)((w >> 40) & 0xFF);
-    if (P >= sd.npasses) continue;
-    PassDesc pd = load_cg(&sd.passes[P]);
-    if ((w & kTaskMask) >= pd.ntasks) continue;
+    const unsigned long long wgen = w >> kGenShift;
+    if (cc.slot != s || cc.gen != wgen) {
+      __threadfence();  // the descriptor was written before the state was reset
+      cc.sd = load_cg(&slots[s]);
+      cc.slot = s;
+      cc.gen = cc.sd.seq & kGenMask;
+      cc.P = -1;
+    }
+    if (cc.sd.npasses <= 0) continue;
+    live = true;
+    if (wgen != cc.gen) continue;  // slot in transition between two codes
+    if (!locate(cc, w & kTaskMask)) continue;  // every task handed out
+    if (!kp.lookahead && cc.P > ld_vol(&st->frontier)) continue;  // one pass at a time
     w = atomicAdd(&st->word, 1ull);
-    const int P2 = (int)((w >> 40) & 0xFF);
-    const unsigned long long t = w & kTaskMask;
-    if ((w >> kGenShift) != gen) {
+    if ((w >> kGenShift) != cc.gen) {
       // the slot now holds a newer code; its descriptor was written before
       // its state, so re-reading it gives the code this task belongs to
-      sd = load_cg(&slots[s]);
-      if ((sd.seq & kGenMask) != (w >> kGenShift)) continue;
-      P = -1;
+      __threadfence();
+      cc.sd = load_cg(&slots[s]);
+      cc.gen = cc.sd.seq & kGenMask;
+      cc.P = -1;
+      if (cc.gen != (w >> kGenShift)) continue;
     }
-    if (P2 >= sd.npasses) continue;
-    if (P2 != P) pd = load_cg(&sd.passes[P2]);
-    if (t >= pd.ntasks) continue;
-    uint64_t key = best_key(st);
-    int U = key == kNoKey ? sd.n - sd.k + 2 : (int)key_weight(key);
-    const int mid = kp.mid_pass < 0 ? sd.mid_pass_exit : kp.mid_pass;
-    *o_skip = (mid && U <= pd.L_before) ? 1 : 0;
-    *o_slot = s;
-    *o_pass = P2;
-    *o_task = t;
-    *o_U = U;
-    *o_sd = sd;
-    *o_pd = pd;
+    const unsigned long long t = w & kTaskMask;
+    if (!locate(cc, t)) continue;
+    const uint64_t key = best_key(st);
+    const int U = key == kNoKey ? cc.sd.n - cc.sd.k + 2 : (int)key_weight(key);
+    const int mid = kp.mid_pass < 0 ? cc.sd.mid_pass_exit : kp.mid_pass;
+    o->sd = cc.sd;
+    o->pd = cc.pd;
+    o->task = t - cc.pd.task_base;
+    o->slot = s;
+    o->pass = cc.P;
+    o->U = U;
+    // Early exit inside a pass: sound only if the best codeword comes from
+    // this pass or an earlier one (passes run ahead of the termination test).
+    o->skip = (mid && key != kNoKey && (int)key_pass(key) <= cc.P && U <= cc.pd.L_before) ? 1 : 0;
     rr = s;
     wait_t0 = 0;
+    cc.sleep_ns = 128;
     return kCmdRun;
   }
   if (!live && !cs.serve) return kCmdExit;
@@ -445,57 +489,89 @@ __device__ __forceinline__ int claim(const SlotDesc *slots, SlotState *states, c
       return kCmdExit;
     }
   }
-  __nanosleep(live ? 256 : 2000);
+  __nanosleep(cc.sleep_ns);  // back off: idle probes must not crowd the state's cache lines
+  if (cc.sleep_ns < 4096) cc.sleep_ns <<= 1;
   return kCmdWait;
 }
 
-// Thread 0: count a finished task; the last task of a pass decides.
-__device__ __forceinline__ void finish_task(const CtlStatic &cs, const SlotDesc &sd, const PassDesc &pd,
-                                            SlotState *st, int slot, int P) {
+constexpr int kFrontierDone = 1 << 30;  // frontier value once the code is concluded
+
+// Finish the code: certified at pass sp, or out of passes.
+__device__ __forceinline__ void conclude(const CtlStatic &cs, const SlotDesc &sd, SlotState *st, SlotAux *ax,
+                                        int slot, int sp, bool certified) {
+  const int status = (certified || sd.complete) ? 0 : 4 /* FPCODE_EBUDGET */;
+  unsigned long long entered = 0;
+  for (int P = 0; P <= sp; ++P) entered += atomicAdd(&ax->pass_count[P], 0ull);
+  const uint64_t key = ~(uint64_t)atomicOr(&st->best_key, 0ull);
+  st->entered = entered;
+  st->stop_pass = sp;
+  st->status = kDoneFlag | status;
   __threadfence();
-  unsigned long long done = atomicAdd(&st->done, 1ull) + 1ull;
-  if (done != pd.ntasks) return;
-  __threadfence();
-  if (sd.pass_times) sd.pass_times[P] = globaltimer();
-  uint64_t key = ~(uint64_t)atomicOr(&st->best_key, 0ull);
-  int U = key == kNoKey ? sd.n - sd.k + 2 : (int)key_weight(key);
-  const bool check = !sd.per_round_check || pd.round_end;
-  const bool certified = check && pd.L_after >= U;
-  if (certified || P + 1 >= sd.npasses) {
-    const int status = (certified || sd.complete) ? 0 : 4 /* FPCODE_EBUDGET */;
-    st->stop_pass = P;
-    st->status = kDoneFlag | status;
-    const unsigned long long enumerated = atomicAdd(&st->enumerated, 0ull);
-    __threadfence();
-    atomicExch(&st->finished, 1);
-    if (cs.done_host) {  // serving: post the outcome; the host may reuse the slot after seq
-      Completion *c = cs.done_host + slot;
-      c->best_key = key;
-      c->enumerated = enumerated;
-      c->status = status;
-      c->stop_pass = P;
-      __threadfence_system();
-      *(volatile unsigned long long *)&c->seq = sd.seq;
-    }
-    return;
+  atomicExch(&st->finished, 1);
+  if (cs.done_host) {  // serving: post the outcome; the host may reuse the slot after seq
+    Completion *c = cs.done_host + slot;
+    c->best_key = key;
+    c->enumerated = entered;
+    c->status = status;
+    c->stop_pass = sp;
+    __threadfence_system();
+    *(volatile unsigned long long *)&c->seq = sd.seq;
   }
-  st->done = 0;
-  __threadfence();
-  atomicExch(&st->word, ((sd.seq & kGenMask) << kGenShift) | ((unsigned long long)(P + 1) << 40));
 }
 
+// Thread 0: count a finished task of pass P.  Passes complete in any order;
+// whoever sees the frontier pass complete applies its termination test
+// (Alg. 6 line 3) with the least weight recorded in it and the passes before
+// it, and moves the frontier on.  Two CTAs may test the same pass: they
+// read the same final values and write the same results, and the
+// compare-and-swap on the frontier lets exactly one move it.
+__device__ __forceinline__ void finish_task(const CtlStatic &cs, const SlotDesc &sd, SlotState *st, SlotAux *ax,
+                                            int slot, int P, const PassDesc &pd) {
+  __threadfence();
+  const unsigned int done = atomicAdd(&ax->pass_done[P], 1u) + 1u;
+  if (done != pd.ntasks) return;
+  __threadfence();
+  for (;;) {
+    const int f = ld_vol(&st->frontier);
+    __threadfence();  // acquire: what the tester of pass f-1 wrote before moving the frontier
+    if (f >= sd.npasses || ld_vol(&st->finished)) return;
+    const PassDesc pf = f == P ? pd : load_cg(&sd.passes[f]);
+    if (atomicAdd(&ax->pass_done[f], 0u) != pf.ntasks) return;  // the frontier pass is still running
+    __threadfence();  // acquire: the records of pass f's tasks
+    const int pm = atomicOr(&ax->pass_min[f], 0);
+    const int u0 = f > 0 ? ld_vol(&ax->useq_after[f - 1]) : 0;
+    int useq = u0 ? u0 : sd.n - sd.k + 2;
+    if (pm) useq = min(useq, 256 - pm);
+    if (sd.pass_times) sd.pass_times[f] = globaltimer();
+    const bool check = !sd.per_round_check || pf.round_end;
+    const bool certified = check && pf.L_after >= useq;
+    if (certified || f + 1 >= sd.npasses) {
+      // the frontier jumps past every pass, so no later pass is ever tested
+      if (atomicCAS(&st->frontier, f, kFrontierDone) == f) conclude(cs, sd, st, ax, slot, f, certified);
+      return;
+    }
+    ax->useq_after[f] = useq;  // a second tester writes the same value here
+    __threadfence();
+    if (atomicCAS(&st->frontier, f, f + 1) != f) return;  // another CTA moved it
+  }
+}
+
+#ifndef FPK_MIN_BLOCKS
+#define FPK_MIN_BLOCKS 4  // CTAs per SM the register allocation is capped for
+#endif
+
 template <class V>
-__global__ void __launch_bounds__(kThreads) bz_kernel(const SlotDesc *__restrict__ slots, SlotState *states,
+__global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const SlotDesc *__restrict__ slots, SlotState *states,
                                                       const CtlStatic *__restrict__ ctl, CtlDyn *cdyn,
                                                       KParams kp) {
   extern __shared__ uint4 smem_raw[];
   uint64_t *bcols = reinterpret_cast<uint64_t *>(smem_raw);  // binomial columns t < kBinomCols
   uint4 *tab4 = smem_raw + kBinomBytes / 16;
   uint32_t *tab = reinterpret_cast<uint32_t *>(tab4);
-  __shared__ SlotDesc s_sd;
-  __shared__ PassDesc s_pd;
-  __shared__ int s_cmd, s_slot, s_pass, s_U, s_skip, s_stage;
-  __shared__ unsigned long long s_task, s_count, s_staged_seq;
+  __shared__ Claim s_cl;
+  __shared__ ClaimCache s_cc;
+  __shared__ int s_cmd, s_stage;
+  __shared__ unsigned long long s_count, s_staged_seq;
   __shared__ int s_staged_slot, s_staged_j;
 
   const CtlStatic cs = *ctl;
@@ -507,6 +583,10 @@ __global__ void __launch_bounds__(kThreads) bz_kernel(const SlotDesc *__restrict
     s_staged_slot = -1;
     s_staged_j = -1;
     s_staged_seq = 0;
+    s_cc.slot = -1;
+    s_cc.P = -1;
+    s_cc.gen = 0;
+    s_cc.sleep_ns = 128;
   }
   for (int i = tid; i < kBinomCols * (fpenum::kMaxK + 1); i += kThreads) {
     const int t = i / (fpenum::kMaxK + 1), n = i % (fpenum::kMaxK + 1);
@@ -520,25 +600,15 @@ __global__ void __launch_bounds__(kThreads) bz_kernel(const SlotDesc *__restrict
   __syncthreads();
   for (;;) {
     if (tid == 0) {
-      int slot = 0, pass = 0, U = 0, skip = 0;
-      unsigned long long task = 0;
-      SlotDesc sd;
-      PassDesc pd;
-      int cmd = claim(slots, states, cs, kp, cdyn, rr, wait_t0, t_start, &slot, &pass, &task, &U, &skip, &sd, &pd);
+      const int cmd = claim(slots, states, cs, kp, cdyn, rr, wait_t0, t_start, &s_cl, s_cc);
       s_cmd = cmd;
       if (cmd == kCmdRun) {
-        s_sd = sd;
-        s_pd = pd;
-        s_slot = slot;
-        s_pass = pass;
-        s_task = task;
-        s_U = U;
-        s_skip = skip;
-        s_stage = (!skip && (slot != s_staged_slot || pd.j != s_staged_j || sd.seq != s_staged_seq)) ? 1 : 0;
+        s_stage = (!s_cl.skip && (s_cl.slot != s_staged_slot || s_cl.pd.j != s_staged_j ||
+                                  s_cl.sd.seq != s_staged_seq)) ? 1 : 0;
         if (s_stage) {
-          s_staged_slot = slot;
-          s_staged_j = pd.j;
-          s_staged_seq = sd.seq;
+          s_staged_slot = s_cl.slot;
+          s_staged_j = s_cl.pd.j;
+          s_staged_seq = s_cl.sd.seq;
         }
       }
       s_count = 0;
@@ -550,22 +620,26 @@ __global__ void __launch_bounds__(kThreads) bz_kernel(const SlotDesc *__restrict
       __syncthreads();
       continue;
     }
-    const int slot = s_slot, pass = s_pass;
+    const int slot = s_cl.slot;
     if (s_stage) {
-      const int words = table_words(s_sd);
-      const uint4 *src = reinterpret_cast<const uint4 *>(s_sd.table + (size_t)s_pd.j * (size_t)words);
+      const int words = table_words(s_cl.sd);
+      const uint4 *src = reinterpret_cast<const uint4 *>(s_cl.sd.table + (size_t)s_cl.pd.j * (size_t)words);
       for (int i = tid; i < words / 4; i += kThreads) tab4[i] = __ldcg(src + i);
       __syncthreads();
     }
     unsigned long long count = 0;
-    if (!s_skip) V::run(s_sd, s_pd, pass, tab, binom, s_task, s_U, &states[slot], count);
+    SlotAux *ax = cs.aux + slot;
+    if (!s_cl.skip) V::run(s_cl.sd, s_cl.pd, s_cl.pass, tab, binom, s_cl.task, s_cl.U, &states[slot], ax, count);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) count += __shfl_xor_sync(0xffffffffu, count, o);
     if ((tid & 31) == 0 && count) atomicAdd(&s_count, count);
     __syncthreads();
     if (tid == 0) {
-      if (s_count) atomicAdd(&states[slot].enumerated, s_count);
-      finish_task(cs, s_sd, s_pd, &states[slot], slot, pass);
+      if (s_count) {
+        atomicAdd(&states[slot].enumerated, s_count);
+        atomicAdd(&ax->pass_count[s_cl.pass], s_count);
+      }
+      finish_task(cs, s_cl.sd, &states[slot], ax, slot, s_cl.pass, s_cl.pd);
     }
   }
 }

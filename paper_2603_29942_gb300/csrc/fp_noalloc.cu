@@ -94,8 +94,10 @@ extern "C" int fpcode_min_distance_noalloc(int p, int n, int k, const uint8_t *G
   const size_t off_table = a256(off_pass + P.passes.size() * sizeof(fpk::PassDesc));
   const size_t off_state = a256(off_table + P.table.size() * sizeof(uint32_t));
   const size_t dyn_bytes = a256(sizeof(fpk::SlotState) + sizeof(fpk::CtlDyn));
-  if (off_state + dyn_bytes > kNoallocScratchBytes) {
-    fph::set_error("fpcode_min_distance_noalloc: the code needs " + std::to_string(off_state + dyn_bytes) +
+  const size_t off_aux = off_state + dyn_bytes;
+  const size_t aux_bytes = a256(sizeof(fpk::SlotAux));
+  if (off_aux + aux_bytes > kNoallocScratchBytes) {
+    fph::set_error("fpcode_min_distance_noalloc: the code needs " + std::to_string(off_aux + aux_bytes) +
                    " bytes of device scratch, above the fixed 524288; use fpcode_min_distance");
     return FPCODE_EINVAL;
   }
@@ -123,6 +125,7 @@ extern "C" int fpcode_min_distance_noalloc(int p, int n, int k, const uint8_t *G
   std::vector<unsigned char> img(off_state - off_ctl, 0);
   fpk::CtlStatic cs{};
   cs.binom = reinterpret_cast<const fpenum::Binom *>(base);
+  cs.aux = reinterpret_cast<fpk::SlotAux *>(base + off_aux);
   cs.nslots = 1;
   cs.serve = 0;
   std::memcpy(&img[0], &cs, sizeof(cs));
@@ -146,7 +149,7 @@ extern "C" int fpcode_min_distance_noalloc(int p, int n, int k, const uint8_t *G
   std::memcpy(&img[off_table - off_ctl], P.table.data(), P.table.size() * sizeof(uint32_t));
 
   NA_CUDA(cudaMemcpyAsync(base + off_ctl, img.data(), img.size(), cudaMemcpyHostToDevice, st));
-  NA_CUDA(cudaMemsetAsync(base + off_state, 0, dyn_bytes, st));  // state starts at zero
+  NA_CUDA(cudaMemsetAsync(base + off_state, 0, dyn_bytes + aux_bytes, st));  // state starts at zero
   if (!P.passes.empty()) {
     const fpk::SlotDesc *slots = reinterpret_cast<const fpk::SlotDesc *>(base + off_slot);
     fpk::SlotState *states = reinterpret_cast<fpk::SlotState *>(base + off_state);
@@ -155,6 +158,7 @@ extern "C" int fpcode_min_distance_noalloc(int p, int n, int k, const uint8_t *G
     fpk::KParams kp{};
     kp.wait_limit_ns = (unsigned long long)(o.wait_limit_s * 1e9);
     kp.mid_pass = o.mid_pass_exit ? 1 : 0;
+    kp.lookahead = o.lookahead ? 1 : 0;
     void *args[] = {(void *)&slots, (void *)&states, (void *)&ctl, (void *)&dyn, (void *)&kp};
     NA_CUDA(cudaLaunchKernel(fn, dim3(ctas), dim3(fpk::kThreads), args, (size_t)smem, st));
   }
@@ -164,7 +168,7 @@ extern "C" int fpcode_min_distance_noalloc(int p, int n, int k, const uint8_t *G
 
   fph::DeviceOutcome oc{};
   oc.best_key = ~(uint64_t)state.best_key;
-  oc.enumerated = state.enumerated;
+  oc.enumerated = state.finished ? state.entered : state.enumerated;
   if (P.passes.empty()) {
     oc.best_key = fpk::kNoKey;
     oc.status = FPCODE_EBUDGET;

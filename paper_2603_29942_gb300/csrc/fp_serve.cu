@@ -68,7 +68,7 @@ struct fpcode_server {
   int smem = 0, ctas = 0, S = 0;
   char *dev = nullptr;
   size_t off_ctl = 0, off_slots = 0, off_passes = 0, off_arena = 0, arena_bytes = 0, off_states = 0,
-         off_dyn = 0, total = 0;
+         off_dyn = 0, off_aux = 0, total = 0;
   fpk::Completion *done_host = nullptr, *done_dev = nullptr;
   char *staging = nullptr;  // pinned, one region per slot
   size_t stage_per_slot = 0;
@@ -188,6 +188,8 @@ int fpcode_serve_create(const fpcode_serve_opts *opts, void *stream, fpcode_serv
   off = a256(off + S * sizeof(fpk::SlotState));
   s->off_dyn = off;
   off = a256(off + sizeof(fpk::CtlDyn));
+  s->off_aux = off;
+  off = a256(off + S * sizeof(fpk::SlotAux));
   s->total = off;
   SV_CUDA(cudaMalloc(&s->dev, s->total));
   SV_CUDA(cudaHostAlloc(&s->done_host, S * sizeof(fpk::Completion), cudaHostAllocMapped));
@@ -205,6 +207,7 @@ int fpcode_serve_create(const fpcode_serve_opts *opts, void *stream, fpcode_serv
   fpk::CtlStatic cs{};
   cs.binom = s->ctx->binom;
   cs.done_host = s->done_dev;
+  cs.aux = reinterpret_cast<fpk::SlotAux *>(s->dev + s->off_aux);
   cs.nslots = s->S;
   cs.serve = 1;
   std::memcpy(s->staging + s->off_ctl, &cs, sizeof(cs));
@@ -292,6 +295,8 @@ int fpcode_serve_submit(fpcode_server *s, const fpcode_desc *code, uint64_t *tic
   SV_CUDA(cudaMemcpyAsync(d_pass, stg + o_pass, P->passes.size() * sizeof(fpk::PassDesc), cudaMemcpyHostToDevice,
                           s->cst));
   SV_CUDA(cudaMemcpyAsync(d_desc, stg, sizeof(sd), cudaMemcpyHostToDevice, s->cst));
+  SV_CUDA(cudaMemsetAsync(s->dev + s->off_aux + (size_t)slot * sizeof(fpk::SlotAux), 0, sizeof(fpk::SlotAux),
+                          s->cst));  // per-pass minima and counts, before the state
   fpk::SlotState fresh{};
   fresh.word = (unsigned long long)(tk & fpk::kGenMask) << fpk::kGenShift;
   std::memcpy(stg + o_state, &fresh, sizeof(fresh));

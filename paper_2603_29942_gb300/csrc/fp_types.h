@@ -48,6 +48,10 @@ struct PassDesc {
   uint64_t NC;        // (p-1)^(g-2) coefficient vectors per prefix subset
   uint32_t plan_ctas; // guided: tasks per phase
   uint32_t unit;      // prefixes per work unit: b^t, aligned to the coefficient counter
+  // Tasks of all passes form one sequence: CTAs take them in order, so a
+  // pass's tasks are handed out as soon as the previous pass has none left.
+  uint32_t task_base;      // tasks of all earlier passes
+  uint32_t pad0, pad1, pad2;
 };
 
 // Words per row of the pair-signature table (Mersenne p = 3, 7): for each
@@ -81,7 +85,7 @@ FPK_HD void task_range(const PassDesc &d, uint64_t t, uint64_t *lo, uint64_t *hi
   *lo = plo + size * i / C;
   *hi = plo + size * (i + 1) / C;
 }
-static_assert(sizeof(PassDesc) == 64, "PassDesc layout");
+static_assert(sizeof(PassDesc) == 80, "PassDesc layout");
 
 // Static description of one code as the kernel sees it.
 struct SlotDesc {
@@ -98,16 +102,28 @@ struct SlotDesc {
 };
 static_assert(sizeof(SlotDesc) == 80, "SlotDesc layout");
 
-// Dynamic state of one code, device memory.
+// Dynamic state of one code, device memory (all zero = fresh).
 struct SlotState {
-  unsigned long long word;        // (generation << 48) | (pass << 40) | next task
-  unsigned long long done;        // tasks finished in the current pass
-  unsigned long long best_key;    // packed witness key (kNoKey: none yet)
-  unsigned long long enumerated;  // codewords evaluated
-  int32_t status;                 // kRunning until finished
+  unsigned long long word;        // (generation << 48) | next task of the whole schedule
+  unsigned long long best_key;    // inverted packed witness key (0: none yet)
+  unsigned long long enumerated;  // codewords evaluated, passes past the stop included
+  unsigned long long entered;     // codewords evaluated in the passes up to stop_pass
+  int32_t frontier;               // next pass whose termination test is pending
+  int32_t pad0;
+  int32_t status;                 // 0 while running, then kDoneFlag | fpcode status
   int32_t stop_pass;              // last pass entered
   int32_t finished;               // 1: nothing left to do
   int32_t pad;
+};
+
+// Per-pass bookkeeping of one code (zeroed with the state): the least
+// weight recorded in each pass (stored as 256 - w, 0: none), the running
+// minimum after each tested pass, tasks done and codewords evaluated.
+struct SlotAux {
+  int32_t pass_min[256];
+  int32_t useq_after[256];  // least weight recorded in passes <= P (written by the test of pass P)
+  uint32_t pass_done[256];
+  unsigned long long pass_count[256];
 };
 
 // Serving: the finaliser of a code posts its outcome to host-mapped memory
@@ -115,13 +131,13 @@ struct SlotState {
 struct Completion {
   unsigned long long seq;
   unsigned long long best_key;   // packed key (kNoKey: none)
-  unsigned long long enumerated;
+  unsigned long long enumerated; // codewords evaluated in the passes entered
   int32_t status;                // fpcode status
   int32_t stop_pass;
 };
 
 constexpr int32_t kRunning = -1;
-// SlotState.word = (generation << 48) | (pass << 40) | next task; the
+// SlotState.word = (generation << 48) | task index over all passes; the
 // generation is the low 16 bits of SlotDesc.seq (0 outside serving).
 constexpr uint64_t kTaskMask = (1ull << 40) - 1;
 constexpr int kGenShift = 48;

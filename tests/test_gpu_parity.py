@@ -211,3 +211,21 @@ def test_bounded_wait_reports_timeout():
     assert res2.L <= 14
     ok, _ = run(code)
     assert ok.status == B.OK and ok.d == 14
+
+
+@pytest.mark.parametrize("lookahead", [0, 1])
+@pytest.mark.parametrize("name", ["f3_n30_k15", "f7_n40_k20", "f3_n80_k40"])
+def test_lookahead_keeps_the_schedule(name, lookahead):
+    """Taking tasks of later passes while earlier ones drain leaves d, L,
+    the passes entered and their counts exactly as the sequential schedule
+    has them."""
+    code = inputs.single(name)
+    exp = golden()[name]["default"]
+    for mid in (0, 1):
+        res, _ = run(code, lookahead=lookahead, mid_pass_exit=mid)
+        assert res.status == B.OK
+        assert (res.d, res.L, res.U, res.counts, res.npasses) == (
+            exp["d"], exp["L"], exp["U"], exp["counts"], len(exp["passes"]))
+        if mid == 0:
+            assert res.enumerated == exp["evaluated"]
+        check_witness(code, res.d, res.witness)
