@@ -15,8 +15,21 @@ roofline  the enumeration kernel against the POPC issue ceiling of the SMs
 cpu_baseline  the CPU oracle (test infrastructure) on the same code, all
           host cores.
 
+Two further workloads have their own JSON line (not the default):
+  --workload batch512  512 random codes (p in {3,7}, n in 24..64, PCG64 seed 3)
+                       certified in one persistent launch
+                       (fpcode_min_distance_batch) vs one launch per code;
+                       codes/s end to end from host matrices, per-code
+                       budget --budget codewords (pass-granular).
+  --workload serve     the first --requests of 10,000 codes (p in {3,5,7},
+                       n in 20..72, PCG64 seed 4) arriving as a Poisson
+                       process at 200 requests/s, served continuously
+                       (fpcode_serve_*); codes/s and p50/p99 latency from
+                       arrival to result.
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W]
                        [--impl ours|reference] [--workload NAME]
+                       [--budget B] [--requests R]
 """
 from __future__ import annotations
 
@@ -36,6 +49,8 @@ WORKLOADS = {
     "f3_n80_k40": "F_3 [80,40] random systematic code G=[I|A], A uniform, PCG64 seed 2",
     "f7_n40_k20": "F_7 [40,20] random systematic code G=[I|A], A uniform, PCG64 seed 1",
     "f3_n30_k15": "F_3 [30,15] random systematic code G=[I|A], A uniform, PCG64 seed 0",
+    "batch512": "512 random codes, p in {3,7}, n in {24,...,64}, k = round(r n), r ~ U[1/3,2/3], PCG64 seed 3",
+    "serve": "Poisson arrivals (200/s) of random codes, p in {3,5,7}, n ~ U[20,72], k ~ U[n/3,2n/3], PCG64 seed 4",
 }
 POPC_PER_CLK_SM = 16.0   # measured by fpcode_int_peaks on GB300 (and CUDA's documented rate)
 SM_MAX_MHZ = 2070.0      # GB300 maximum SM clock
@@ -146,6 +161,127 @@ def run_reference(args, code, rank: int):
     print(json.dumps(line), flush=True)
 
 
+def _cuda(local):
+    import torch
+
+    torch.cuda.set_device(local)
+    from paper_2603_29942_gb300 import _binding as B
+    from paper_2603_29942_gb300 import build as _b
+
+    _b.build()
+    B.lib()
+    return torch, B
+
+
+def run_batch(args, rank, world, local):
+    """512 codes: one persistent batched launch vs one launch per code."""
+    from paper_2603_29942_gb300 import inputs
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle is timed on the single-code "
+                              "workloads only; batch512 has no reference arm"}))
+        return
+    torch, B = _cuda(local)
+    codes = inputs.batch_codes(512)
+    budget = int(args.budget)
+    budgets = [budget] * len(codes)
+    stream = torch.cuda.Stream()
+    for _ in range(args.warmup):
+        res = B.fpcode_min_distance_batch(codes, stream, budgets=budgets, want_witness=False)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            res = B.fpcode_min_distance_batch(codes, stream, budgets=budgets, want_witness=True)
+        t_batch = (time.perf_counter() - t0) / args.steps
+        # the plain form: one launch per code, same budget
+        t0 = time.perf_counter()
+        for c in codes:
+            B.fpcode_min_distance_batch([c], stream, budgets=[budget], want_witness=True)
+        t_single = time.perf_counter() - t0
+    certified = sum(r.status == B.OK for r in res)
+    work = sum(r.enumerated for r in res)
+    line = {
+        "metric": "codes_per_s", "value": world * len(codes) / t_batch, "unit": "codes/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_batch, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "batch512", "description": WORKLOADS["batch512"], "budget_per_code": budget,
+                   "certified": certified, "budget_limited": len(codes) - certified,
+                   "codewords_per_step": work, "kernel_ms": res[0].t_kernel_ms,
+                   "timing": "end to end from host matrices (host preparation on all cores, H2D, one launch, D2H)"},
+        "per_code": {"codes_per_s": len(codes) / t_single, "ms_total": 1e3 * t_single,
+                     "form": "fpcode_min_distance_batch on one code at a time (one launch per code)"},
+        "batched_over_per_code": t_single / t_batch,
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_serve(args, rank, world, local):
+    """Continuous batching of Poisson arrivals; latency from arrival to result."""
+    from paper_2603_29942_gb300 import inputs
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle is timed on the single-code "
+                              "workloads only; serve has no reference arm"}))
+        return
+    torch, B = _cuda(local)
+    codes, arrivals = inputs.serve_codes()
+    n_req = min(args.requests, len(codes))
+    codes, arrivals = codes[:n_req], arrivals[:n_req]
+    budget = int(args.budget)
+    stream = torch.cuda.Stream()
+    srv = B.fpcode_serve_create(B.fpcode_serve_opts_default(slots=128), stream)
+    # warm-up: a few codes through the server
+    for c in codes[:8]:
+        B.fpcode_serve_submit(srv, c, budget=budget)
+    B.fpcode_serve_drain(srv)
+    B.fpcode_serve_poll(srv)
+    pending = list(range(n_req))
+    ticket_of = {}
+    done_at = {}
+    results = {}
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        while len(done_at) < n_req:
+            now = time.perf_counter() - t0
+            while pending and arrivals[pending[0]] <= now:
+                i = pending[0]
+                t = B.fpcode_serve_submit(srv, codes[i], budget=budget)
+                if t is None:
+                    break  # no slot or memory free: the request waits (its latency runs)
+                ticket_of[t] = i
+                pending.pop(0)
+            for t, r in B.fpcode_serve_poll(srv, want_witness=False):
+                i = ticket_of.pop(t)
+                done_at[i] = time.perf_counter() - t0
+                results[i] = r
+            if not pending and not ticket_of:
+                break
+            time.sleep(0.0002)
+        elapsed = time.perf_counter() - t0
+    lat = sorted((done_at[i] - arrivals[i]) * 1e3 for i in done_at)
+    certified = sum(r.status == B.OK for r in results.values())
+    pct = lambda q: lat[min(len(lat) - 1, int(q * len(lat)))]
+    line = {
+        "metric": "codes_per_s", "value": world * n_req / elapsed, "unit": "codes/s", "n_gpus": world,
+        "steps": 1, "warmup": 1, "ms_per_step": 1e3 * elapsed, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "serve", "description": WORKLOADS["serve"], "requests": n_req,
+                   "budget_per_code": budget, "certified": certified, "arrival_span_s": float(arrivals[-1])},
+        "latency_ms": {"p50": pct(0.50), "p90": pct(0.90), "p99": pct(0.99), "max": lat[-1]},
+        "gpu_launches": None,
+        "clocks": clk.summary(),
+    }
+    B.fpcode_serve_destroy(srv)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -154,12 +290,18 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="f3_n80_k40", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--budget", type=float, default=1e8, help="per-code budget (batch512, serve)")
+    ap.add_argument("--requests", type=int, default=2000, help="requests served (serve)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
     from paper_2603_29942_gb300 import inputs
 
     rank, world, local = dist_env()
+    if args.workload == "batch512":
+        return run_batch(args, rank, world, local)
+    if args.workload == "serve":
+        return run_serve(args, rank, world, local)
     code = inputs.single(args.workload)
     if args.impl == "reference":
         run_reference(args, code, rank)

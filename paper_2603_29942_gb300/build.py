@@ -55,7 +55,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
                      "-c", os.path.join(CSRC, src), "-o", obj])
     for src in CPP_SOURCES:
         obj = os.path.join(BUILD, src.replace(".cpp", ".o"))
-        jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", "-Wno-unknown-pragmas", "-I", INCLUDE, "-c", os.path.join(CSRC, src),
+        jobs.append(["g++", "-O3", "-std=c++17", "-fPIC", "-Wall", "-Wno-unknown-pragmas", "-I", INCLUDE, "-c", os.path.join(CSRC, src),
                      "-o", obj])
 
     def run(cmd):

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <thread>
 #include <chrono>
 #include <cstdio>
 #include <cstring>
@@ -453,11 +455,24 @@ int fpcode_min_distance_batch(int num, const fpcode_desc *codes, void *stream, c
   if (opts) o = *opts;
   std::vector<std::unique_ptr<fph::Prepared>> preps(num);
   std::vector<int> status(num, FPCODE_OK);
-  for (int i = 0; i < num; ++i) {
-    preps[i].reset(new fph::Prepared());
-    fpcode_opts oi = o;
-    if (codes[i].budget) oi.budget = codes[i].budget;
-    status[i] = fph::prepare(codes[i].p, codes[i].n, codes[i].k, codes[i].G, oi, preps[i].get());
+  {
+    // host preparation of the codes, spread over the host's cores
+    const int nth = std::max(1, std::min<int>((int)std::thread::hardware_concurrency(), (num + 7) / 8));
+    std::atomic<int> next{0};
+    auto work = [&]() {
+      for (;;) {
+        const int i = next.fetch_add(1);
+        if (i >= num) break;
+        preps[i].reset(new fph::Prepared());
+        fpcode_opts oi = o;
+        if (codes[i].budget) oi.budget = codes[i].budget;
+        status[i] = fph::prepare(codes[i].p, codes[i].n, codes[i].k, codes[i].G, oi, preps[i].get());
+      }
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nth; ++t) pool.emplace_back(work);
+    work();
+    for (auto &th : pool) th.join();
   }
   const double t_prep = ms_since(t0);
   DevCtx *c;
