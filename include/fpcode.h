@@ -59,7 +59,7 @@ enum fpcode_status {
 /* Search options.  fpcode_opts_default() fills the defaults shown. */
 typedef struct fpcode_opts {
   int per_round_check; /* 0: test L >= U after every pass (default);
-                          1: only after each full round g (Alg. 6 line 3) */
+                          1: only after each full round g (Alg. 6) */
   int defer;           /* 1 (default): a rank-deficient Gamma_j is first
                           enumerated in round g = k - k_j (it cannot raise L
                           earlier), catching up its levels 1..g */

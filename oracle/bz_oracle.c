@@ -26,18 +26,18 @@
  *                       (Sec. 4.3) and early termination (Sec. 4.4).
  *
  * Readings of the paper taken here (the paper is silent or ambiguous):
- *   - Alg. 6 line 5 enumerates c in F_2^k of weight g (copied from the binary
+ *   - Alg. 6 enumerates, per pass, c in F_2^k of weight g (carried over from the binary
  *     algorithm); over F_p this is every c in F_p^k with exactly g nonzero
  *     entries, normalised projectively, C(k,g)(p-1)^(g-1) codewords per pass.
  *   - Lower bound after any pass: L = sum_i max(0, e_i + 1 - (k - k_i)),
  *     e_i = highest level completed for Gamma_i.  After a full round with
- *     only Gamma_m rank-deficient this is Alg. 6 line 7.
- *   - Termination when L >= U (Alg. 6 line 3); checked after every pass by
+ *     only Gamma_m rank-deficient this is the bound of Alg. 6.
+ *   - Termination when L >= U (the test of Alg. 6); checked after every pass by
  *     default, or only after each full round (per_round_check = 1).
  *   - A rank-deficient Gamma_j cannot raise L before level k - k_j; with
  *     defer = 1 it is first enumerated in round g = k - k_j, catching up all
  *     of its levels 1..g.
- *   - U starts at the Singleton bound n-k+1 (Alg. 6 line 1); a codeword of
+ *   - U starts at the Singleton bound n-k+1 (the start of Alg. 6); a codeword of
  *     that weight is still recorded while no witness is held, so a witness
  *     always exists at the end.
  *   - Budget: a pass is not entered if it would take the number of
@@ -263,7 +263,7 @@ int oracle_info_sets(int p, int n, int k, const uint8_t *G, int max_m, int *m_ou
 }
 
 /* ------------------------------------------------------------------ */
-/* One pass (g, j) of Alg. 6 line 5.                                    */
+/* One pass (g, j) of Alg. 6: every codeword of weight-g combinations. */
 /* ------------------------------------------------------------------ */
 
 /* Every g-subset T of the rows of Gamma_j in lexicographic order, with
@@ -438,7 +438,7 @@ uint64_t oracle_pass_size(int p, int k, int g) {
   return c;
 }
 
-/* Lower bound from the levels completed so far (reading of Alg. 6 line 7). */
+/* Lower bound from the levels completed so far (reading of the bound in Alg. 6). */
 static int lower_bound(int m, const int *e, const int *kj, int k) {
   int L = 0;
   for (int i = 0; i < m; ++i) {

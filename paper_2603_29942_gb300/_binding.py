@@ -306,29 +306,58 @@ def fpcode_min_distance_noalloc(p: int, n: int, k: int, G, stream=None) -> tuple
     return d.value, w
 
 
-def fpcode_min_distance_batch(codes, stream=None, opts: fpcode_opts | None = None, budgets=None,
-                              want_witness: bool = True) -> list[Result]:
-    """codes: objects with p, n, k, G (e.g. inputs.Code)."""
-    num = len(codes)
-    mats = [_matrix(c.G) for c in codes]
-    descs = (fpcode_desc * max(num, 1))()
-    for i, (c, G) in enumerate(zip(codes, mats)):
-        descs[i].p, descs[i].n, descs[i].k = int(c.p), int(c.n), int(c.k)
-        descs[i].G = G.ctypes.data_as(_U8P)
-        descs[i].budget = int(budgets[i]) if budgets is not None else 0
-    res = (fpcode_result * max(num, 1))()
-    total_n = sum(int(c.n) for c in codes)
-    wit = np.zeros(max(total_n, 1), dtype=np.uint8)
-    _check(lib().fpcode_min_distance_batch(num, descs, _stream(stream), ctypes.byref(opts) if opts else None, res,
-                                           wit.ctypes.data_as(_U8P) if want_witness else None),
-           "fpcode_min_distance_batch")
+_DESC_DT = np.dtype([("p", "<i4"), ("n", "<i4"), ("k", "<i4"), ("reserved", "<i4"), ("G", "<u8"), ("budget", "<u8")])
+_RESULT_DT = np.dtype(fpcode_result)
+
+
+def _results_of(res: np.ndarray, ks, ns, wit) -> list[Result]:
+    """Result objects from a structured array of fpcode_result (field by
+    field, vectorised, so that a large batch costs little Python)."""
+    cols = {f: res[f].tolist() for f in ("status", "d", "L", "U", "m", "npasses", "enumerated", "t_prepare_ms",
+                                         "t_kernel_ms", "t_total_ms")}
+    counts, kj = res["counts"], res["kj"]
     out = []
     off = 0
-    for i, c in enumerate(codes):
-        w = wit[off:off + int(c.n)].copy() if want_witness else None
-        off += int(c.n)
-        out.append(Result.of(res[i], int(c.k), w))
+    for i, (k, n) in enumerate(zip(ks, ns)):
+        w = wit[off:off + n] if wit is not None else None
+        off += n
+        m = cols["m"][i]
+        out.append(Result(cols["status"][i], cols["d"][i], cols["L"][i], cols["U"][i], m, cols["npasses"][i],
+                          cols["enumerated"][i], counts[i, :k + 1].tolist(), kj[i, :max(m, 0)].tolist(),
+                          cols["t_prepare_ms"][i], cols["t_kernel_ms"][i], cols["t_total_ms"][i], w))
     return out
+
+
+def fpcode_min_distance_batch(codes, stream=None, opts: fpcode_opts | None = None, budgets=None,
+                              want_witness: bool = True) -> list[Result]:
+    """codes: objects with p, n, k, G (e.g. inputs.Code).  The codes'
+    matrices are packed into one buffer and the descriptors and results are
+    numpy structured arrays with the C layouts, so the call's Python cost
+    stays small next to the search."""
+    num = len(codes)
+    ps = [int(c.p) for c in codes]
+    ns = [int(c.n) for c in codes]
+    ks = [int(c.k) for c in codes]
+    mats = [np.asarray(c.G, dtype=np.uint8).reshape(-1) for c in codes]
+    for G, n, k in zip(mats, ns, ks):
+        if G.size != n * k:
+            raise ValueError("a generator matrix is not k x n")
+    buf = np.concatenate(mats) if num else np.zeros(1, dtype=np.uint8)
+    offs = np.zeros(num + 1, dtype=np.uint64)
+    np.cumsum(np.asarray([n * k for n, k in zip(ns, ks)], dtype=np.uint64), out=offs[1:])
+    descs = np.zeros(max(num, 1), dtype=_DESC_DT)
+    descs["p"][:num], descs["n"][:num], descs["k"][:num] = ps, ns, ks
+    descs["G"][:num] = np.uint64(buf.ctypes.data) + offs[:-1]
+    if budgets is not None:
+        descs["budget"][:num] = np.asarray(budgets, dtype=np.uint64)
+    res = np.zeros(max(num, 1), dtype=_RESULT_DT)
+    wit = np.zeros(max(sum(ns), 1), dtype=np.uint8) if want_witness else None
+    _check(lib().fpcode_min_distance_batch(num, ctypes.cast(descs.ctypes.data, ctypes.POINTER(fpcode_desc)),
+                                           _stream(stream), ctypes.byref(opts) if opts else None,
+                                           ctypes.cast(res.ctypes.data, ctypes.POINTER(fpcode_result)),
+                                           wit.ctypes.data_as(_U8P) if want_witness else None),
+           "fpcode_min_distance_batch")
+    return _results_of(res[:num], ks, ns, wit)
 
 
 def fpcode_int_peaks(stream=None) -> dict:

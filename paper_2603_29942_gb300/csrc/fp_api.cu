@@ -138,7 +138,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // ---------------------------------------------------------------------------
 struct Layout {
   size_t off_ctl = 0, off_slots = 0, off_passes = 0, off_tables = 0, static_bytes = 0;
-  size_t off_states = 0, dyn_bytes = 0, off_aux = 0, aux_bytes = 0, off_times = 0, total = 0;
+  size_t off_states = 0, dyn_bytes = 0, off_aux = 0, aux_bytes = 0, off_flags = 0, off_times = 0, total = 0;
   std::vector<size_t> pass_off, table_off;
 };
 
@@ -164,7 +164,8 @@ Layout make_layout(const std::vector<const fph::Prepared *> &codes) {
   L.off_states = o;
   L.dyn_bytes = align256(ns * sizeof(SlotState) + sizeof(CtlDyn));  // read back after a search
   L.off_aux = o + L.dyn_bytes;
-  L.aux_bytes = align256(ns * sizeof(fpk::SlotAux));                  // zeroed, never read back
+  L.off_flags = L.off_aux + align256(ns * sizeof(fpk::SlotAux));
+  L.aux_bytes = L.off_flags - L.off_aux + align256((ns + 3) / 4 * 16);  // aux and flags: zeroed, never read back
   L.off_times = L.off_aux + L.aux_bytes;  // per-pass end times of a single code (diagnostics)
   L.total = L.off_times + (fpk::kMaxPasses + 1) * sizeof(unsigned long long);
   return L;
@@ -176,6 +177,7 @@ void fill_static(const Layout &L, const std::vector<const fph::Prepared *> &code
   CtlStatic cs{};
   cs.binom = c.binom;
   cs.aux = reinterpret_cast<fpk::SlotAux *>(d + L.off_aux);
+  cs.slot_flags = reinterpret_cast<uint32_t *>(d + L.off_flags);
   cs.nslots = (int)codes.size();
   cs.serve = serve;
   std::memcpy(h + L.off_ctl, &cs, sizeof(cs));

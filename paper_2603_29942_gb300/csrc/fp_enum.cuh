@@ -39,9 +39,16 @@ namespace fpenum {
 
 constexpr int kMaxK = 64;
 
+// Columns t < kBinomCols of the table are all the enumeration needs on the
+// GPU (t <= g - 2 and g is capped well below 26).
+constexpr int kBinomCols = 24;
+
 // Binomial table C(n, t), 0 <= t <= n <= 64 (C(64,32) < 2^63).  The
-// enumeration functions take any accessor B with B(n, t) = C(n, t).
+// enumeration functions take any accessor B with B(n, t) = C(n, t).  The
+// first kBinomCols columns are stored a second time, t-major, so that a
+// CTA copies them into shared memory with plain coalesced 16-byte loads.
 struct Binom {
+  uint64_t cols[kBinomCols][kMaxK + 1];  // cols[t][n] = C(n, t); 12480 bytes, a multiple of 16
   uint64_t c[kMaxK + 1][kMaxK + 1];
   FP_HD uint64_t operator()(int n, int t) const { return c[n][t]; }
 };
@@ -59,6 +66,8 @@ inline void fill_binom(Binom *b) {
     b->c[n][0] = 1;
     for (int t = 1; t <= n; ++t) b->c[n][t] = b->c[n - 1][t - 1] + (t <= n - 1 ? b->c[n - 1][t] : 0);
   }
+  for (int t = 0; t < kBinomCols; ++t)
+    for (int n = 0; n <= kMaxK; ++n) b->cols[t][n] = b->c[n][t];
 }
 
 FP_HD int ctz64(uint64_t x) {

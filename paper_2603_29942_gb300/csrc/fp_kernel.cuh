@@ -36,9 +36,20 @@ struct CtlStatic {
   const fpenum::Binom *binom;
   Completion *done_host;  // serving: host-mapped completion records (else null)
   SlotAux *aux;           // per-slot pass minima and counts (zeroed with the states)
+  uint32_t *slot_flags;   // per slot, padded to a multiple of four: see kSlotFinished
   int32_t nslots;
   int32_t serve;          // serving: slots appear while the kernel runs
 };
+
+// A slot's flag word: (generation << 16) | kSlotFinished | kSlotExhausted.
+// Claims read the flags four slots per 16-byte load and skip the slots
+// with a bit set.  The host writes generation << 16 when it installs a
+// code (zero for one-shot launches); a CTA that finds the code's task
+// sequence used up sets kSlotExhausted by compare-and-swap on that exact
+// value, so a late writer from an earlier code cannot mark its successor.
+constexpr uint32_t kSlotFinished = 1u;
+constexpr uint32_t kSlotExhausted = 2u;
+__host__ __device__ inline uint32_t slot_flag_gen(unsigned long long gen) { return (uint32_t)(gen & 0xFFFFull) << 16; }
 
 // Per-launch limits, passed by value.
 struct KParams {
@@ -57,7 +68,7 @@ struct CtlDyn {
 
 // Shared memory: binomial columns C(n, t), t < kBinomCols, then the staged
 // table of one information set.
-constexpr int kBinomCols = 24;
+constexpr int kBinomCols = fpenum::kBinomCols;
 constexpr int kBinomBytes = kBinomCols * (fpenum::kMaxK + 1) * 8;  // 12480, a multiple of 16
 
 // Words of one information set's table: multiples, then pair signatures.
@@ -160,13 +171,12 @@ __device__ __forceinline__ int leaf_weight(const uint32_t (&s)[R * W], const uin
 }
 
 // Record a candidate codeword: the code's packed best key and the least
-// weight of its pass.  Returns the (possibly lowered) bound U.
-__device__ __forceinline__ int record(SlotState *st, SlotAux *ax, int pass, uint64_t key) {
+// weight of its pass.  Both are reductions whose result is not waited for:
+// the caller lowers its own bound to the recorded weight and takes up the
+// other CTAs' records when it next reads the best key.
+__device__ __forceinline__ void record(SlotState *st, SlotAux *ax, int pass, uint64_t key) {
   atomicMax(&ax->pass_min[pass], 256 - (int)key_weight(key));
-  unsigned long long old = atomicMax(&st->best_key, (unsigned long long)~key);
-  uint64_t best = ~(uint64_t)old;
-  if (key < best) best = key;
-  return (int)key_weight(best);
+  atomicMax(&st->best_key, (unsigned long long)~key);
 }
 
 // ---------------------------------------------------------------------------
@@ -264,9 +274,16 @@ __device__ void task_prefixes(const SlotDesc &sd, const PassDesc &pd, int pass, 
 
   for (uint64_t step = 0; step < pl; ++step) {
     if ((step & 15) == 15) {
-      // a finished code only has tasks of passes past its stop left: drop them
-      int fin = (threadIdx.x & 31) == 0 ? ld_vol(&st->finished) : 0;
+      // a finished code only has tasks of passes past its stop left: drop
+      // them; else take up the best weight recorded anywhere since
+      int fin = 0, ub = 0;
+      if ((threadIdx.x & 31) == 0) {
+        fin = ld_vol(&st->finished);
+        const uint64_t key = best_key(st);
+        ub = key == kNoKey ? 255 : (int)key_weight(key);
+      }
       if (__shfl_sync(0xffffffffu, fin, 0)) break;
+      thr = min(thr, __shfl_sync(0xffffffffu, ub, 0) - g + 1);
     }
     const bool act = I < Iend;
     const int mlane = act ? pf.m : k;
@@ -310,10 +327,9 @@ __device__ void task_prefixes(const SlotDesc &sd, const PassDesc &pd, int pass, 
             uint32_t e[RWP];
             load_entry<RWP>(tab, x * b + (p - c - 1), e);
             const int wr = leaf_weight<R, W>(s, e);
-            if (wr < thr) {
-              const int newU =
-                  record(st, ax, pass, make_key((uint32_t)(g + wr), (uint32_t)pass, I, (uint32_t)x, (uint32_t)c));
-              thr = newU - g + 1;
+            if (wr < thr) {  // weights up to g + wr stay of interest: ties decide the witness by key
+              record(st, ax, pass, make_key((uint32_t)(g + wr), (uint32_t)pass, I, (uint32_t)x, (uint32_t)c));
+              thr = wr + 1;
             }
           }
         }
@@ -392,6 +408,8 @@ struct Claim {
   PassDesc pd;              // the task's pass
   unsigned long long task;  // task index within the pass
   int slot, pass, U, skip;
+  unsigned int ndone;       // tasks of the pass this claim completes (skipped runs: more than one)
+  unsigned int pad;
 };
 
 // Thread 0's cache of the descriptors it read last (one slot and pass), so
@@ -405,18 +423,75 @@ struct ClaimCache {
   unsigned int sleep_ns;
 };
 
-// Pass of global task t, searching forward from the cached pass.
+// Pass of global task t: the cached pass, the next one, else a binary
+// search over the passes' task_base fields.
 __device__ __forceinline__ bool locate(ClaimCache &cc, unsigned long long t) {
-  if (cc.P < 0 || t < cc.pd.task_base) {
-    cc.P = 0;
-    cc.pd = load_cg(&cc.sd.passes[0]);
-  }
-  while (t >= (unsigned long long)cc.pd.task_base + cc.pd.ntasks) {
+  if (cc.P >= 0 && t >= cc.pd.task_base) {
+    if (t < (unsigned long long)cc.pd.task_base + cc.pd.ntasks) return true;
     if (cc.P + 1 >= cc.sd.npasses) return false;
-    ++cc.P;
-    cc.pd = load_cg(&cc.sd.passes[cc.P]);
+    const PassDesc nx = load_cg(&cc.sd.passes[cc.P + 1]);
+    if (t < (unsigned long long)nx.task_base + nx.ntasks) {
+      ++cc.P;
+      cc.pd = nx;
+      return true;
+    }
   }
+  const PassDesc last = load_cg(&cc.sd.passes[cc.sd.npasses - 1]);
+  if (t >= (unsigned long long)last.task_base + last.ntasks) {
+    cc.P = cc.sd.npasses - 1;
+    cc.pd = last;
+    return false;
+  }
+  int lo = 0, hi = cc.sd.npasses - 1;  // the pass with the largest task_base <= t
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldcg(&cc.sd.passes[mid].task_base) <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  cc.P = lo;
+  cc.pd = load_cg(&cc.sd.passes[lo]);
   return true;
+}
+
+// Mark the slot's task sequence used up, for the code of generation gen only.
+__device__ __forceinline__ void mark_exhausted(const CtlStatic &cs, int s, unsigned long long gen) {
+  const uint32_t g = slot_flag_gen(gen);
+  atomicCAS(&cs.slot_flags[s], g, g | kSlotExhausted);
+}
+
+// Thread 0: fill in the claim of task t (global index, already located in
+// cc.P) of slot s.  A task the skip rule drops needs no work; every later
+// task of the pass is then droppable too, so the rest of the pass is taken
+// in the same claim by compare-and-swap on the code's own generation.
+__device__ __forceinline__ void take(SlotState *st, const KParams &kp, int s, unsigned long long w, uint64_t key,
+                                    Claim *o, ClaimCache &cc) {
+  const unsigned long long t = w & kTaskMask;
+  const int U = key == kNoKey ? cc.sd.n - cc.sd.k + 2 : (int)key_weight(key);
+  const int mid = kp.mid_pass < 0 ? cc.sd.mid_pass_exit : kp.mid_pass;
+  o->sd = cc.sd;
+  o->pd = cc.pd;
+  o->task = t - cc.pd.task_base;
+  o->slot = s;
+  o->pass = cc.P;
+  o->U = U;
+  // Early exit inside a pass: sound only if the best codeword comes from
+  // this pass or an earlier one (passes run ahead of the termination test).
+  o->skip = (mid && key != kNoKey && (int)key_pass(key) <= cc.P && U <= cc.pd.L_before) ? 1 : 0;
+  o->ndone = 1;
+  if (o->skip) {
+    const unsigned long long end = (unsigned long long)cc.pd.task_base + cc.pd.ntasks;
+    unsigned long long cur = w + 1;
+    for (int tries = 0; tries < 4; ++tries) {
+      if ((cur >> kGenShift) != cc.gen || (cur & kTaskMask) >= end) break;
+      const unsigned long long want = cur - (cur & kTaskMask) + end;
+      const unsigned long long prev = atomicCAS(&st->word, cur, want);
+      if (prev == cur) {
+        o->ndone += (unsigned int)(end - (cur & kTaskMask));
+        break;
+      }
+      cur = prev;
+    }
+  }
 }
 
 // Thread 0: claim the next task of any live code.
@@ -429,54 +504,87 @@ __device__ __forceinline__ int claim(const SlotDesc *slots, SlotState *states, c
     atomicExch(&cd->err, 2);
     return kCmdExit;
   }
-  bool live = false;
-  for (int probe = 0; probe < nslots; ++probe) {
-    int s = rr + probe;
-    if (s >= nslots) s -= nslots;
+  // Fast path: the slot served last, descriptors cached.  The task counter,
+  // the finished flag and the best key are read in one round trip.  A task
+  // taken from a code that has finished is dropped (nothing is left to
+  // count for it); one taken from a newer code in the slot is run.
+  if (kp.lookahead && cc.slot >= 0 && cc.P >= 0) {
+    const int s = cc.slot;
     SlotState *st = &states[s];
-    if (ld_vol(&st->finished)) continue;
-    unsigned long long w = ld_vol(&st->word);
-    const unsigned long long wgen = w >> kGenShift;
-    if (cc.slot != s || cc.gen != wgen) {
+    unsigned long long w = atomicAdd(&st->word, 1ull);
+    int fin = ld_vol(&st->finished);
+    uint64_t key = best_key(st);
+    if ((w >> kGenShift) != cc.gen) {
       __threadfence();  // the descriptor was written before the state was reset
       cc.sd = load_cg(&slots[s]);
-      cc.slot = s;
       cc.gen = cc.sd.seq & kGenMask;
       cc.P = -1;
+      fin = ld_vol(&st->finished);
+      key = best_key(st);
     }
-    if (cc.sd.npasses <= 0) continue;
-    live = true;
-    if (wgen != cc.gen) continue;  // slot in transition between two codes
-    if (!locate(cc, w & kTaskMask)) continue;  // every task handed out
-    if (!kp.lookahead && cc.P > ld_vol(&st->frontier)) continue;  // one pass at a time
-    w = atomicAdd(&st->word, 1ull);
-    if ((w >> kGenShift) != cc.gen) {
-      // the slot now holds a newer code; its descriptor was written before
-      // its state, so re-reading it gives the code this task belongs to
-      __threadfence();
-      cc.sd = load_cg(&slots[s]);
-      cc.gen = cc.sd.seq & kGenMask;
-      cc.P = -1;
-      if (cc.gen != (w >> kGenShift)) continue;
+    if ((w >> kGenShift) == cc.gen && cc.sd.npasses > 0 && !fin) {
+      if (locate(cc, w & kTaskMask)) {
+        take(st, kp, s, w, key, o, cc);
+        rr = s;
+        wait_t0 = 0;
+        cc.sleep_ns = 128;
+        return kCmdRun;
+      }
+      mark_exhausted(cs, s, cc.gen);
     }
-    const unsigned long long t = w & kTaskMask;
-    if (!locate(cc, t)) continue;
-    const uint64_t key = best_key(st);
-    const int U = key == kNoKey ? cc.sd.n - cc.sd.k + 2 : (int)key_weight(key);
-    const int mid = kp.mid_pass < 0 ? cc.sd.mid_pass_exit : kp.mid_pass;
-    o->sd = cc.sd;
-    o->pd = cc.pd;
-    o->task = t - cc.pd.task_base;
-    o->slot = s;
-    o->pass = cc.P;
-    o->U = U;
-    // Early exit inside a pass: sound only if the best codeword comes from
-    // this pass or an earlier one (passes run ahead of the termination test).
-    o->skip = (mid && key != kNoKey && (int)key_pass(key) <= cc.P && U <= cc.pd.L_before) ? 1 : 0;
-    rr = s;
-    wait_t0 = 0;
-    cc.sleep_ns = 128;
-    return kCmdRun;
+  }
+  bool live = false;
+  // four slot flags per load, from the group of the slot served last
+  const int ngroups = (nslots + 3) >> 2;
+  int q = rr >> 2;
+  for (int qi = 0; qi < ngroups; ++qi, ++q) {
+    if (q >= ngroups) q = 0;
+    const uint4 f4 = __ldcg(reinterpret_cast<const uint4 *>(cs.slot_flags) + q);
+    const uint32_t fl[4] = {f4.x, f4.y, f4.z, f4.w};
+#pragma unroll 1
+    for (int b = 0; b < 4; ++b) {
+      const int s = 4 * q + b;
+      if (s >= nslots) break;
+      if (fl[b] & (kSlotFinished | kSlotExhausted)) continue;
+      SlotState *st = &states[s];
+      if (ld_vol(&st->finished)) continue;
+      unsigned long long w = ld_vol(&st->word);
+      const unsigned long long wgen = w >> kGenShift;
+      if (cc.slot != s || cc.gen != wgen) {
+        __threadfence();  // the descriptor was written before the state was reset
+        cc.sd = load_cg(&slots[s]);
+        cc.slot = s;
+        cc.gen = cc.sd.seq & kGenMask;
+        cc.P = -1;
+      }
+      if (cc.sd.npasses <= 0) continue;
+      live = true;
+      if (wgen != cc.gen) continue;  // slot in transition between two codes
+      if (!locate(cc, w & kTaskMask)) {  // every task handed out
+        mark_exhausted(cs, s, wgen);
+        continue;
+      }
+      if (!kp.lookahead && cc.P > ld_vol(&st->frontier)) continue;  // one pass at a time
+      w = atomicAdd(&st->word, 1ull);
+      if ((w >> kGenShift) != cc.gen) {
+        // the slot now holds a newer code; its descriptor was written before
+        // its state, so re-reading it gives the code this task belongs to
+        __threadfence();
+        cc.sd = load_cg(&slots[s]);
+        cc.gen = cc.sd.seq & kGenMask;
+        cc.P = -1;
+        if (cc.gen != (w >> kGenShift)) continue;
+      }
+      if (!locate(cc, w & kTaskMask)) {
+        mark_exhausted(cs, s, cc.gen);
+        continue;
+      }
+      take(st, kp, s, w, best_key(st), o, cc);
+      rr = s;
+      wait_t0 = 0;
+      cc.sleep_ns = 128;
+      return kCmdRun;
+    }
   }
   if (!live && !cs.serve) return kCmdExit;
   if (ld_vol(&cd->err)) return kCmdExit;
@@ -508,6 +616,7 @@ __device__ __forceinline__ void conclude(const CtlStatic &cs, const SlotDesc &sd
   st->status = kDoneFlag | status;
   __threadfence();
   atomicExch(&st->finished, 1);
+  atomicOr(&cs.slot_flags[slot], kSlotFinished);
   if (cs.done_host) {  // serving: post the outcome; the host may reuse the slot after seq
     Completion *c = cs.done_host + slot;
     c->best_key = key;
@@ -521,14 +630,14 @@ __device__ __forceinline__ void conclude(const CtlStatic &cs, const SlotDesc &sd
 
 // Thread 0: count a finished task of pass P.  Passes complete in any order;
 // whoever sees the frontier pass complete applies its termination test
-// (Alg. 6 line 3) with the least weight recorded in it and the passes before
+// (Alg. 6) with the least weight recorded in it and the passes before
 // it, and moves the frontier on.  Two CTAs may test the same pass: they
 // read the same final values and write the same results, and the
 // compare-and-swap on the frontier lets exactly one move it.
 __device__ __forceinline__ void finish_task(const CtlStatic &cs, const SlotDesc &sd, SlotState *st, SlotAux *ax,
-                                            int slot, int P, const PassDesc &pd) {
+                                            int slot, int P, const PassDesc &pd, unsigned int ndone) {
   __threadfence();
-  const unsigned int done = atomicAdd(&ax->pass_done[P], 1u) + 1u;
+  const unsigned int done = atomicAdd(&ax->pass_done[P], ndone) + ndone;
   if (done != pd.ntasks) return;
   __threadfence();
   for (;;) {
@@ -588,9 +697,10 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
     s_cc.gen = 0;
     s_cc.sleep_ns = 128;
   }
-  for (int i = tid; i < kBinomCols * (fpenum::kMaxK + 1); i += kThreads) {
-    const int t = i / (fpenum::kMaxK + 1), n = i % (fpenum::kMaxK + 1);
-    bcols[i] = cs.binom->c[n][t];
+  {
+    static_assert(kBinomBytes == sizeof(cs.binom->cols), "staged binomial columns");
+    const uint4 *bsrc = reinterpret_cast<const uint4 *>(cs.binom->cols);
+    for (int i = tid; i < kBinomBytes / 16; i += kThreads) smem_raw[i] = __ldg(bsrc + i);
   }
   const fpenum::BinomCols binom{bcols};
   if (blockIdx.x == 0 && tid == 0 && cs.nslots == 1) {
@@ -639,7 +749,7 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
         atomicAdd(&states[slot].enumerated, s_count);
         atomicAdd(&ax->pass_count[s_cl.pass], s_count);
       }
-      finish_task(cs, s_cl.sd, &states[slot], ax, slot, s_cl.pass, s_cl.pd);
+      finish_task(cs, s_cl.sd, &states[slot], ax, slot, s_cl.pass, s_cl.pd, s_cl.ndone);
     }
   }
 }

@@ -87,7 +87,7 @@ extern "C" int fpcode_min_distance_noalloc(int p, int n, int k, const uint8_t *G
   int s = fph::prepare(p, n, k, G, o, &P);
   if (s) return s;
 
-  // layout inside the array: [binom][CtlStatic][SlotDesc][passes][table][state][dyn]
+  // layout inside the array: [binom][CtlStatic][SlotDesc][passes][table][state][dyn][aux][flags]
   const size_t off_ctl = a256(sizeof(fpenum::Binom));
   const size_t off_slot = a256(off_ctl + sizeof(fpk::CtlStatic));
   const size_t off_pass = a256(off_slot + sizeof(fpk::SlotDesc));
@@ -95,7 +95,8 @@ extern "C" int fpcode_min_distance_noalloc(int p, int n, int k, const uint8_t *G
   const size_t off_state = a256(off_table + P.table.size() * sizeof(uint32_t));
   const size_t dyn_bytes = a256(sizeof(fpk::SlotState) + sizeof(fpk::CtlDyn));
   const size_t off_aux = off_state + dyn_bytes;
-  const size_t aux_bytes = a256(sizeof(fpk::SlotAux));
+  const size_t off_flags = off_aux + a256(sizeof(fpk::SlotAux));
+  const size_t aux_bytes = off_flags - off_aux + 256;  // per-pass bookkeeping, then the slot's flag word
   if (off_aux + aux_bytes > kNoallocScratchBytes) {
     fph::set_error("fpcode_min_distance_noalloc: the code needs " + std::to_string(off_aux + aux_bytes) +
                    " bytes of device scratch, above the fixed 524288; use fpcode_min_distance");
@@ -126,6 +127,7 @@ extern "C" int fpcode_min_distance_noalloc(int p, int n, int k, const uint8_t *G
   fpk::CtlStatic cs{};
   cs.binom = reinterpret_cast<const fpenum::Binom *>(base);
   cs.aux = reinterpret_cast<fpk::SlotAux *>(base + off_aux);
+  cs.slot_flags = reinterpret_cast<uint32_t *>(base + off_flags);
   cs.nslots = 1;
   cs.serve = 0;
   std::memcpy(&img[0], &cs, sizeof(cs));

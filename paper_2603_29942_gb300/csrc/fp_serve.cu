@@ -68,9 +68,10 @@ struct fpcode_server {
   int smem = 0, ctas = 0, S = 0;
   char *dev = nullptr;
   size_t off_ctl = 0, off_slots = 0, off_passes = 0, off_arena = 0, arena_bytes = 0, off_states = 0,
-         off_dyn = 0, off_aux = 0, total = 0;
+         off_dyn = 0, off_aux = 0, off_flags = 0, total = 0;
   fpk::Completion *done_host = nullptr, *done_dev = nullptr;
   char *staging = nullptr;  // pinned, one region per slot
+  char *zeros = nullptr;    // pinned, never written: the source that clears a slot's bookkeeping
   size_t stage_per_slot = 0;
   std::vector<Slot> slots;
   std::vector<std::pair<size_t, size_t>> free_ext;  // arena extents (offset, bytes), sorted
@@ -190,6 +191,8 @@ int fpcode_serve_create(const fpcode_serve_opts *opts, void *stream, fpcode_serv
   off = a256(off + sizeof(fpk::CtlDyn));
   s->off_aux = off;
   off = a256(off + S * sizeof(fpk::SlotAux));
+  s->off_flags = off;
+  off = a256(off + (S + 3) / 4 * 16);
   s->total = off;
   SV_CUDA(cudaMalloc(&s->dev, s->total));
   SV_CUDA(cudaHostAlloc(&s->done_host, S * sizeof(fpk::Completion), cudaHostAllocMapped));
@@ -198,7 +201,11 @@ int fpcode_serve_create(const fpcode_serve_opts *opts, void *stream, fpcode_serv
   s->stage_per_slot =
       a256(sizeof(fpk::SlotDesc)) + a256(kMaxPassesPerSlot * sizeof(fpk::PassDesc)) + 256 + kServeTableCode;
   const size_t init_bytes = s->off_arena;  // ctl + descriptors + schedules
-  SV_CUDA(cudaMallocHost(&s->staging, std::max(S * s->stage_per_slot, init_bytes + S * sizeof(fpk::SlotState))));
+  const size_t flag_bytes = (S + 3) / 4 * 16;
+  SV_CUDA(cudaMallocHost(&s->staging, std::max(S * s->stage_per_slot,
+                                               init_bytes + S * sizeof(fpk::SlotState) + flag_bytes)));
+  SV_CUDA(cudaHostAlloc(&s->zeros, sizeof(fpk::SlotAux), cudaHostAllocDefault));
+  std::memset(s->zeros, 0, sizeof(fpk::SlotAux));
   SV_CUDA(cudaStreamCreateWithFlags(&s->cst, cudaStreamNonBlocking));
   SV_CUDA(cudaEventCreateWithFlags(&s->copies_done, cudaEventDisableTiming));
   SV_CUDA(cudaEventCreateWithFlags(&s->kernel_done, cudaEventDisableTiming));
@@ -208,6 +215,7 @@ int fpcode_serve_create(const fpcode_serve_opts *opts, void *stream, fpcode_serv
   cs.binom = s->ctx->binom;
   cs.done_host = s->done_dev;
   cs.aux = reinterpret_cast<fpk::SlotAux *>(s->dev + s->off_aux);
+  cs.slot_flags = reinterpret_cast<uint32_t *>(s->dev + s->off_flags);
   cs.nslots = s->S;
   cs.serve = 1;
   std::memcpy(s->staging + s->off_ctl, &cs, sizeof(cs));
@@ -218,6 +226,9 @@ int fpcode_serve_create(const fpcode_serve_opts *opts, void *stream, fpcode_serv
   std::memcpy(s->staging + init_bytes, states.data(), S * sizeof(fpk::SlotState));
   SV_CUDA(cudaMemcpyAsync(s->dev + s->off_states, s->staging + init_bytes, S * sizeof(fpk::SlotState),
                           cudaMemcpyHostToDevice, s->cst));
+  uint32_t *flags = reinterpret_cast<uint32_t *>(s->staging + init_bytes + S * sizeof(fpk::SlotState));
+  for (size_t i = 0; i < flag_bytes / 4; ++i) flags[i] = fpk::kSlotFinished;  // no code in any slot
+  SV_CUDA(cudaMemcpyAsync(s->dev + s->off_flags, flags, flag_bytes, cudaMemcpyHostToDevice, s->cst));
   SV_CUDA(cudaMemsetAsync(s->dev + s->off_dyn, 0, sizeof(fpk::CtlDyn), s->cst));
   SV_CUDA(cudaStreamSynchronize(s->cst));
   s->slots.resize(S);
@@ -295,13 +306,21 @@ int fpcode_serve_submit(fpcode_server *s, const fpcode_desc *code, uint64_t *tic
   SV_CUDA(cudaMemcpyAsync(d_pass, stg + o_pass, P->passes.size() * sizeof(fpk::PassDesc), cudaMemcpyHostToDevice,
                           s->cst));
   SV_CUDA(cudaMemcpyAsync(d_desc, stg, sizeof(sd), cudaMemcpyHostToDevice, s->cst));
-  SV_CUDA(cudaMemsetAsync(s->dev + s->off_aux + (size_t)slot * sizeof(fpk::SlotAux), 0, sizeof(fpk::SlotAux),
-                          s->cst));  // per-pass minima and counts, before the state
+  // per-pass minima and counts, before the state.  Admissions use copies
+  // only: a memset is a kernel, and it could not start while the serving
+  // kernel holds every SM.
+  SV_CUDA(cudaMemcpyAsync(s->dev + s->off_aux + (size_t)slot * sizeof(fpk::SlotAux), s->zeros,
+                          sizeof(fpk::SlotAux), cudaMemcpyHostToDevice, s->cst));
   fpk::SlotState fresh{};
   fresh.word = (unsigned long long)(tk & fpk::kGenMask) << fpk::kGenShift;
   std::memcpy(stg + o_state, &fresh, sizeof(fresh));
   SV_CUDA(cudaMemcpyAsync(s->dev + s->off_states + (size_t)slot * sizeof(fpk::SlotState), stg + o_state,
                           sizeof(fpk::SlotState), cudaMemcpyHostToDevice, s->cst));
+  // the flag word last: until it changes, claims skip the slot
+  const uint32_t flag = fpk::slot_flag_gen(tk & fpk::kGenMask);
+  std::memcpy(stg + o_state + sizeof(fpk::SlotState), &flag, sizeof(flag));
+  SV_CUDA(cudaMemcpyAsync(s->dev + s->off_flags + (size_t)slot * 4, stg + o_state + sizeof(fpk::SlotState),
+                          sizeof(flag), cudaMemcpyHostToDevice, s->cst));
   SV_CUDA(cudaEventRecord(s->copies_done, s->cst));
   Slot &sl = s->slots[slot];
   sl.busy = true;
@@ -383,6 +402,7 @@ void fpcode_serve_destroy(fpcode_server *s) {
   if (s->dev) cudaFree(s->dev);
   if (s->done_host) cudaFreeHost(s->done_host);
   if (s->staging) cudaFreeHost(s->staging);
+  if (s->zeros) cudaFreeHost(s->zeros);
   delete s;
 }
 

@@ -159,7 +159,7 @@ def test_paper_shift_and_rewrites(lib):
 
 
 def test_alg3_reading():
-    """Alg. 3 line 6 as printed (s0 = s0 and carry_1) is wrong on 5 of the 9
+    """Alg. 3 as printed (its update s0 = s0 and carry_1) is wrong on 5 of the 9
     pairs of F_3; read as xor it is right on all 9 (natural encoding)."""
     def alg3(a, b, sixth):
         a0, a1, b0, b1 = a & 1, a >> 1, b & 1, b >> 1

@@ -172,7 +172,7 @@ def pin_counts_closed_form(lib_path=None):
 
 def pin_bounds_alg6(lib_path=None):
     """With full-rank Gamma_1..Gamma_(m-1) and the per-round check, the bound
-    after round g is (m-1)(g+1) + max(0, g+1-k+k_m) (Alg. 6 line 7); every
+    after round g is (m-1)(g+1) + max(0, g+1-k+k_m) (the bound of Alg. 6); every
     pass's best weight is >= d; the search stops at L >= U = d; Singleton
     and Griesmer hold."""
     rng = np.random.default_rng(14)
