@@ -200,6 +200,11 @@ typedef struct fpcode_serve_opts {
   size_t device_bytes;    /* device memory for code tables (default 64 MiB) */
   double idle_exit_s;     /* persistent kernel exits after this long idle
                              (default 0.02 s); it is relaunched on demand */
+  int max_words;          /* 32-bit words per slice a served code may need:
+                             2 (default: n - k <= 64, the faster kernel) or
+                             4 (n - k <= 128); a code above it is rejected
+                             with FPCODE_EINVAL */
+  int reserved;
   fpcode_opts search;     /* per-code search options */
 } fpcode_serve_opts;
 

@@ -81,6 +81,8 @@ class fpcode_serve_opts(ctypes.Structure):
         ("ctas_per_sm", ctypes.c_int),
         ("device_bytes", ctypes.c_size_t),
         ("idle_exit_s", ctypes.c_double),
+        ("max_words", ctypes.c_int),
+        ("reserved", ctypes.c_int),
         ("search", fpcode_opts),
     ]
 

@@ -480,17 +480,19 @@ int fpcode_min_distance_batch(int num, const fpcode_desc *codes, void *stream, c
   DevCtx *c;
   int s = get_ctx(&c);
   if (s) return s;
-  // groups: the batched kernel for p in {3,5,7}; one launch per other variant
+  // groups: the batched kernels for p in {3,5,7} (narrow: W <= 2, wide:
+  // W <= 4); one launch per other variant
   std::vector<std::vector<int>> groups;
   {
-    std::vector<int> multi;
+    std::vector<int> narrow, wide;
     std::vector<std::vector<int>> other(64);
     for (int i = 0; i < num; ++i) {
       if (status[i] != FPCODE_OK) continue;
-      if (preps[i]->variant < 12) multi.push_back(i);
+      if (preps[i]->variant < 12) (preps[i]->W <= 2 ? narrow : wide).push_back(i);
       else other[preps[i]->variant].push_back(i);
     }
-    if (!multi.empty()) groups.push_back(multi);
+    if (!narrow.empty()) groups.push_back(narrow);
+    if (!wide.empty()) groups.push_back(wide);
     for (auto &g : other)
       if (!g.empty()) groups.push_back(g);
   }
@@ -510,7 +512,9 @@ int fpcode_min_distance_batch(int num, const fpcode_desc *codes, void *stream, c
       }
     if (codesv.empty()) continue;
     const bool multi = codesv[0]->variant < 12;
-    const void *fn = multi ? fpk::kernel_multi357() : kernel_for(codesv[0]->variant);
+    int wmax = 1;
+    for (auto *P : codesv) wmax = std::max(wmax, P->W);
+    const void *fn = multi ? fpk::kernel_multi357(wmax) : kernel_for(codesv[0]->variant);
     const int smem = smem_for(codesv);
     int per_sm = 0;
     s = occupancy(fn, smem, o.ctas_per_sm, &per_sm);

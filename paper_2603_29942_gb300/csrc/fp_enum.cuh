@@ -205,6 +205,24 @@ FP_HD int gray_digit(uint64_t d, int s, int b, int L) {
 // Precondition: the counter is not at its last value.
 template <int DB>
 FP_HD int gray_step(uint64_t *d, int b, int L, int *dir) {
+  if constexpr (DB == 1) {
+    // b = 2: the counter is a binary number; its lowest 0 bit is the digit
+    // that moves, and the 1 bits below it wrap to 0
+    const int s = ctz64(~*d);
+    *d += 1;
+    *dir = (s + 1 < L && ((*d >> (s + 1)) & 1ull)) ? -1 : 1;
+    return s;
+  } else if constexpr (DB == 4) {
+    // nibble digits: the lowest digit below b - 1 moves; those below it
+    // (all b - 1) wrap to 0
+    const uint64_t x = *d ^ (0x1111111111111111ull * (uint64_t)(b - 1));  // zero nibble: digit b - 1
+    const uint64_t nz = (x | (x >> 1) | (x >> 2) | (x >> 3)) & 0x1111111111111111ull;
+    const int s = ctz64(nz) >> 2;
+    const uint64_t low = s == 0 ? 0ull : ((1ull << (4 * s)) - 1);
+    *d = (*d & ~low) + (1ull << (4 * s));
+    *dir = (s + 1 < L && ((*d >> (4 * (s + 1))) & 1ull)) ? -1 : 1;
+    return s;
+  }
   int s = 0;
   while (digit<DB>(*d, s) == b - 1) ++s;
   uint64_t keep = (s + 1) * DB >= 64 ? 0ull : (*d >> ((s + 1) * DB)) << ((s + 1) * DB);

@@ -147,14 +147,20 @@ __device__ __forceinline__ void set_row(uint32_t (&s)[R * W], const uint32_t *ta
 }
 
 // Exact sum of a prefix: A[m] (coefficient 1) + sum over the slots of Q.
+// Rows of Q by slot, 6 bits each, for the first kSlotRows slots (a Gray
+// step then finds its row with one shift instead of a walk over Q).
+constexpr int kSlotRows = 10;
+
 template <int P, int R, int W, int DB>
 __device__ __forceinline__ void build_sum(uint32_t (&s)[R * W], const uint32_t *tab, const fpenum::Prefix &pf,
-                                          int L, int b, int p) {
+                                          int L, int b, int p, uint64_t &qrows) {
   set_row<P, R, W>(s, tab, pf.m, 1, p);
   uint64_t Q = pf.Q;
+  qrows = 0;
   for (int slot = 0; slot < L; ++slot) {
     int q = fpenum::ctz64(Q);
     Q &= Q - 1;
+    if (slot < kSlotRows) qrows |= (uint64_t)q << (6 * slot);
     int coef = fpenum::gray_digit<DB>(pf.d, slot, b, L) + 1;
     add_row<P, R, W>(s, tab, q, coef, p);
   }
@@ -219,7 +225,68 @@ struct LeafFilter {
   static constexpr bool kMersenne = (P == 3 || P == 7);
   static constexpr int kSigW = kMersenne ? (((P == 3 ? W * (R - 1) : 3 * W * (R - 1)) + 3) & ~3) : 0;
   static constexpr int kPrefSig = kMersenne ? W * (R - 1) : 1;
+  // leaves evaluated per vote: as many as the registers allow
+  static constexpr int kUnroll = !kMersenne ? 1 : kSigW <= 4 ? 4 : kSigW <= 8 ? 2 : 1;
 };
+
+// Lower bound on the redundant weight of S + c A[x] over every nonzero
+// leaf coefficient c: the least bound of the pairs {c, p - c}.
+template <int P, int R, int W, int NA>
+__device__ __forceinline__ int pair_bound(const uint32_t (&s)[R * W], const uint32_t (&a)[NA], const uint32_t *sig,
+                                          const uint32_t *tab, int x, int p) {
+  using F = LeafFilter<P, R, W>;
+  constexpr int RWP = Shape<R, W>::RWP;
+  int best = 1 << 20;
+  if constexpr (F::kMersenne) {
+    uint32_t e[F::kSigW];
+    load_entry<F::kSigW>(sig, x, e);
+    constexpr int NP = (P - 1) / 2;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      int lb = 0;
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        uint32_t f = 0;
+#pragma unroll
+        for (int i = 0; i + 1 < R; ++i) f |= a[w * (R - 1) + i] ^ e[(q * W + w) * (R - 1) + i];
+        lb += __popc(f);
+      }
+      best = min(best, lb);
+    }
+  } else {
+    const int b = p - 1;
+    for (int q = 0; q < (p - 1) / 2; ++q) {
+      const int c = q + 1;
+      uint32_t e1[RWP], e2[RWP];
+      load_entry<RWP>(tab, x * b + (p - c - 1), e1);  // (p - c) A = -c A
+      load_entry<RWP>(tab, x * b + (c - 1), e2);      // c A = -(p - c) A
+      int lb = 0;
+#pragma unroll
+      for (int w = 0; w < W; ++w)
+        lb += __popc(fpbs::nz_sub<R>(&s[w * R], &e1[w * R]) & fpbs::nz_sub<R>(&s[w * R], &e2[w * R]));
+      best = min(best, lb);
+    }
+  }
+  return best;
+}
+
+// Slow path of leaf x: the exact redundant weight of S + c A[x] for every
+// c, recording those below the lane's threshold (which then drops to it).
+template <int P, int R, int W>
+__device__ __forceinline__ void leaf_exact(const uint32_t (&s)[R * W], const uint32_t *tab, int x, int p, int g,
+                                        int pass, uint64_t I, int &thr, SlotState *st, SlotAux *ax) {
+  constexpr int RWP = Shape<R, W>::RWP;
+  const int b = p - 1;
+  for (int c = 1; c < p; ++c) {
+    uint32_t e[RWP];
+    load_entry<RWP>(tab, x * b + (p - c - 1), e);
+    const int wr = leaf_weight<R, W>(s, e);
+    if (wr < thr) {  // weights up to g + wr stay of interest: ties decide the witness by key
+      record(st, ax, pass, make_key((uint32_t)(g + wr), (uint32_t)pass, I, (uint32_t)x, (uint32_t)c));
+      thr = wr + 1;
+    }
+  }
+}
 
 template <int R, int W, int NA>
 __device__ __forceinline__ void prefix_signature(const uint32_t (&s)[R * W], uint32_t (&a)[NA]) {
@@ -230,7 +297,7 @@ __device__ __forceinline__ void prefix_signature(const uint32_t (&s)[R * W], uin
     for (int i = 0; i + 1 < R; ++i) a[w * (R - 1) + i] = s[w * R + i] ^ s[w * R + i + 1];
 }
 
-template <int P, int R, int W, int DB>
+template <int P, int R, int W, int DB, int UNR>
 __device__ void task_prefixes(const SlotDesc &sd, const PassDesc &pd, int pass, const uint32_t *tab,
                               const fpenum::BinomCols &B, uint64_t task, int U, SlotState *st, SlotAux *ax,
                               unsigned long long &count) {
@@ -263,16 +330,19 @@ __device__ void task_prefixes(const SlotDesc &sd, const PassDesc &pd, int pass, 
   pf.qi = 0;
   pf.Q = 0;
   pf.d = 0;
-  uint64_t ci = 0, nq = 1;
+  uint64_t ci = 0, nq = 1, qrows = 0;
   if (I < Iend) {
     pf = fpenum::prefix_unrank<DB>(B, I, k, g, b);
     ci = (I - fpenum::prefixes_below(B, pf.m, g, pd.NC)) - pf.qi * pd.NC;
     nq = B(pf.m, L);
-    build_sum<P, R, W, DB>(s, tab, pf, L, b, p);
+    build_sum<P, R, W, DB>(s, tab, pf, L, b, p, qrows);
     if constexpr (F::kMersenne) prefix_signature<R, W>(s, a);
   }
 
-  for (uint64_t step = 0; step < pl; ++step) {
+  // prefixes left to this lane (the current one included); its index is Iend - left
+  uint32_t left = I < Iend ? (uint32_t)(Iend - I) : 0u;
+  const uint32_t nsteps = (uint32_t)pl;
+  for (uint32_t step = 0; step < nsteps; ++step) {
     if ((step & 15) == 15) {
       // a finished code only has tasks of passes past its stop left: drop
       // them; else take up the best weight recorded anywhere since
@@ -285,75 +355,72 @@ __device__ void task_prefixes(const SlotDesc &sd, const PassDesc &pd, int pass, 
       if (__shfl_sync(0xffffffffu, fin, 0)) break;
       thr = min(thr, __shfl_sync(0xffffffffu, ub, 0) - g + 1);
     }
-    const bool act = I < Iend;
+    const bool act = left > 0;
     const int mlane = act ? pf.m : k;
     const int xs = (int)__reduce_min_sync(0xffffffffu, (unsigned)mlane) + 1;
-    for (int x = xs; x < k; ++x) {
-      const int tx = x > mlane ? thr : 0;
-      bool hit = false;
-      if constexpr (F::kMersenne) {
-        uint32_t e[F::kSigW];
-        load_entry<F::kSigW>(sig, x, e);
-        constexpr int NP = (P - 1) / 2;
-#pragma unroll
-        for (int q = 0; q < NP; ++q) {
-          int lb = 0;
-#pragma unroll
-          for (int w = 0; w < W; ++w) {
-            uint32_t f = 0;
-#pragma unroll
-            for (int i = 0; i + 1 < R; ++i) f |= a[w * (R - 1) + i] ^ e[(q * W + w) * (R - 1) + i];
-            lb += __popc(f);
-          }
-          hit |= lb < tx;
-        }
-      } else {
-        const int np = (p - 1) / 2;
-        for (int q = 0; q < np; ++q) {
-          const int c = q + 1;
-          uint32_t e1[RWP], e2[RWP];
-          load_entry<RWP>(tab, x * b + (p - c - 1), e1);  // (p - c) A = -c A
-          load_entry<RWP>(tab, x * b + (c - 1), e2);      // c A = -(p - c) A
-          int lb = 0;
-#pragma unroll
-          for (int w = 0; w < W; ++w)
-            lb += __popc(fpbs::nz_sub<R>(&s[w * R], &e1[w * R]) & fpbs::nz_sub<R>(&s[w * R], &e2[w * R]));
-          hit |= lb < tx;
+    if constexpr (UNR == 1) {
+      for (int x = xs; x < k; ++x) {  // lanes whose prefix reaches above x sit it out
+        const int tx = x > mlane ? thr : 0;
+        if (__any_sync(0xffffffffu, pair_bound<P, R, W>(s, a, sig, tab, x, p) < tx)) {
+          if (x > mlane) leaf_exact<P, R, W>(s, tab, x, p, g, pass, Iend - left, thr, st, ax);
+          thr = (int)__reduce_min_sync(0xffffffffu, (unsigned)thr);
         }
       }
-      if (__any_sync(0xffffffffu, hit)) {
-        if (hit) {  // slow path: exact weights of every leaf coefficient
-          for (int c = 1; c < p; ++c) {
-            uint32_t e[RWP];
-            load_entry<RWP>(tab, x * b + (p - c - 1), e);
-            const int wr = leaf_weight<R, W>(s, e);
-            if (wr < thr) {  // weights up to g + wr stay of interest: ties decide the witness by key
-              record(st, ax, pass, make_key((uint32_t)(g + wr), (uint32_t)pass, I, (uint32_t)x, (uint32_t)c));
-              thr = wr + 1;
-            }
-          }
+    } else {
+      // leaves above every active lane's largest row: no per-lane test needed
+      const int xu = max(xs, (int)__reduce_max_sync(0xffffffffu, (unsigned)(act ? pf.m + 1 : 0)));
+      for (int x = xs; x < xu; ++x) {  // lanes whose prefix reaches above x sit these out
+        const int tx = x > mlane ? thr : 0;
+        if (__any_sync(0xffffffffu, pair_bound<P, R, W>(s, a, sig, tab, x, p) < tx)) {
+          if (x > mlane) leaf_exact<P, R, W>(s, tab, x, p, g, pass, Iend - left, thr, st, ax);
+          thr = (int)__reduce_min_sync(0xffffffffu, (unsigned)thr);
         }
-        thr = (int)__reduce_min_sync(0xffffffffu, (unsigned)thr);
+      }
+      int x = xu;
+      for (; x + UNR <= k; x += UNR) {
+        int lb[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) lb[u] = pair_bound<P, R, W>(s, a, sig, tab, x + u, p);
+        int lbm = lb[0];
+#pragma unroll
+        for (int u = 1; u < UNR; ++u) lbm = min(lbm, lb[u]);
+        if (__any_sync(0xffffffffu, act && lbm < thr)) {
+          if (act) {
+#pragma unroll
+            for (int u = 0; u < UNR; ++u)
+              if (lb[u] < thr) leaf_exact<P, R, W>(s, tab, x + u, p, g, pass, Iend - left, thr, st, ax);
+          }
+          thr = (int)__reduce_min_sync(0xffffffffu, (unsigned)thr);
+        }
+      }
+      for (; x < k; ++x) {
+        if (__any_sync(0xffffffffu, act && pair_bound<P, R, W>(s, a, sig, tab, x, p) < thr)) {
+          if (act) leaf_exact<P, R, W>(s, tab, x, p, g, pass, Iend - left, thr, st, ax);
+          thr = (int)__reduce_min_sync(0xffffffffu, (unsigned)thr);
+        }
       }
     }
     if (act) count += (unsigned long long)(k - 1 - pf.m) * (unsigned long long)b;
-    // advance to prefix I + 1
-    ++I;
-    if (I < Iend) {
+    // advance to the next prefix
+    if (left > 1) {
       int dir;
       const int slot = fpenum::prefix_advance<DB>(B, pf, ci, nq, pd.NC, b, L, &dir);
       if (slot >= 0) {
-        const int q = fpenum::nth_member(pf.Q, slot);
+        const int q = slot < kSlotRows ? (int)(qrows >> (6 * slot)) & 63 : fpenum::nth_member(pf.Q, slot);
         add_row<P, R, W>(s, tab, q, dir > 0 ? 1 : b, p);  // c -> c+1: +A; c -> c-1: +(p-1)A
       } else {
-        build_sum<P, R, W, DB>(s, tab, pf, L, b, p);
+        build_sum<P, R, W, DB>(s, tab, pf, L, b, p, qrows);
       }
       if constexpr (F::kMersenne) prefix_signature<R, W>(s, a);
     }
+    left -= left > 0 ? 1u : 0u;
   }
 }
 
-template <int P, int R, int W>
+// One kernel variant: prime P (0: any, from the descriptor), r slices, W
+// words per slice; UNR leaves per vote in the leaf loop (1: the plain loop,
+// whose smaller code suits the batched kernels).
+template <int P, int R, int W, int UNR = LeafFilter<P, R, W>::kUnroll>
 struct Fixed {
   static constexpr int DB = P == 3 ? 1 : (P == 5 || P == 7) ? 4 : 8;  // as the host's digit width
   static __device__ __forceinline__ void run(const SlotDesc &sd, const PassDesc &pd, int pass, const uint32_t *tab,
@@ -362,7 +429,7 @@ struct Fixed {
     if (pd.g == 1) {
       if (task == 0) task_rows<P, R, W>(sd, pass, tab, U, st, ax, count);
     } else {
-      task_prefixes<P, R, W, DB>(sd, pd, pass, tab, B, task, U, st, ax, count);
+      task_prefixes<P, R, W, DB, UNR>(sd, pd, pass, tab, B, task, U, st, ax, count);
     }
   }
 };
@@ -374,14 +441,18 @@ __host__ __device__ inline int variant_id(int p, int r, int W) {
   return cls * 4 + (W - 1);
 }
 
-// Batched launches over codes with p in {3, 5, 7}: dispatch per task.
+// Batched launches over codes with p in {3, 5, 7}: dispatch per task.  The
+// narrow kernel (WMAX = 2: n - k <= 64) holds half the variants and so
+// fits its registers without spilling; the wide one (WMAX = 4) takes the
+// rest.
+template <int WMAX>
 struct Multi357 {
   static __device__ __forceinline__ void run(const SlotDesc &sd, const PassDesc &pd, int pass, const uint32_t *tab,
                                              const fpenum::BinomCols &B, uint64_t task, int U, SlotState *st,
                                              SlotAux *ax, unsigned long long &count) {
     switch (sd.variant) {
 #define FPK_CASE(id, P, R, W) \
-  case id: Fixed<P, R, W>::run(sd, pd, pass, tab, B, task, U, st, ax, count); break;
+  case id: if constexpr (W <= WMAX) Fixed<P, R, W, 1>::run(sd, pd, pass, tab, B, task, U, st, ax, count); break;
       FPK_CASE(0, 3, 2, 1)
       FPK_CASE(1, 3, 2, 2)
       FPK_CASE(2, 3, 2, 3)

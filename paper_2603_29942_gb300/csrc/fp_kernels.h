@@ -8,5 +8,7 @@ const void *kernel_p5(int W);
 const void *kernel_p7(int W);
 const void *kernel_generic(int r, int W);
 // Batched kernel dispatching per task over p in {3, 5, 7}, W in 1..4.
-const void *kernel_multi357();
+const void *kernel_multi357_narrow();  // W <= 2
+const void *kernel_multi357_wide();    // W <= 4
+inline const void *kernel_multi357(int W) { return W <= 2 ? kernel_multi357_narrow() : kernel_multi357_wide(); }
 }  // namespace fpk

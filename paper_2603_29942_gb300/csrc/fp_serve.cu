@@ -149,6 +149,7 @@ void fpcode_serve_opts_default(fpcode_serve_opts *o) {
   o->ctas_per_sm = 0;
   o->device_bytes = (size_t)64 << 20;
   o->idle_exit_s = 0.02;
+  o->max_words = 2;
   fpcode_opts_default(&o->search);
 }
 
@@ -158,8 +159,8 @@ int fpcode_serve_create(const fpcode_serve_opts *opts, void *stream, fpcode_serv
   fpcode_serve_opts o;
   fpcode_serve_opts_default(&o);
   if (opts) o = *opts;
-  if (o.slots < 1 || o.slots > 4096 || o.device_bytes < 4096) {
-    fph::set_error("serve: need 1..4096 slots and some device memory");
+  if (o.slots < 1 || o.slots > 4096 || o.device_bytes < 4096 || (o.max_words != 2 && o.max_words != 4)) {
+    fph::set_error("serve: need 1..4096 slots, some device memory and max_words 2 or 4");
     return FPCODE_EINVAL;
   }
   std::unique_ptr<fpcode_server> s(new fpcode_server());
@@ -167,7 +168,7 @@ int fpcode_serve_create(const fpcode_serve_opts *opts, void *stream, fpcode_serv
   s->kst = (cudaStream_t)stream;
   int st = fpd::get_ctx(&s->ctx);
   if (st) return st;
-  s->fn = fpk::kernel_multi357();
+  s->fn = fpk::kernel_multi357(o.max_words);
   s->smem = (int)kServeTableSet + fpk::kBinomBytes;
   int per_sm = 0;
   st = fpd::occupancy(s->fn, s->smem, o.ctas_per_sm, &per_sm);
@@ -246,6 +247,10 @@ int fpcode_serve_submit(fpcode_server *s, const fpcode_desc *code, uint64_t *tic
   if (st) return st;
   if (P->variant >= 12) {
     fph::set_error("serve: p must be 3, 5 or 7");
+    return FPCODE_EINVAL;
+  }
+  if (P->W > s->o.max_words) {
+    fph::set_error("serve: n - k needs more words per slice than the server's max_words");
     return FPCODE_EINVAL;
   }
   const size_t table_bytes = P->table.size() * sizeof(uint32_t);

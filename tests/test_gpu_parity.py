@@ -199,6 +199,20 @@ def test_batch_against_oracle_mixed_primes():
             check_witness(c, rb.d, rb.witness)
 
 
+def test_batch_mixed_widths_against_oracle():
+    """Codes of one, two and three words per slice in one batch run in the
+    narrow and the wide batched kernels; each matches the oracle."""
+    shapes = [(3, 70, 5), (3, 40, 6), (3, 30, 6), (7, 75, 4), (5, 100, 4), (7, 50, 8), (5, 36, 7), (3, 98, 6)]
+    codes = [inputs.single_code(700 + i, p, n, k) for i, (p, n, k) in enumerate(shapes)]
+    res = B.fpcode_min_distance_batch(codes, budgets=[10 ** 7] * len(codes))
+    for c, rb in zip(codes, res):
+        r = oracle.bz(c, budget=10 ** 7, threads=4)
+        assert (rb.status, rb.counts, rb.L, rb.U) == (status_of_oracle(r.status), r.counts, r.L, r.U)
+        if r.status == oracle.OK:
+            assert rb.d == r.d
+            check_witness(c, rb.d, rb.witness)
+
+
 def test_bounded_wait_reports_timeout():
     """A hand-off wait limit far below a task's duration makes the waiting
     CTAs give up and the kernel return; the host reports ETIMEOUT and the

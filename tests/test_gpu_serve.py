@@ -107,3 +107,21 @@ def test_serve_relaunch_after_idle():
         assert out[t].status == B.OK and out[t].d == 6
         time.sleep(0.05)  # longer than the idle period: the kernel has exited
     B.fpcode_serve_destroy(srv)
+
+
+def test_serve_word_limit():
+    """A server for n - k <= 64 turns a wider code away with EINVAL; a
+    server created with max_words = 4 serves it, with the result it has
+    alone."""
+    wide = inputs.single_code(801, 3, 72, 6)  # n - k = 66: three words per slice
+    srv = B.fpcode_serve_create(B.fpcode_serve_opts_default(slots=4))
+    with pytest.raises(B.FpcodeError):
+        B.fpcode_serve_submit(srv, wide, budget=10 ** 6)
+    B.fpcode_serve_destroy(srv)
+    srv = B.fpcode_serve_create(B.fpcode_serve_opts_default(slots=4, max_words=4))
+    t = B.fpcode_serve_submit(srv, wide, budget=10 ** 6)
+    assert t is not None
+    B.fpcode_serve_drain(srv)
+    got = dict(B.fpcode_serve_poll(srv))
+    B.fpcode_serve_destroy(srv)
+    _check(wide, got[t], _alone(wide, 10 ** 6))
