@@ -277,8 +277,12 @@ int prepare(int p, int n, int k, const uint8_t *G, const fpcode_opts &opts, Prep
           nprefix = sat_mul(binom().c[k - 1][h - 1], NC);
         }
         const bool over_budget = opts.budget && (size > opts.budget || total > opts.budget - size);
+        // a level the kernels cannot take ends the schedule (status EBUDGET
+        // if the search gets there): prefix indices must fit the key, the
+        // coefficient counter 64 bits, the binomials of an unrank the staged
+        // columns t < kBinomCols, the pass index 8 bits
         if (over_budget || size == ~0ull || nprefix >= fpk::kMaxPrefix || h > gmax_digits ||
-            (int)P->passes.size() >= fpk::kMaxPasses) {
+            h > fpenum::kBinomCols || (int)P->passes.size() >= fpk::kMaxPasses) {
           truncated = true;
           break;
         }

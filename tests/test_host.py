@@ -360,3 +360,20 @@ def test_task_ranges_tile_each_pass(ctas, fixed_pl, lib):
         if fixed_pl == 0 and nprefix > 2 * 256 * ctas:
             sizes = [hi - lo for lo, hi in ranges]
             assert sizes[0] + 256 >= sizes[-1]  # tasks shrink as the pass drains (up to one unit)
+
+
+def test_schedule_stays_within_staged_binomial_columns():
+    """A level g needs binomial columns up to g - 1 in shared memory (24 are
+    staged).  k = 24 over F_3 schedules every level up to g = 24; for larger
+    k the prefix-index limit ends the schedule earlier, so no schedule holds
+    a level past the staged columns."""
+    rng = np.random.default_rng(5)
+    for k, complete in ((24, True), (26, False), (40, False)):
+        A = rng.integers(0, 3, size=(k, k), dtype=np.uint8)
+        code = inputs.systematic(3, 2 * k, k, A)
+        pr = B.fpcode_prepare(code.p, code.n, code.k, code.G, B.fpcode_opts_default(budget=0))
+        gmax = max(x[0] for x in B.fpcode_prepared_passes(pr))
+        assert gmax <= 24
+        assert B.fpcode_prepared_shape(pr)[3] is complete
+        if complete:
+            assert gmax == 24
