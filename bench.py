@@ -49,6 +49,10 @@ WORKLOADS = {
     "f3_n80_k40": "F_3 [80,40] random systematic code G=[I|A], A uniform, PCG64 seed 2",
     "f7_n40_k20": "F_7 [40,20] random systematic code G=[I|A], A uniform, PCG64 seed 1",
     "f3_n30_k15": "F_3 [30,15] random systematic code G=[I|A], A uniform, PCG64 seed 0",
+    "probe_f3_n80_k40_g8": "one pass (g=8, Gamma_1) of the F_3 [80,40] code alone, termination off, U seeded at d: "
+                           "C(40,8) 2^7 = 9 843 799 680 codewords",
+    "probe_f7_n40_k20_g7": "one pass (g=7, Gamma_1) of the F_7 [40,20] code alone, termination off, U seeded at d: "
+                           "C(20,7) 6^6 = 3 616 773 120 codewords",
     "batch512": "512 random codes, p in {3,7}, n in {24,...,64}, k = round(r n), r ~ U[1/3,2/3], PCG64 seed 3",
     "serve": "Poisson arrivals (200/s) of random codes, p in {3,5,7}, n ~ U[20,72], k ~ U[n/3,2n/3], PCG64 seed 4",
 }
@@ -201,6 +205,81 @@ def _cuda(local):
     return torch, B
 
 
+PROBES = {"probe_f3_n80_k40_g8": ("f3_n80_k40", 8), "probe_f7_n40_k20_g7": ("f7_n40_k20", 7)}
+
+
+def time_pass(torch, B, code, pr, idx, d, stream, steps, warmup):
+    """Time pass `idx` of prepared code `pr` alone (U seeded at d), L2
+    flushed between steps.  Returns (total event ms, mean kernel ms, least
+    weight found in the pass)."""
+    g, size = B.fpcode_prepared_passes(pr)[idx][0], B.fpcode_prepared_passes(pr)[idx][5]
+    probe = B.fpcode_prepared_single_pass(pr, idx, d)
+    B.fpcode_prepared_upload(probe, stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(warmup):
+        B.fpcode_search_enqueue(probe, stream)
+        r = B.fpcode_search_finish(probe, stream, want_witness=False)
+    assert r.counts[g] == size
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    kern = []
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for i in range(steps):
+            flush.fill_(i & 0xFF)
+            evs[i][0].record(stream)
+            B.fpcode_search_enqueue(probe, stream)
+            evs[i][1].record(stream)
+            r = B.fpcode_search_finish(probe, stream, want_witness=False)
+            assert r.counts[g] == size
+            kern.append(r.t_kernel_ms)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs), statistics.mean(kern), r.U
+
+
+def run_probe(args, rank, world, local):
+    """Kernel efficiency on one pass of fixed, closed-form size (no early
+    termination): the pass runs alone, every task to the end, with the record
+    threshold a certified search has at that level (U = d)."""
+    from paper_2603_29942_gb300 import inputs
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle is timed on the certified "
+                              "single-code searches; a single pass has no reference arm"}))
+        return
+    torch, B = _cuda(local)
+    name, g = PROBES[args.workload]
+    code = inputs.single(name)
+    stream = torch.cuda.Stream()
+    full = B.fpcode_prepare(code.p, code.n, code.k, code.G)
+    d = B.fpcode_min_distance_ex(full, stream).d  # the bound a certified search ends with
+    pr = B.fpcode_prepare(code.p, code.n, code.k, code.G, B.fpcode_opts_default(budget=0))
+    passes = B.fpcode_prepared_passes(pr)
+    idx = next(i for i, x in enumerate(passes) if x[0] == g and x[1] == 0)
+    size = passes[idx][5]
+    with ClockSampler(local) as clk:
+        t_ms, kern_ms, least = time_pass(torch, B, code, pr, idx, d, stream, args.steps, args.warmup)
+    W = max(1, -(-(code.n - code.k) // 32))
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peak = POPC_PER_CLK_SM * sms * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = size * W / (kern_ms * 1e-3) / 1e12
+    line = {
+        "metric": "codewords_per_s", "value": world * size * args.steps / (t_ms * 1e-3), "unit": "codewords/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "pass": [g, 0],
+                   "codewords_per_step": size, "u_seed": d, "least_weight_in_pass": least,
+                   "l2": "flushed between timed steps (256 MiB memset)", "parallelism": "single GPU"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tpopc/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "bz_kernel", "ops_per_codeword": W,
+                     "peak_basis": f"{POPC_PER_CLK_SM:.0f} POPC/clk/SM x {sms} SMs x {SM_MAX_MHZ:.0f} MHz"},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_batch(args, rank, world, local):
     """512 codes: one persistent batched launch vs one launch per code."""
     from paper_2603_29942_gb300 import inputs
@@ -328,6 +407,8 @@ def main():
     rank, world, local = dist_env()
     if args.workload == "batch512":
         return run_batch(args, rank, world, local)
+    if args.workload in PROBES:
+        return run_probe(args, rank, world, local)
     if args.workload == "serve":
         return run_serve(args, rank, world, local)
     code = inputs.single(args.workload)
@@ -409,6 +490,20 @@ def main():
             "traffic": profiled_traffic(args.workload), "kernel": "bz_kernel", "ops_per_codeword": popc_per_cw,
             "peak_basis": f"{POPC_PER_CLK_SM:.0f} POPC/clk/SM x {sms} SMs x {SM_MAX_MHZ:.0f} MHz"}
 
+    # --- the same kernel in steady state: one long pass alone (fixed size) ---
+    probe_of = {v[0]: (k, v[1]) for k, v in PROBES.items()}
+    roof_probe = None
+    if args.workload in probe_of:
+        pname, pg = probe_of[args.workload]
+        pr_all = B.fpcode_prepare(code.p, code.n, code.k, code.G, B.fpcode_opts_default(budget=0))
+        pidx = next(i for i, x in enumerate(B.fpcode_prepared_passes(pr_all)) if x[0] == pg and x[1] == 0)
+        psize = B.fpcode_prepared_passes(pr_all)[pidx][5]
+        _t, pk_ms, _least = time_pass(torch, B, code, pr_all, pidx, res.d, stream, 5, 3)
+        pach = psize * popc_per_cw / (pk_ms * 1e-3) / 1e12
+        roof_probe = {"bound": "alu", "achieved": pach, "peak": peak, "unit": "Tpopc/s", "frac": pach / peak,
+                      "pass": [pg, 0], "codewords": psize, "kernel_ms": pk_ms, "workload": pname,
+                      "note": "the same kernel on one pass of fixed size alone, termination off, U seeded at d"}
+
     line = {
         "metric": "codewords_per_s", "value": value, "unit": "codewords/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -418,6 +513,7 @@ def main():
                    "time_to_certified_d_ms": t_ms / args.steps, "l2": "flushed between timed steps (256 MiB memset)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roof,
+        "roofline_pass_probe": roof_probe,
         "e2e": {"value": e2e_value, "unit": "codewords/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": 1e3 * e2e_s / args.steps},
         "gpu_launches": args.steps,

@@ -66,6 +66,19 @@ int fpcode_test_task_ranges(fpcode_prepared *prep, int pass, int ctas, int fixed
  * each of its passes (-1: not reached), for up to max passes.  Returns the
  * number of passes written, or -1. */
 int fpcode_test_pass_times(fpcode_prepared *prep, void *stream, double *us, int max);
+
+/* Single-pass probe (kernel efficiency on a pass of fixed, closed-form size,
+ * Sec. 3.1 Alg. 6 with its termination test switched off): *out is a new
+ * prepared code whose schedule is pass `pass` of `src` alone, with lower
+ * bounds 0 so that every task runs and nothing is certified.  u_init > 0
+ * starts the search with the upper bound U = u_init (the record threshold a
+ * real search has by that level); 0 starts from the Singleton bound.  Run it
+ * with fpcode_search_enqueue / fpcode_search_finish: the status is
+ * FPCODE_EBUDGET, counts[g] is the pass size, U the least weight found in
+ * the pass (or u_init if none is lower), and a witness is returned only for
+ * a codeword of the pass.  Owned by the caller (fpcode_prepared_free).
+ * FPCODE_EINVAL: no such pass, or u_init outside 0..255. */
+int fpcode_prepared_single_pass(const fpcode_prepared *src, int pass, int u_init, fpcode_prepared **out);
 /* Bytes one search moves: host-to-device (tables, schedule, descriptors)
  * and device-to-host (final state). */
 int fpcode_prepared_bytes(const fpcode_prepared *prep, uint64_t *h2d, uint64_t *d2h);

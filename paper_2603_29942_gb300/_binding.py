@@ -152,6 +152,7 @@ def _declare(lib):
                                                    ctypes.c_int]),
         "fpcode_test_pass_times": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
         "fpcode_prepared_bytes": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
+        "fpcode_prepared_single_pass": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_VP)]),
     }
     found = []
     for name, (res, args) in sig.items():
@@ -442,6 +443,14 @@ def fpcode_prepared_passes(prep: Prepared):
     n = lib().fpcode_prepared_passes(prep.handle, arr, 256)
     return [(arr[i].g, arr[i].j, arr[i].L_before, arr[i].L_after, arr[i].round_end, int(arr[i].size),
              int(arr[i].nprefix)) for i in range(n)]
+
+
+def fpcode_prepared_single_pass(prep: Prepared, pass_index: int, u_init: int = 0) -> Prepared:
+    """Probe: pass `pass_index` of prep's schedule alone, termination off."""
+    h = _VP()
+    _check(lib().fpcode_prepared_single_pass(prep.handle, int(pass_index), int(u_init), ctypes.byref(h)),
+           "fpcode_prepared_single_pass")
+    return Prepared(h.value, prep.p, prep.n, prep.k)
 
 
 def fpcode_prepared_bytes(prep: Prepared) -> tuple[int, int]:

@@ -272,6 +272,12 @@ int enqueue_one(fpcode_prepared *prep, cudaStream_t st, const fpcode_opts &o) {
   fph::Prepared &P = prep->host;
   Layout L = make_layout({&P});
   FP_CUDA(cudaMemsetAsync(prep->dev + L.off_states, 0, L.dyn_bytes + L.aux_bytes, st));
+  if (prep->init_u > 0) {  // the bound as a key past every real one (pass 255), stored inverted
+    static thread_local unsigned long long seed;
+    seed = ~fpk::make_key((uint32_t)prep->init_u, 255u, (1ull << 34) - 1, 63u, 255u);
+    FP_CUDA(cudaMemcpyAsync(prep->dev + L.off_states + offsetof(SlotState, best_key), &seed, sizeof(seed),
+                            cudaMemcpyHostToDevice, st));
+  }
   if (!P.passes.empty()) {
     FP_CUDA(cudaEventRecord((cudaEvent_t)prep->ev0, st));
     int s = launch(kernel_for(P.variant), prep->ctas, prep->smem, st, prep->dev, L, kparams(o, 0));
@@ -347,6 +353,28 @@ int fpcode_prepare(int p, int n, int k, const uint8_t *G, const fpcode_opts *opt
     delete prep;
     return s;
   }
+  *out = prep;
+  return FPCODE_OK;
+}
+
+int fpcode_prepared_single_pass(const fpcode_prepared *src, int pass, int u_init, fpcode_prepared **out) {
+  if (!out) return FPCODE_EINVAL;
+  *out = nullptr;
+  if (!src || pass < 0 || pass >= (int)src->host.passes.size() || u_init < 0 || u_init > fpk::kMaxN) {
+    fph::set_error("fpcode_prepared_single_pass: no such pass, or a bound outside 0..255");
+    return FPCODE_EINVAL;
+  }
+  fpcode_prepared *prep = new (std::nothrow) fpcode_prepared();
+  if (!prep) return FPCODE_ENOMEM;
+  prep->host = src->host;
+  fpk::PassDesc d = src->host.passes[pass];
+  d.L_before = 0;  // no bound ever reaches U: every task runs, nothing is certified
+  d.L_after = 0;
+  d.round_end = 1;
+  d.task_base = 0;
+  prep->host.passes.assign(1, d);
+  prep->host.complete = 0;
+  prep->init_u = u_init;
   *out = prep;
   return FPCODE_OK;
 }

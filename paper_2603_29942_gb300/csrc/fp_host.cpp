@@ -405,8 +405,10 @@ int decode_result(const Prepared &P, const DeviceOutcome &o, fpcode_result *res,
   res->npasses = o.stop_pass + 1;
   for (int i = 0; i <= o.stop_pass && i < (int)P.passes.size(); ++i) res->counts[P.passes[i].g] += P.passes[i].size;
   res->L = o.stop_pass >= 0 ? P.passes[o.stop_pass].L_after : P.L0;
-  const bool have = o.best_key != fpk::kNoKey;
-  res->U = have ? std::min<int>((int)fpk::key_weight(o.best_key), singleton) : singleton;
+  // a key whose pass is outside the schedule is a seeded bound, not a codeword
+  const bool seeded = o.best_key != fpk::kNoKey && fpk::key_pass(o.best_key) >= P.passes.size();
+  const bool have = o.best_key != fpk::kNoKey && !seeded;
+  res->U = o.best_key != fpk::kNoKey ? std::min<int>((int)fpk::key_weight(o.best_key), singleton) : singleton;
   res->status = o.status < 0 ? FPCODE_ETIMEOUT : o.status;
   res->d = -1;
   if (res->status == FPCODE_OK) {

@@ -64,6 +64,7 @@ struct fpcode_prepared {
   int device = -1;
   int ctas = 0;         // grid the tasks were planned for
   int smem = 0;         // dynamic shared memory of one launch
+  int init_u = 0;       // > 0: the search starts with this upper bound (single-pass probes)
   bool uploaded = false;
   bool external = false;  // device/pinned buffers borrowed from a workspace
   char *dev = nullptr;    // [CtlStatic][SlotDesc][PassDesc...][table] [SlotState][CtlDyn]

@@ -8,7 +8,9 @@ verified, not compared.
 """
 from __future__ import annotations
 
+import itertools
 import json
+import math
 import os
 
 import numpy as np
@@ -211,6 +213,43 @@ def test_batch_mixed_widths_against_oracle():
         if r.status == oracle.OK:
             assert rb.d == r.d
             check_witness(c, rb.d, rb.witness)
+
+
+def _pass_minimum(gamma, p, g):
+    """Least weight over every codeword that combines exactly g rows of
+    gamma with nonzero coefficients (brute force, numpy)."""
+    k, n = gamma.shape
+    coefs = np.array(list(itertools.product(range(1, p), repeat=g)), dtype=np.int64)
+    best = n + 1
+    for rows in itertools.combinations(range(k), g):
+        cw = (coefs @ gamma[list(rows)].astype(np.int64)) % p
+        best = min(best, int((cw != 0).sum(axis=1).min()))
+    return best
+
+
+@pytest.mark.parametrize("name,g", [("f3_n30_k15", 3), ("f7_n40_k20", 3), ("f3_n80_k40", 2)])
+def test_single_pass_probe(name, g):
+    """One pass alone (termination off): every codeword of the pass is
+    evaluated (count = closed-form size), the least weight found equals the
+    brute-force minimum over the pass, a seeded bound at that minimum keeps
+    it, and a seeded bound below it is returned unchanged with no witness."""
+    code = inputs.single(name)
+    pr = B.fpcode_prepare(code.p, code.n, code.k, code.G, B.fpcode_opts_default(budget=0))
+    passes = B.fpcode_prepared_passes(pr)
+    idx = next(i for i, x in enumerate(passes) if x[0] == g and x[1] == 0)
+    gamma, _ = B.fpcode_prepared_gamma(pr, 0)
+    want = _pass_minimum(gamma, code.p, g)
+    for u_init, expect_u, witness in ((0, want, True), (want, want, True), (want - 1, want - 1, False)):
+        q = B.fpcode_prepared_single_pass(pr, idx, u_init)
+        B.fpcode_prepared_upload(q)
+        B.fpcode_search_enqueue(q)
+        r = B.fpcode_search_finish(q)
+        assert r.status == B.EBUDGET
+        assert r.counts[g] == passes[idx][5] == math.comb(code.k, g) * (code.p - 1) ** (g - 1)
+        assert sum(r.counts) == passes[idx][5]
+        assert r.U == expect_u
+        if witness:
+            check_witness(code, want, r.witness)
 
 
 def test_bounded_wait_reports_timeout():
