@@ -201,6 +201,23 @@ def test_batch_against_oracle_mixed_primes():
             check_witness(c, rb.d, rb.witness)
 
 
+def test_batch512_sample_against_oracle():
+    """The batched workload at its bench size (512 codes, budget 10^8
+    codewords per code, one launch): a fixed sample spread over the batch
+    matches the oracle run alone at the same budget (status, d, per-level
+    counts, L, U) with a valid witness."""
+    codes = inputs.batch_codes(512)
+    budget = 10 ** 8
+    res = B.fpcode_min_distance_batch(codes, budgets=[budget] * len(codes))
+    for i in range(0, 512, 51):
+        c, rb = codes[i], res[i]
+        r = oracle.bz(c, budget=budget, threads=os.cpu_count() or 4)
+        assert (rb.status, rb.counts, rb.L, rb.U) == (status_of_oracle(r.status), r.counts, r.L, r.U), i
+        if r.status == oracle.OK:
+            assert rb.d == r.d
+            check_witness(c, rb.d, rb.witness)
+
+
 def test_batch_mixed_widths_against_oracle():
     """Codes of one, two and three words per slice in one batch run in the
     narrow and the wide batched kernels; each matches the oracle."""

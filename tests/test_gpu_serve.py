@@ -11,7 +11,10 @@ import time
 import numpy as np
 import pytest
 
+import os
+
 import gf
+import oracle
 from paper_2603_29942_gb300 import _binding as B
 from paper_2603_29942_gb300 import inputs
 
@@ -125,3 +128,33 @@ def test_serve_word_limit():
     got = dict(B.fpcode_serve_poll(srv))
     B.fpcode_serve_destroy(srv)
     _check(wide, got[t], _alone(wide, 10 ** 6))
+
+
+def test_serve_stream_sample_against_oracle():
+    """The serving workload's first 64 requests at the bench budget (10^8
+    codewords per code), all admitted together so that they share the
+    persistent kernel: a fixed sample matches the oracle run alone at the
+    same budget (status, d, per-level counts, L, U) with a valid witness."""
+    codes, _ = inputs.serve_codes(count=64)
+    budget = 10 ** 8
+    srv = B.fpcode_serve_create(B.fpcode_serve_opts_default(slots=64))
+    tickets = {}
+    for i, c in enumerate(codes):
+        t = B.fpcode_serve_submit(srv, c, budget=budget)
+        assert t is not None
+        tickets[t] = i
+    B.fpcode_serve_drain(srv)
+    results = {tickets[t]: r for t, r in B.fpcode_serve_poll(srv)}
+    B.fpcode_serve_destroy(srv)
+    assert len(results) == len(codes)
+    status = {oracle.OK: B.OK, oracle.EBUDGET: B.EBUDGET}
+    for i in range(0, 64, 8):
+        c, rs = codes[i], results[i]
+        r = oracle.bz(c, budget=budget, threads=os.cpu_count() or 4)
+        assert (rs.status, rs.counts[:c.k + 1], rs.L, rs.U) == (status[r.status], r.counts, r.L, r.U), i
+        if r.status == oracle.OK:
+            assert rs.d == r.d
+            w = [int(x) for x in rs.witness[:c.n]]
+            assert gf.weight(w) == r.d
+            for h in gf.null_space(c.G.tolist(), c.p):
+                assert sum(a * b for a, b in zip(h, w)) % c.p == 0
