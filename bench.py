@@ -95,6 +95,56 @@ def dist_env():
     return rank, world, local
 
 
+def dist_init(world: int, local: int, backend: str = "nccl") -> None:
+    """One process per GPU (torchrun); nothing to do for a single rank."""
+    if world <= 1:
+        return
+    import torch
+    import torch.distributed as dist
+
+    if dist.is_initialized():
+        return
+    if backend == "nccl":
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        dist.init_process_group(backend)
+
+
+def shard(n: int, rank: int, world: int) -> range:
+    """The contiguous block of n independent units (codes) rank `rank` of
+    `world` takes: n split evenly, the first n % world ranks one more."""
+    base, extra = divmod(n, world)
+    lo = rank * base + min(rank, extra)
+    return range(lo, lo + base + (1 if rank < extra else 0))
+
+
+def sum_over_ranks(x: float, world: int) -> float:
+    """The total of a per-rank count over all ranks."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    dev = torch.device("cuda") if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    """The largest value over all ranks (a job takes as long as its slowest
+    rank); barrier semantics come with the collective."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    dev = torch.device("cuda") if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during a region."""
 
@@ -290,34 +340,40 @@ def run_batch(args, rank, world, local):
                               "workloads only; batch512 has no reference arm"}))
         return
     torch, B = _cuda(local)
-    codes = inputs.batch_codes(512)
+    dist_init(world, local)
+    all_codes = inputs.batch_codes(512)
+    codes = [all_codes[i] for i in shard(len(all_codes), rank, world)]  # codes are independent: no exchange
     budget = int(args.budget)
     budgets = [budget] * len(codes)
     stream = torch.cuda.Stream()
     for _ in range(args.warmup):
         res = B.fpcode_min_distance_batch(codes, stream, budgets=budgets, want_witness=False)
     torch.cuda.synchronize()
+    max_over_ranks(0.0, world)  # barrier
     with ClockSampler(local) as clk:
         t0 = time.perf_counter()
         for _ in range(args.steps):
             res = B.fpcode_min_distance_batch(codes, stream, budgets=budgets, want_witness=True)
-        t_batch = (time.perf_counter() - t0) / args.steps
+        torch.cuda.synchronize()
+        t_batch = max_over_ranks((time.perf_counter() - t0) / args.steps, world)
         # the plain form: one launch per code, same budget
         t0 = time.perf_counter()
         for c in codes:
             B.fpcode_min_distance_batch([c], stream, budgets=[budget], want_witness=True)
-        t_single = time.perf_counter() - t0
-    certified = sum(r.status == B.OK for r in res)
-    work = sum(r.enumerated for r in res)
+        torch.cuda.synchronize()
+        t_single = max_over_ranks(time.perf_counter() - t0, world)
+    certified = int(sum_over_ranks(sum(r.status == B.OK for r in res), world))
+    work = int(sum_over_ranks(sum(r.enumerated for r in res), world))
     line = {
-        "metric": "codes_per_s", "value": world * len(codes) / t_batch, "unit": "codes/s", "n_gpus": world,
+        "metric": "codes_per_s", "value": len(all_codes) / t_batch, "unit": "codes/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_batch, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": "batch512", "description": WORKLOADS["batch512"], "budget_per_code": budget,
-                   "certified": certified, "budget_limited": len(codes) - certified,
+                   "certified": certified, "budget_limited": len(all_codes) - certified,
+                   "shard": "the 512 codes split into contiguous blocks, one per rank" if world > 1 else "one GPU",
                    "codewords_per_step": work, "kernel_ms": res[0].t_kernel_ms,
                    "timing": "end to end from host matrices (host preparation on all cores, H2D, one launch, D2H)"},
-        "per_code": {"codes_per_s": len(codes) / t_single, "ms_total": 1e3 * t_single,
+        "per_code": {"codes_per_s": len(all_codes) / t_single, "ms_total": 1e3 * t_single,
                      "form": "fpcode_min_distance_batch on one code at a time (one launch per code)"},
         "batched_over_per_code": t_single / t_batch,
         "gpu_launches": args.steps,
@@ -336,6 +392,8 @@ def run_serve(args, rank, world, local):
             print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle is timed on the single-code "
                               "workloads only; serve has no reference arm"}))
         return
+    if rank != 0:
+        return  # one request stream, served by one GPU (the other ranks hold none)
     torch, B = _cuda(local)
     codes, arrivals = inputs.serve_codes()
     n_req = min(args.requests, len(codes))
@@ -375,7 +433,7 @@ def run_serve(args, rank, world, local):
     certified = sum(r.status == B.OK for r in results.values())
     pct = lambda q: lat[min(len(lat) - 1, int(q * len(lat)))]
     line = {
-        "metric": "codes_per_s", "value": world * n_req / elapsed, "unit": "codes/s", "n_gpus": world,
+        "metric": "codes_per_s", "value": n_req / elapsed, "unit": "codes/s", "n_gpus": 1,
         "steps": 1, "warmup": 1, "ms_per_step": 1e3 * elapsed, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": "serve", "description": WORKLOADS["serve"], "requests": n_req,
@@ -419,10 +477,7 @@ def main():
     import torch
 
     torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dist_init(world, local)
 
     from paper_2603_29942_gb300 import _binding as B
     from paper_2603_29942_gb300 import build as _b
@@ -460,10 +515,7 @@ def main():
     t_ms = sum(step_ms)
     codewords = r.enumerated  # evaluated per step (the last step; all steps enumerate the same passes)
     counts_total = sum(r.counts)
-    if world > 1:
-        t = torch.tensor([t_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(t.item())
+    t_ms = max_over_ranks(t_ms, world)
     value = world * codewords * args.steps / (t_ms * 1e-3)
 
     # --- e2e: public API from host matrices, with copies ---
