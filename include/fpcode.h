@@ -145,6 +145,34 @@ int fpcode_search_enqueue(fpcode_prepared *prep, void *stream, const fpcode_opts
  * rebuilt exactly from its Gamma_j rows and checked to have weight d. */
 int fpcode_search_finish(fpcode_prepared *prep, void *stream, fpcode_result *res, uint8_t *witness);
 
+/* Checkpoint of a search that stopped at its budget without certifying
+ * (status FPCODE_EBUDGET): the state of Sec. 3.1 Alg. 6 between two passes,
+ * i.e. how many passes of the schedule are complete and the best codeword
+ * found.  A later search of the same code, prepared with the same
+ * per_round_check and defer and a larger budget (its schedule starts with
+ * the same passes), continues from it with fpcode_search_resume instead of
+ * starting over.  The result equals that of one search with the larger
+ * budget, except that `enumerated` counts the codewords of the resumed run
+ * only.  The paper has no counterpart: it budgets nothing. */
+typedef struct fpcode_checkpoint {
+  int p, n, k;
+  int passes_done;     /* passes 0 .. passes_done - 1 of the schedule are complete */
+  uint64_t best_key;   /* packed key of the best codeword found (all ones: none) */
+  uint64_t code_hash;  /* FNV-1a of (p, n, k, per_round_check, defer) and G */
+} fpcode_checkpoint;
+
+/* After fpcode_search_finish returned FPCODE_EBUDGET: the checkpoint of that
+ * search.  FPCODE_EINVAL if the last search certified, timed out or never
+ * ran. */
+int fpcode_search_checkpoint(const fpcode_prepared *prep, fpcode_checkpoint *out);
+
+/* Like fpcode_search_enqueue, but the search starts after the checkpoint's
+ * passes with its best codeword as the bound; pair with
+ * fpcode_search_finish.  FPCODE_EINVAL if the checkpoint is of another code
+ * or other schedule options, if `prep`'s schedule has no pass after it, or
+ * if `prep` is not uploaded. */
+int fpcode_search_resume(fpcode_prepared *prep, const fpcode_checkpoint *ck, void *stream, const fpcode_opts *opts);
+
 /* Upload (if needed) + enqueue + finish. */
 int fpcode_min_distance_ex(fpcode_prepared *prep, void *stream, const fpcode_opts *opts, fpcode_result *res,
                            uint8_t *witness);

@@ -75,6 +75,17 @@ class fpcode_desc(ctypes.Structure):
     ]
 
 
+class fpcode_checkpoint(ctypes.Structure):
+    _fields_ = [
+        ("p", ctypes.c_int),
+        ("n", ctypes.c_int),
+        ("k", ctypes.c_int),
+        ("passes_done", ctypes.c_int),
+        ("best_key", ctypes.c_uint64),
+        ("code_hash", ctypes.c_uint64),
+    ]
+
+
 class fpcode_serve_opts(ctypes.Structure):
     _fields_ = [
         ("slots", ctypes.c_int),
@@ -153,6 +164,9 @@ def _declare(lib):
         "fpcode_test_pass_times": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
         "fpcode_prepared_bytes": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
         "fpcode_prepared_single_pass": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_VP)]),
+        "fpcode_search_checkpoint": (ctypes.c_int, [_VP, ctypes.POINTER(fpcode_checkpoint)]),
+        "fpcode_search_resume": (ctypes.c_int, [_VP, ctypes.POINTER(fpcode_checkpoint), _VP,
+                                                ctypes.POINTER(fpcode_opts)]),
     }
     found = []
     for name, (res, args) in sig.items():
@@ -278,6 +292,21 @@ def fpcode_search_finish(prep: Prepared, stream=None, want_witness: bool = True)
                                       w.ctypes.data_as(_U8P) if want_witness else None),
            "fpcode_search_finish", ok=(OK, EBUDGET, ETIMEOUT))
     return Result.of(r, prep.k, w if (want_witness and r.U <= prep.n) else None)
+
+
+def fpcode_search_checkpoint(prep: Prepared) -> fpcode_checkpoint:
+    """State after a search that stopped at its budget (status EBUDGET)."""
+    ck = fpcode_checkpoint()
+    _check(lib().fpcode_search_checkpoint(prep.handle, ctypes.byref(ck)), "fpcode_search_checkpoint")
+    return ck
+
+
+def fpcode_search_resume(prep: Prepared, ck: fpcode_checkpoint, stream=None,
+                         opts: fpcode_opts | None = None) -> None:
+    """Enqueue a search that continues after checkpoint `ck` (pair with
+    fpcode_search_finish)."""
+    _check(lib().fpcode_search_resume(prep.handle, ctypes.byref(ck), _stream(stream),
+                                      ctypes.byref(opts) if opts else None), "fpcode_search_resume")
 
 
 def fpcode_min_distance_ex(prep: Prepared, stream=None, opts: fpcode_opts | None = None) -> Result:

@@ -272,6 +272,23 @@ int enqueue_one(fpcode_prepared *prep, cudaStream_t st, const fpcode_opts &o) {
   fph::Prepared &P = prep->host;
   Layout L = make_layout({&P});
   FP_CUDA(cudaMemsetAsync(prep->dev + L.off_states, 0, L.dyn_bytes + L.aux_bytes, st));
+  if (prep->resume_from > 0) {  // continue after a checkpoint: next task, frontier, bound
+    const fpk::PassDesc &d = P.passes[prep->resume_from];
+    static thread_local unsigned long long word, key;
+    static thread_local int32_t frontier, useq;
+    word = (unsigned long long)d.task_base;
+    key = prep->resume_key == fpk::kNoKey ? 0ull : ~prep->resume_key;
+    frontier = prep->resume_from;
+    useq = prep->resume_key == fpk::kNoKey ? 0 : (int32_t)fpk::key_weight(prep->resume_key);
+    char *stp = prep->dev + L.off_states;
+    FP_CUDA(cudaMemcpyAsync(stp + offsetof(SlotState, word), &word, 8, cudaMemcpyHostToDevice, st));
+    FP_CUDA(cudaMemcpyAsync(stp + offsetof(SlotState, best_key), &key, 8, cudaMemcpyHostToDevice, st));
+    FP_CUDA(cudaMemcpyAsync(stp + offsetof(SlotState, frontier), &frontier, 4, cudaMemcpyHostToDevice, st));
+    FP_CUDA(cudaMemcpyAsync(prep->dev + L.off_aux + offsetof(fpk::SlotAux, useq_after) +
+                                (size_t)(prep->resume_from - 1) * sizeof(int32_t),
+                            &useq, 4, cudaMemcpyHostToDevice, st));
+    prep->resume_from = 0;  // one search
+  }
   if (prep->init_u > 0) {  // the bound as a key past every real one (pass 255), stored inverted
     static thread_local unsigned long long seed;
     seed = ~fpk::make_key((uint32_t)prep->init_u, 255u, (1ull << 34) - 1, 63u, 255u);
@@ -300,7 +317,11 @@ int finish_one(fpcode_prepared *prep, cudaStream_t st, fpcode_result *res, uint8
   CtlDyn dyn;
   std::memcpy(&s, prep->pinned, sizeof(s));
   std::memcpy(&dyn, prep->pinned + prep->dyn_bytes - sizeof(CtlDyn), sizeof(dyn));
-  int rc = fph::decode_result(P, outcome_of(s, dyn), res, witness);
+  const fph::DeviceOutcome oc = outcome_of(s, dyn);
+  prep->last_status = oc.status;
+  prep->last_stop = oc.stop_pass;
+  prep->last_key = oc.best_key;
+  int rc = fph::decode_result(P, oc, res, witness);
   float ms = 0;
   if (cudaEventElapsedTime(&ms, (cudaEvent_t)prep->ev0, (cudaEvent_t)prep->ev1) == cudaSuccess) res->t_kernel_ms = ms;
   return rc;
@@ -416,6 +437,48 @@ int fpcode_search_enqueue(fpcode_prepared *prep, void *stream, const fpcode_opts
     return FPCODE_EINVAL;
   }
   return enqueue_one(prep, (cudaStream_t)stream, opts ? *opts : prep->host.opts);
+}
+
+int fpcode_search_checkpoint(const fpcode_prepared *prep, fpcode_checkpoint *out) {
+  if (!prep || !out) return FPCODE_EINVAL;
+  const fph::Prepared &P = prep->host;
+  // a search that ran every pass of its schedule and stopped at the budget
+  if (prep->last_status != FPCODE_EBUDGET || prep->last_stop + 1 != (int)P.passes.size() || P.complete) {
+    fph::set_error("fpcode_search_checkpoint: the last search did not stop at its budget after its last pass");
+    return FPCODE_EINVAL;
+  }
+  std::memset(out, 0, sizeof(*out));
+  out->p = P.p;
+  out->n = P.n;
+  out->k = P.k;
+  out->passes_done = prep->last_stop + 1;
+  out->best_key = prep->last_key;
+  out->code_hash = P.code_hash;
+  return FPCODE_OK;
+}
+
+int fpcode_search_resume(fpcode_prepared *prep, const fpcode_checkpoint *ck, void *stream, const fpcode_opts *opts) {
+  if (!prep || !ck) return FPCODE_EINVAL;
+  const fph::Prepared &P = prep->host;
+  if (ck->p != P.p || ck->n != P.n || ck->k != P.k || ck->code_hash != P.code_hash) {
+    fph::set_error("fpcode_search_resume: the checkpoint is of another code or other schedule options");
+    return FPCODE_EINVAL;
+  }
+  if (ck->passes_done < 1 || ck->passes_done >= (int)P.passes.size()) {
+    fph::set_error("fpcode_search_resume: the schedule has no pass after the checkpoint (raise the budget)");
+    return FPCODE_EINVAL;
+  }
+  if (ck->best_key != fpk::kNoKey && (int)fpk::key_pass(ck->best_key) >= ck->passes_done) {
+    fph::set_error("fpcode_search_resume: the checkpoint's best key is not of a completed pass");
+    return FPCODE_EINVAL;
+  }
+  if (!prep->uploaded) {
+    fph::set_error("fpcode_search_resume: not uploaded");
+    return FPCODE_EINVAL;
+  }
+  prep->resume_from = ck->passes_done;
+  prep->resume_key = ck->best_key;
+  return enqueue_one(prep, (cudaStream_t)stream, opts ? *opts : P.opts);
 }
 
 int fpcode_search_finish(fpcode_prepared *prep, void *stream, fpcode_result *res, uint8_t *witness) {

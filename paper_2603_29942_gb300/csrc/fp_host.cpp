@@ -161,6 +161,25 @@ int prepare(int p, int n, int k, const uint8_t *G, const fpcode_opts &opts, Prep
   P->n = n;
   P->k = k;
   P->opts = opts;
+  {  // identity of the code and of the options that shape its schedule
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&h](uint64_t v) {
+      for (int b = 0; b < 8; ++b) {
+        h ^= (v >> (8 * b)) & 0xFF;
+        h *= 1099511628211ull;
+      }
+    };
+    mix((uint64_t)p);
+    mix((uint64_t)n);
+    mix((uint64_t)k);
+    mix((uint64_t)opts.per_round_check);
+    mix((uint64_t)opts.defer);
+    for (size_t i = 0; i < (size_t)k * n; ++i) {
+      h ^= G[i];
+      h *= 1099511628211ull;
+    }
+    P->code_hash = h;
+  }
   P->r = fpbs::bits_for(p);
   P->W = std::max(1, ceil_div(n - k, 32));
   P->rwpad = (P->r * P->W + 3) & ~3;

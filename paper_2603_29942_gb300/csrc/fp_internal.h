@@ -34,6 +34,7 @@ struct Prepared {
   std::vector<uint32_t> table;   // m * k * (p-1) * rwpad bit-sliced multiples
   std::vector<fpk::PassDesc> passes;
   int complete = 0;              // schedule reaches the last level
+  uint64_t code_hash = 0;        // FNV-1a of (p, n, k, per_round_check, defer) and G: the schedule's identity
   int L0 = 0;                    // lower bound before any pass
   double t_prepare_ms = 0;
   size_t table_words_per_set() const { return (size_t)k * ((size_t)(p - 1) * rwpad + fpk::sig_words(p, r, W)); }
@@ -65,6 +66,11 @@ struct fpcode_prepared {
   int ctas = 0;         // grid the tasks were planned for
   int smem = 0;         // dynamic shared memory of one launch
   int init_u = 0;       // > 0: the search starts with this upper bound (single-pass probes)
+  int resume_from = 0;  // > 0: the next search starts at this pass (fpcode_search_resume)
+  uint64_t resume_key = ~0ull;  // ... with this best key
+  int last_status = -100;       // outcome of the last finished search (for checkpoints)
+  int last_stop = -1;
+  uint64_t last_key = ~0ull;
   bool uploaded = false;
   bool external = false;  // device/pinned buffers borrowed from a workspace
   char *dev = nullptr;    // [CtlStatic][SlotDesc][PassDesc...][table] [SlotState][CtlDyn]

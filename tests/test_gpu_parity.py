@@ -269,6 +269,31 @@ def test_single_pass_probe(name, g):
             check_witness(code, want, r.witness)
 
 
+@pytest.mark.parametrize("name", ["f7_n40_k20", "f3_n80_k40"])
+def test_checkpoint_resume_equals_one_search(name):
+    """A search stopped at a small budget, checkpointed and resumed twice
+    with larger budgets ends exactly as one unbounded search: status, d,
+    L, U and per-level counts; a valid witness."""
+    code = inputs.single(name)
+    ref, _ = run(code)
+    pr = B.fpcode_prepare(code.p, code.n, code.k, code.G, B.fpcode_opts_default(budget=10 ** 5))
+    B.fpcode_prepared_upload(pr)
+    B.fpcode_search_enqueue(pr)
+    r = B.fpcode_search_finish(pr)
+    assert r.status == B.EBUDGET
+    ck = B.fpcode_search_checkpoint(pr)
+    for budget in (3 * 10 ** 6, 0):
+        pr = B.fpcode_prepare(code.p, code.n, code.k, code.G, B.fpcode_opts_default(budget=budget))
+        B.fpcode_prepared_upload(pr)
+        B.fpcode_search_resume(pr, ck)
+        r = B.fpcode_search_finish(pr)
+        if r.status == B.EBUDGET:
+            ck = B.fpcode_search_checkpoint(pr)
+    assert r.status == B.OK
+    assert (r.d, r.L, r.U, r.counts, r.m, r.kj) == (ref.d, ref.L, ref.U, ref.counts, ref.m, ref.kj)
+    check_witness(code, r.d, r.witness)
+
+
 def test_bounded_wait_reports_timeout():
     """A hand-off wait limit far below a task's duration makes the waiting
     CTAs give up and the kernel return; the host reports ETIMEOUT and the

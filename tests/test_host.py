@@ -377,3 +377,50 @@ def test_schedule_stays_within_staged_binomial_columns():
         assert B.fpcode_prepared_shape(pr)[3] is complete
         if complete:
             assert gmax == 24
+
+
+def test_checkpoint_and_resume_validation(lib):
+    """Checkpoints exist only after a search that stopped at its budget, and
+    a resume refuses a checkpoint of another code, of other schedule
+    options, or one the schedule does not reach past (all before any
+    device work)."""
+    code = inputs.single("f7_n40_k20")
+    pr = B.fpcode_prepare(code.p, code.n, code.k, code.G, B.fpcode_opts_default(budget=10 ** 6))
+    with pytest.raises(B.FpcodeError) as e:
+        B.fpcode_search_checkpoint(pr)
+    assert e.value.status == B.EINVAL
+    npasses = len(B.fpcode_prepared_passes(pr))
+    other = inputs.single_code(5, code.p, code.n, code.k)
+    pr_other = B.fpcode_prepare(other.p, other.n, other.k, other.G, B.fpcode_opts_default(budget=10 ** 6))
+    pr_lit = B.fpcode_prepare(code.p, code.n, code.k, code.G,
+                              B.fpcode_opts_default(budget=10 ** 6, per_round_check=1))
+    ck = B.fpcode_checkpoint(code.p, code.n, code.k, 2, ~0 & 0xFFFFFFFFFFFFFFFF, 0)
+    for target in (pr, pr_other, pr_lit):  # wrong hash for all three (0)
+        with pytest.raises(B.FpcodeError, match="another code"):
+            B.fpcode_search_resume(target, ck)
+    # a checkpoint of this code taken at the end of a shorter schedule ...
+    short = B.fpcode_prepare(code.p, code.n, code.k, code.G, B.fpcode_opts_default(budget=10 ** 5))
+    h = _code_hash(short)
+    ck = B.fpcode_checkpoint(code.p, code.n, code.k, npasses, ~0 & 0xFFFFFFFFFFFFFFFF, h)
+    with pytest.raises(B.FpcodeError, match="no pass after"):
+        B.fpcode_search_resume(pr, ck)
+    ck.passes_done = 2
+    with pytest.raises(B.FpcodeError, match="not uploaded"):
+        B.fpcode_search_resume(pr, ck)  # valid checkpoint, but nothing on the device yet
+
+
+def _code_hash(prep):
+    """The code identity the library stores (FNV-1a of p, n, k, the two
+    schedule options and G), recomputed here from its definition."""
+    h = 1469598103934665603
+    def mix(v, nbytes=8):
+        nonlocal h
+        for b in range(nbytes):
+            h ^= (v >> (8 * b)) & 0xFF
+            h = (h * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+    code = inputs.single("f7_n40_k20")
+    for v in (code.p, code.n, code.k, 0, 1):  # per_round_check 0, defer 1 (defaults)
+        mix(v)
+    for byte in np.asarray(code.G, dtype=np.uint8).reshape(-1):
+        mix(int(byte), 1)
+    return h
