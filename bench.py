@@ -49,6 +49,8 @@ WORKLOADS = {
     "f3_n80_k40": "F_3 [80,40] random systematic code G=[I|A], A uniform, PCG64 seed 2",
     "f7_n40_k20": "F_7 [40,20] random systematic code G=[I|A], A uniform, PCG64 seed 1",
     "f3_n30_k15": "F_3 [30,15] random systematic code G=[I|A], A uniform, PCG64 seed 0",
+    "additions_f3": "10 000 pairs of F_3 vectors of 512 symbols added 10 000 times (Sec. 5.1 workload)",
+    "additions_f7": "10 000 pairs of F_7 vectors of 512 symbols added 10 000 times (Sec. 5.1 workload)",
     "probe_f3_n80_k40_g8": "one pass (g=8, Gamma_1) of the F_3 [80,40] code alone, termination off, U seeded at d: "
                            "C(40,8) 2^7 = 9 843 799 680 codewords",
     "probe_f7_n40_k20_g7": "one pass (g=7, Gamma_1) of the F_7 [40,20] code alone, termination off, U seeded at d: "
@@ -256,6 +258,52 @@ def _cuda(local):
 
 
 PROBES = {"probe_f3_n80_k40_g8": ("f3_n80_k40", 8), "probe_f7_n40_k20_g7": ("f7_n40_k20", 7)}
+ADDITIONS = {"additions_f3": 3, "additions_f7": 7}
+
+
+def run_additions(args, rank, world, local):
+    """The additions benchmark of Sec. 5.1 on the GPU: two sets of 10 000
+    vectors of 512 symbols added pairwise 10 000 times (a dependent chain),
+    bit-sliced against one symbol per byte."""
+    import numpy as np
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle is timed on the certified "
+                              "single-code searches; the additions benchmark has no reference arm"}))
+        return
+    if rank != 0:
+        return
+    torch, B = _cuda(local)
+    p = ADDITIONS[args.workload]
+    nvec, nsym, reps = 10_000, 512, 10_000
+    rng = np.random.default_rng(5)
+    a = rng.integers(0, p, size=(nvec, nsym), dtype=np.uint8)
+    b = rng.integers(0, p, size=(nvec, nsym), dtype=np.uint8)
+    want = ((a.astype(np.int64) + reps * b.astype(np.int64)) % p).astype(np.uint8)
+    rates, times = {}, {}
+    with ClockSampler(local) as clk:
+        for form, sliced in (("sliced", True), ("bytes", False)):
+            B.fpcode_bench_additions(p, a[:64], b[:64], 10, sliced)  # warm-up
+            ms = []
+            for _ in range(max(1, min(args.steps, 5))):
+                out, t = B.fpcode_bench_additions(p, a, b, reps, sliced)
+                assert np.array_equal(out, want)
+                ms.append(t)
+            times[form] = statistics.median(ms)
+            rates[form] = nvec * nsym * reps / (times[form] * 1e-3)
+    line = {
+        "metric": "symbol_additions_per_s", "value": rates["sliced"], "unit": "symbol additions/s", "n_gpus": 1,
+        "steps": max(1, min(args.steps, 5)), "warmup": 1, "ms_per_step": times["sliced"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": args.workload, "p": p, "vectors": nvec, "symbols": nsym, "repetitions": reps,
+                   "form": "bit-sliced natural encoding, 32 symbols per word and slice; repetitions chained",
+                   "bytes_form_ms": times["bytes"], "bytes_form_symbol_additions_per_s": rates["bytes"],
+                   "sliced_over_bytes": times["bytes"] / times["sliced"], "checked": "a + reps*b mod p, every symbol"},
+        "gpu_launches": 2 * max(1, min(args.steps, 5)),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
 
 
 def time_pass(torch, B, code, pr, idx, d, stream, steps, warmup):
@@ -467,6 +515,8 @@ def main():
         return run_batch(args, rank, world, local)
     if args.workload in PROBES:
         return run_probe(args, rank, world, local)
+    if args.workload in ADDITIONS:
+        return run_additions(args, rank, world, local)
     if args.workload == "serve":
         return run_serve(args, rank, world, local)
     code = inputs.single(args.workload)

@@ -79,6 +79,18 @@ int fpcode_test_pass_times(fpcode_prepared *prep, void *stream, double *us, int 
  * a codeword of the pass.  Owned by the caller (fpcode_prepared_free).
  * FPCODE_EINVAL: no such pass, or u_init outside 0..255. */
 int fpcode_prepared_single_pass(const fpcode_prepared *src, int pass, int u_init, fpcode_prepared **out);
+
+/* Additions benchmark (Sec. 5.1: two sets of vectors over F_p added
+ * pairwise, repeated): a and b are nvec x nsym symbols in [0, p) (host,
+ * row-major, caller-owned); the device computes out = a + reps * b (mod p)
+ * as a dependent chain of `reps` additions c <- c + b, in the bit-sliced
+ * natural encoding (sliced = 1: p = 3 or 7, 32 symbols per word and slice)
+ * or one symbol per byte with per-byte SIMD operations (sliced = 0: any
+ * odd prime p < 128).  *ms is the kernel time (CUDA events on `stream`).
+ * Allocates and frees its own device buffers.  FPCODE_EINVAL on bad
+ * arguments or a symbol >= p, FPCODE_ECUDA on a CUDA error. */
+int fpcode_bench_additions(int p, int sliced, int nvec, int nsym, int reps, const uint8_t *a, const uint8_t *b,
+                           uint8_t *out, void *stream, double *ms);
 /* Bytes one search moves: host-to-device (tables, schedule, descriptors)
  * and device-to-host (final state). */
 int fpcode_prepared_bytes(const fpcode_prepared *prep, uint64_t *h2d, uint64_t *d2h);

@@ -165,6 +165,9 @@ def _declare(lib):
         "fpcode_prepared_bytes": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
         "fpcode_prepared_single_pass": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_VP)]),
         "fpcode_search_checkpoint": (ctypes.c_int, [_VP, ctypes.POINTER(fpcode_checkpoint)]),
+        "fpcode_bench_additions": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                  ctypes.c_int, _U8P, _U8P, _U8P, _VP,
+                                                  ctypes.POINTER(ctypes.c_double)]),
         "fpcode_search_resume": (ctypes.c_int, [_VP, ctypes.POINTER(fpcode_checkpoint), _VP,
                                                 ctypes.POINTER(fpcode_opts)]),
     }
@@ -307,6 +310,21 @@ def fpcode_search_resume(prep: Prepared, ck: fpcode_checkpoint, stream=None,
     fpcode_search_finish)."""
     _check(lib().fpcode_search_resume(prep.handle, ctypes.byref(ck), _stream(stream),
                                       ctypes.byref(opts) if opts else None), "fpcode_search_resume")
+
+
+def fpcode_bench_additions(p: int, a, b, reps: int, sliced: bool, stream=None):
+    """Additions benchmark: (a + reps * b mod p, kernel ms) for nvec x nsym
+    symbol arrays a, b."""
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.uint8))
+    b = np.ascontiguousarray(np.asarray(b, dtype=np.uint8))
+    if a.shape != b.shape or a.ndim != 2:
+        raise ValueError("a and b must be nvec x nsym arrays of the same shape")
+    out = np.zeros_like(a)
+    ms = ctypes.c_double(0.0)
+    _check(lib().fpcode_bench_additions(int(p), int(bool(sliced)), a.shape[0], a.shape[1], int(reps),
+                                        a.ctypes.data_as(_U8P), b.ctypes.data_as(_U8P), out.ctypes.data_as(_U8P),
+                                        _stream(stream), ctypes.byref(ms)), "fpcode_bench_additions")
+    return out, ms.value
 
 
 def fpcode_min_distance_ex(prep: Prepared, stream=None, opts: fpcode_opts | None = None) -> Result:

@@ -294,6 +294,20 @@ def test_checkpoint_resume_equals_one_search(name):
     check_witness(code, r.d, r.witness)
 
 
+@pytest.mark.parametrize("p,sliced", [(3, True), (7, True), (3, False), (7, False), (5, False), (127, False)])
+def test_additions_benchmark_kernels(p, sliced):
+    """The additions benchmark's kernels give a + reps * b (mod p) on every
+    symbol, with ragged vector lengths (not a multiple of 32 or 4)."""
+    rng = np.random.default_rng(p + 100 * sliced)
+    a = rng.integers(0, p, size=(37, 517), dtype=np.uint8)
+    b = rng.integers(0, p, size=(37, 517), dtype=np.uint8)
+    for reps in (0, 1, 7, 100):
+        out, ms = B.fpcode_bench_additions(p, a, b, reps, sliced)
+        want = (a.astype(np.int64) + reps * b.astype(np.int64)) % p
+        assert np.array_equal(out, want.astype(np.uint8)), reps
+        assert ms >= 0
+
+
 def test_bounded_wait_reports_timeout():
     """A hand-off wait limit far below a task's duration makes the waiting
     CTAs give up and the kernel return; the host reports ETIMEOUT and the
