@@ -282,10 +282,15 @@ FP_HD Prefix prefix_unrank(const BT &B, uint64_t I, int k, int g, int b) {
 template <int DB, class BT>
 FP_HD int prefix_advance(const BT &B, Prefix &pf, uint64_t &ci, uint64_t &nq, uint64_t NC, int b, int L,
                          int *dir) {
-  if (ci + 1 < NC) {
-    int s = gray_step<DB>(&pf.d, b, L, dir);
-    ++ci;
-    return s;
+  if constexpr (DB == 1) {
+    // b = 2: the packed digits are the counter itself (ci is not kept)
+    if (pf.d + 1 < NC) return gray_step<DB>(&pf.d, b, L, dir);
+  } else {
+    if (ci + 1 < NC) {
+      int s = gray_step<DB>(&pf.d, b, L, dir);
+      ++ci;
+      return s;
+    }
   }
   ci = 0;
   pf.d = 0;

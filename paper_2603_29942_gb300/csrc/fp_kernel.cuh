@@ -342,8 +342,10 @@ __device__ void task_prefixes(const SlotDesc &sd, const PassDesc &pd, int pass, 
   // prefixes left to this lane (the current one included); its index is Iend - left
   uint32_t left = I < Iend ? (uint32_t)(Iend - I) : 0u;
   const uint32_t nsteps = (uint32_t)pl;
-  for (uint32_t step = 0; step < nsteps; ++step) {
-    if ((step & 15) == 15) {
+  uint32_t cw = (uint32_t)(k - 1 - pf.m) * (uint32_t)b;  // codewords of the current prefix (set at rebuilds)
+  uint32_t count32 = 0;                                   // codewords of this lane, flushed every 16 steps
+  for (uint32_t base = 0; base < nsteps; base += 16) {
+   if (base) {
       // a finished code only has tasks of passes past its stop left: drop
       // them; else take up the best weight recorded anywhere since
       int fin = 0, ub = 0;
@@ -355,6 +357,10 @@ __device__ void task_prefixes(const SlotDesc &sd, const PassDesc &pd, int pass, 
       if (__shfl_sync(0xffffffffu, fin, 0)) break;
       thr = min(thr, __shfl_sync(0xffffffffu, ub, 0) - g + 1);
     }
+    count += count32;
+    count32 = 0;
+    const uint32_t end = min(base + 16u, nsteps);
+   for (uint32_t step = base; step < end; ++step) {
     const bool act = left > 0;
     const int mlane = act ? pf.m : k;
     const int xs = (int)__reduce_min_sync(0xffffffffu, (unsigned)mlane) + 1;
@@ -400,7 +406,7 @@ __device__ void task_prefixes(const SlotDesc &sd, const PassDesc &pd, int pass, 
         }
       }
     }
-    if (act) count += (unsigned long long)(k - 1 - pf.m) * (unsigned long long)b;
+    if (act) count32 += cw;
     // advance to the next prefix
     if (left > 1) {
       int dir;
@@ -410,11 +416,14 @@ __device__ void task_prefixes(const SlotDesc &sd, const PassDesc &pd, int pass, 
         add_row<P, R, W>(s, tab, q, dir > 0 ? 1 : b, p);  // c -> c+1: +A; c -> c-1: +(p-1)A
       } else {
         build_sum<P, R, W, DB>(s, tab, pf, L, b, p, qrows);
+        cw = (uint32_t)(k - 1 - pf.m) * (uint32_t)b;
       }
       if constexpr (F::kMersenne) prefix_signature<R, W>(s, a);
     }
     left -= left > 0 ? 1u : 0u;
+   }
   }
+  count += count32;
 }
 
 // One kernel variant: prime P (0: any, from the descriptor), r slices, W
