@@ -78,6 +78,14 @@ FP_HD int ctz64(uint64_t x) {
 #endif
 }
 
+FP_HD int ctz32(uint32_t x) {
+#if defined(__CUDA_ARCH__)
+  return __ffs((int)x) - 1;
+#else
+  return __builtin_ctz(x);
+#endif
+}
+
 FP_HD int popc64(uint64_t x) {
 #if defined(__CUDA_ARCH__)
   return __popcll(x);
@@ -207,10 +215,14 @@ template <int DB>
 FP_HD int gray_step(uint64_t *d, int b, int L, int *dir) {
   if constexpr (DB == 1) {
     // b = 2: the counter is a binary number; its lowest 0 bit is the digit
-    // that moves, and the 1 bits below it wrap to 0
-    const int s = ctz64(~*d);
-    *d += 1;
-    *dir = (s + 1 < L && ((*d >> (s + 1)) & 1ull)) ? -1 : 1;
+    // that moves, and the 1 bits below it wrap to 0.  The schedule keeps
+    // L = g - 2 below the staged binomial columns, so the counter fits 32
+    // bits.
+    const uint32_t d32 = (uint32_t)*d;
+    const int s = ctz32(~d32);
+    const uint32_t n32 = d32 + 1u;
+    *d = n32;
+    *dir = (s + 1 < L && ((n32 >> (s + 1)) & 1u)) ? -1 : 1;
     return s;
   } else if constexpr (DB == 4) {
     // nibble digits: the lowest digit below b - 1 moves; those below it
