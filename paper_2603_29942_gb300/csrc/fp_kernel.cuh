@@ -227,11 +227,21 @@ struct LeafFilter {
   static constexpr int kPrefSig = kMersenne ? W * (R - 1) : 1;
   // leaves evaluated per vote: as many as the registers allow
   static constexpr int kUnroll = !kMersenne ? 1 : kSigW <= 4 ? 4 : kSigW <= 8 ? 2 : 1;
+  // The one-popcount bound of W > 1 words (popc of the words' OR) is used
+  // while the threshold is at most this: about 32 (1 - q^W) - 8, eight
+  // under the bound's mean for random symbols, where q is the chance that
+  // a position is zero in a word's pair mask (5/9 for p = 3, 13/49 for p = 7).
+  static constexpr int kQuickMax = P == 3 ? (W == 2 ? 14 : W == 3 ? 18 : 21) : P == 7 ? (W == 2 ? 21 : 23) : 0;
 };
 
 // Lower bound on the redundant weight of S + c A[x] over every nonzero
 // leaf coefficient c: the least bound of the pairs {c, p - c}.
-template <int P, int R, int W, int NA>
+template <bool B>
+struct BoolTag {
+  static constexpr bool value = B;
+};
+
+template <int P, int R, int W, bool QUICK, int NA>
 __device__ __forceinline__ int pair_bound(const uint32_t (&s)[R * W], const uint32_t (&a)[NA], const uint32_t *sig,
                                           const uint32_t *tab, int x, int p) {
   using F = LeafFilter<P, R, W>;
@@ -243,15 +253,27 @@ __device__ __forceinline__ int pair_bound(const uint32_t (&s)[R * W], const uint
     constexpr int NP = (P - 1) / 2;
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
-      int lb = 0;
+      if constexpr (W > 1 && QUICK) {
+        // OR the words' masks before one popcount: popc(f_0 | f_1 | ...) is
+        // at most sum_w popc(f_w), so it is a lower bound too; weaker, so
+        // it is used only while the threshold is well under its mean
+        uint32_t u = 0;
 #pragma unroll
-      for (int w = 0; w < W; ++w) {
-        uint32_t f = 0;
+        for (int w = 0; w < W; ++w)
 #pragma unroll
-        for (int i = 0; i + 1 < R; ++i) f |= a[w * (R - 1) + i] ^ e[(q * W + w) * (R - 1) + i];
-        lb += __popc(f);
+          for (int i = 0; i + 1 < R; ++i) u |= a[w * (R - 1) + i] ^ e[(q * W + w) * (R - 1) + i];
+        best = min(best, __popc(u));
+      } else {
+        int lb = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+          uint32_t f = 0;
+#pragma unroll
+          for (int i = 0; i + 1 < R; ++i) f |= a[w * (R - 1) + i] ^ e[(q * W + w) * (R - 1) + i];
+          lb += __popc(f);
+        }
+        best = min(best, lb);
       }
-      best = min(best, lb);
     }
   } else {
     const int b = p - 1;
@@ -364,47 +386,58 @@ __device__ void task_prefixes(const SlotDesc &sd, const PassDesc &pd, int pass, 
     const bool act = left > 0;
     const int mlane = act ? pf.m : k;
     const int xs = (int)__reduce_min_sync(0xffffffffu, (unsigned)mlane) + 1;
-    if constexpr (UNR == 1) {
-      for (int x = xs; x < k; ++x) {  // lanes whose prefix reaches above x sit it out
-        const int tx = x > mlane ? thr : 0;
-        if (__any_sync(0xffffffffu, pair_bound<P, R, W>(s, a, sig, tab, x, p) < tx)) {
-          if (x > mlane) leaf_exact<P, R, W>(s, tab, x, p, g, pass, Iend - left, thr, st, ax);
-          thr = (int)__reduce_min_sync(0xffffffffu, (unsigned)thr);
-        }
-      }
-    } else {
-      // leaves above every active lane's largest row: no per-lane test needed
-      const int xu = max(xs, (int)__reduce_max_sync(0xffffffffu, (unsigned)(act ? pf.m + 1 : 0)));
-      for (int x = xs; x < xu; ++x) {  // lanes whose prefix reaches above x sit these out
-        const int tx = x > mlane ? thr : 0;
-        if (__any_sync(0xffffffffu, pair_bound<P, R, W>(s, a, sig, tab, x, p) < tx)) {
-          if (x > mlane) leaf_exact<P, R, W>(s, tab, x, p, g, pass, Iend - left, thr, st, ax);
-          thr = (int)__reduce_min_sync(0xffffffffu, (unsigned)thr);
-        }
-      }
-      int x = xu;
-      for (; x + UNR <= k; x += UNR) {
-        int lb[UNR];
-#pragma unroll
-        for (int u = 0; u < UNR; ++u) lb[u] = pair_bound<P, R, W>(s, a, sig, tab, x + u, p);
-        int lbm = lb[0];
-#pragma unroll
-        for (int u = 1; u < UNR; ++u) lbm = min(lbm, lb[u]);
-        if (__any_sync(0xffffffffu, act && lbm < thr)) {
-          if (act) {
-#pragma unroll
-            for (int u = 0; u < UNR; ++u)
-              if (lb[u] < thr) leaf_exact<P, R, W>(s, tab, x + u, p, g, pass, Iend - left, thr, st, ax);
+    // the leaves of this step, with the one-popcount bound (QUICK) or the
+    // per-word sum; the mode is picked once per step from the threshold
+    auto leaves = [&](auto quick_tag) {
+      constexpr bool QUICK = decltype(quick_tag)::value;
+      if constexpr (UNR == 1) {
+        for (int x = xs; x < k; ++x) {  // lanes whose prefix reaches above x sit it out
+          const int tx = x > mlane ? thr : 0;
+          if (__any_sync(0xffffffffu, pair_bound<P, R, W, QUICK>(s, a, sig, tab, x, p) < tx)) {
+            if (x > mlane) leaf_exact<P, R, W>(s, tab, x, p, g, pass, Iend - left, thr, st, ax);
+            thr = (int)__reduce_min_sync(0xffffffffu, (unsigned)thr);
           }
-          thr = (int)__reduce_min_sync(0xffffffffu, (unsigned)thr);
+        }
+      } else {
+        // leaves above every active lane's largest row: no per-lane test needed
+        const int xu = max(xs, (int)__reduce_max_sync(0xffffffffu, (unsigned)(act ? pf.m + 1 : 0)));
+        for (int x = xs; x < xu; ++x) {  // lanes whose prefix reaches above x sit these out
+          const int tx = x > mlane ? thr : 0;
+          if (__any_sync(0xffffffffu, pair_bound<P, R, W, QUICK>(s, a, sig, tab, x, p) < tx)) {
+            if (x > mlane) leaf_exact<P, R, W>(s, tab, x, p, g, pass, Iend - left, thr, st, ax);
+            thr = (int)__reduce_min_sync(0xffffffffu, (unsigned)thr);
+          }
+        }
+        int x = xu;
+        for (; x + UNR <= k; x += UNR) {
+          int lb[UNR];
+#pragma unroll
+          for (int u = 0; u < UNR; ++u) lb[u] = pair_bound<P, R, W, QUICK>(s, a, sig, tab, x + u, p);
+          int lbm = lb[0];
+#pragma unroll
+          for (int u = 1; u < UNR; ++u) lbm = min(lbm, lb[u]);
+          if (__any_sync(0xffffffffu, act && lbm < thr)) {
+            if (act) {
+#pragma unroll
+              for (int u = 0; u < UNR; ++u)
+                if (lb[u] < thr) leaf_exact<P, R, W>(s, tab, x + u, p, g, pass, Iend - left, thr, st, ax);
+            }
+            thr = (int)__reduce_min_sync(0xffffffffu, (unsigned)thr);
+          }
+        }
+        for (; x < k; ++x) {
+          if (__any_sync(0xffffffffu, act && pair_bound<P, R, W, QUICK>(s, a, sig, tab, x, p) < thr)) {
+            if (act) leaf_exact<P, R, W>(s, tab, x, p, g, pass, Iend - left, thr, st, ax);
+            thr = (int)__reduce_min_sync(0xffffffffu, (unsigned)thr);
+          }
         }
       }
-      for (; x < k; ++x) {
-        if (__any_sync(0xffffffffu, act && pair_bound<P, R, W>(s, a, sig, tab, x, p) < thr)) {
-          if (act) leaf_exact<P, R, W>(s, tab, x, p, g, pass, Iend - left, thr, st, ax);
-          thr = (int)__reduce_min_sync(0xffffffffu, (unsigned)thr);
-        }
-      }
+    };
+    if constexpr (W > 1 && UNR > 1) {  // single-code kernels; the batched ones keep one copy
+      if (thr <= F::kQuickMax) leaves(BoolTag<true>{});  // thr is the same on every lane here
+      else leaves(BoolTag<false>{});
+    } else {
+      leaves(BoolTag<false>{});
     }
     if (act) count32 += cw;
     // advance to the next prefix
