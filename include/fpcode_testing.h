@@ -57,11 +57,13 @@ int fpcode_prepared_shape(const fpcode_prepared *prep, int *m, int *kj, int *npa
 /* Gamma_j (k x n) and its pivot columns (k). */
 int fpcode_prepared_gamma(const fpcode_prepared *prep, int j, uint8_t *gamma, int *pivots);
 int fpcode_prepared_passes(const fpcode_prepared *prep, fpcode_pass_info *passes, int max);
-/* The CTA task ranges [lo, hi) of pass `pass` when planned for `ctas` CTAs
- * (fixed_pl > 0: fixed tasks of 256 * fixed_pl prefixes; 0: guided).
- * Returns the number of tasks (at most max written). */
-int fpcode_test_task_ranges(fpcode_prepared *prep, int pass, int ctas, int fixed_pl, uint64_t *lo, uint64_t *hi,
-                            int max);
+/* The CTA task ranges [lo, hi), in prefixes, of pass `pass` when planned
+ * for `ctas` CTAs (fixed_pl > 0: fixed tasks of 256 * fixed_pl prefixes; 0:
+ * guided, with fixed tasks of at least min_steps prefixes per lane for a pass
+ * too small to give every lane of the grid that many).  Returns the number
+ * of tasks (at most max written). */
+int fpcode_test_task_ranges(fpcode_prepared *prep, int pass, int ctas, int fixed_pl, int min_steps, uint64_t *lo,
+                            uint64_t *hi, int max);
 /* Microseconds from the start of the last search on `prep` to the end of
  * each of its passes (-1: not reached), for up to max passes.  Returns the
  * number of passes written, or -1. */

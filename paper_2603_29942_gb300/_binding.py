@@ -158,7 +158,7 @@ def _declare(lib):
         "fpcode_prepared_shape": (ctypes.c_int, [_VP, _IP, _IP, _IP, _IP]),
         "fpcode_prepared_gamma": (ctypes.c_int, [_VP, ctypes.c_int, _U8P, _IP]),
         "fpcode_prepared_passes": (ctypes.c_int, [_VP, ctypes.POINTER(fpcode_pass_info), ctypes.c_int]),
-        "fpcode_test_task_ranges": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+        "fpcode_test_task_ranges": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                    ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                                    ctypes.c_int]),
         "fpcode_test_pass_times": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
@@ -580,11 +580,11 @@ def fpcode_serve_destroy(server: Server) -> None:
         server.handle = None
 
 
-def fpcode_test_task_ranges(prep: Prepared, pass_index: int, ctas: int, fixed_pl: int = 0):
+def fpcode_test_task_ranges(prep: Prepared, pass_index: int, ctas: int, fixed_pl: int = 0, min_steps: int = 8):
     cap = 1 << 16
     lo = (ctypes.c_uint64 * cap)()
     hi = (ctypes.c_uint64 * cap)()
-    n = lib().fpcode_test_task_ranges(prep.handle, pass_index, ctas, fixed_pl, lo, hi, cap)
+    n = lib().fpcode_test_task_ranges(prep.handle, pass_index, ctas, fixed_pl, min_steps, lo, hi, cap)
     if n < 0:
         raise FpcodeError(EINVAL, "fpcode_test_task_ranges")
     return [(int(lo[i]), int(hi[i])) for i in range(min(n, cap))]

@@ -46,7 +46,16 @@ struct Prepared {
 int prepare(int p, int n, int k, const uint8_t *G, const fpcode_opts &opts, Prepared *out);
 
 // Tasks and prefixes per lane of every pass for a grid of `ctas` CTAs.
-void plan_tasks(Prepared *P, int ctas, int fixed_pl);
+// fixed_pl > 0: tasks of fixed_pl prefixes per lane everywhere.  Else a pass
+// too small to give every lane of the grid min_steps prefixes gets fixed
+// tasks of min_steps prefixes per lane (fewer tasks than CTAs), the others
+// guided tasks.  min_steps trades the latency of one small code (1: spread
+// each pass over the whole grid) against throughput (a lane's setup cost
+// shared by more prefixes).
+void plan_tasks(Prepared *P, int ctas, int fixed_pl, int min_steps);
+constexpr int kMinStepsSingle = 8;   // one code per launch
+constexpr int kMinStepsBatch = 32;   // many codes share the grid
+constexpr int kMinStepsServe = 1;    // streamed codes: latency first
 
 // Fill a result from the final device state of one code.
 struct DeviceOutcome {

@@ -40,7 +40,7 @@ struct PassDesc {
   int32_t L_before;   // lower bound before the pass (valid: earlier passes complete)
   int32_t L_after;    // lower bound once the pass is complete
   int32_t round_end;  // last pass of round g (per-round termination check)
-  int32_t pl;         // > 0: fixed tasks of kThreads * pl prefixes; 0: guided
+  int32_t pl;         // > 0: fixed tasks of kThreads * pl units; 0: guided
   uint32_t ntasks;    // CTA tasks in the pass
   uint32_t phases;    // guided: phases of plan_ctas tasks, each half the last (0: 256-prefix tasks)
   uint64_t nprefix;   // prefixes (g >= 2) or rows (g == 1)

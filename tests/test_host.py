@@ -338,17 +338,23 @@ def test_prepare_rejects_bad_input(lib):
         B.fpcode_prepare(3, 5, 2, rank_def)
 
 
-@pytest.mark.parametrize("ctas,fixed_pl", [(760, 0), (608, 0), (152, 0), (7, 0), (760, 3), (1, 0)])
-def test_task_ranges_tile_each_pass(ctas, fixed_pl, lib):
+@pytest.mark.parametrize("ctas,fixed_pl,min_steps", [(760, 0, 8), (608, 0, 8), (608, 0, 1), (608, 0, 32), (152, 0, 8),
+                                                     (7, 0, 8), (760, 3, 8), (1, 0, 8)])
+def test_task_ranges_tile_each_pass(ctas, fixed_pl, min_steps, lib):
     """Guided (shrinking) and fixed task ranges cover every prefix of a pass
-    exactly once, in order."""
+    exactly once, in order; a pass too small to give every lane of the grid
+    min_steps prefixes gets fewer tasks than CTAs, each (but the last)
+    giving every lane at least min_steps prefixes."""
     code = inputs.single("f3_n80_k40")
     pr = _prep(code)
     passes = B.fpcode_prepared_passes(pr)
     for i, (g, _j, _Lb, _La, _re, _size, nprefix) in enumerate(passes[:14]):
         if fixed_pl and nprefix > 256 * fixed_pl * 60000:
             continue  # more tasks than the hook returns
-        ranges = B.fpcode_test_task_ranges(pr, i, ctas, fixed_pl)
+        ranges = B.fpcode_test_task_ranges(pr, i, ctas, fixed_pl, min_steps)
+        if not fixed_pl and g > 1 and nprefix < 256 * ctas * min_steps:
+            assert len(ranges) <= ctas
+            assert all(hi - lo >= 256 * min_steps for lo, hi in ranges[:-1])
         if g == 1:
             assert ranges == [(0, nprefix)]
             continue
