@@ -60,8 +60,9 @@ int fpcode_prepared_passes(const fpcode_prepared *prep, fpcode_pass_info *passes
 /* The CTA task ranges [lo, hi), in prefixes, of pass `pass` when planned
  * for `ctas` CTAs (fixed_pl > 0: fixed tasks of 256 * fixed_pl prefixes; 0:
  * guided, with fixed tasks of at least min_steps prefixes per lane for a pass
- * too small to give every lane of the grid that many).  Returns the number
- * of tasks (at most max written). */
+ * too small to give every lane of the grid that many; with min_steps <= 8,
+ * as for one code, a pass under one prefix unit per lane of the grid gets one
+ * unit per lane).  Returns the number of tasks (at most max written). */
 int fpcode_test_task_ranges(fpcode_prepared *prep, int pass, int ctas, int fixed_pl, int min_steps, uint64_t *lo,
                             uint64_t *hi, int max);
 /* Microseconds from the start of the last search on `prep` to the end of

@@ -252,7 +252,7 @@ int upload_one(fpcode_prepared *prep, cudaStream_t st, DevCtx &c, char *d, char 
   int s = occupancy(fn, prep->smem, P.opts.ctas_per_sm, &per_sm);
   if (s) return s;
   prep->ctas = c.sms * per_sm;
-  fph::plan_tasks(&P, prep->ctas, P.opts.prefixes_per_lane, fph::kMinStepsSingle);
+  fph::plan_tasks(&P, prep->ctas, P.opts.prefixes_per_lane, fph::kMinStepsSingle, true);
   Layout L = make_layout({&P});
   prep->off_ctl = L.off_ctl;
   prep->off_slot = L.off_slots;
@@ -611,8 +611,9 @@ int fpcode_min_distance_batch(int num, const fpcode_desc *codes, void *stream, c
     s = occupancy(fn, smem, o.ctas_per_sm, &per_sm);
     if (s) break;
     const int ctas = c->sms * per_sm;
-    const int min_steps = idx.size() > 1 ? fph::kMinStepsBatch : fph::kMinStepsSingle;
-    for (int i : idx) fph::plan_tasks(preps[i].get(), ctas, o.prefixes_per_lane, min_steps);
+    const bool many = idx.size() > 1;
+    for (int i : idx)
+      fph::plan_tasks(preps[i].get(), ctas, o.prefixes_per_lane, many ? fph::kMinStepsBatch : fph::kMinStepsSingle, !many);
     Layout L = make_layout(codesv);
     s = ws_reserve(*c, L.total, std::max(L.static_bytes, L.dyn_bytes));
     if (s) break;

@@ -96,22 +96,26 @@ FP_HD int popc64(uint64_t x) {
 
 FP_HD uint64_t low_mask(int n) { return n >= 64 ? ~0ull : ((1ull << n) - 1ull); }
 
-// Subset of rank r in R(n, t), as a bit mask over {0..n-1}.
+// Subset of rank r in R(n, t), as a bit mask over {0..n-1}.  Top down, a
+// level n whose element n-1 is not a member keeps the rank (the subset lies
+// in the first half, R(n-1, t)); the largest member is therefore the largest
+// x with C(x, t) <= r, found by bisection (C(x, t) grows with x, and
+// C(t-1, t) = 0), and the rest is the subset of rank C(x+1, t) - 1 - r in
+// R(x, t-1) (the reflected second half).
 template <class BT>
 FP_HD uint64_t rd_unrank(const BT &B, uint64_t r, int n, int t) {
   uint64_t mask = 0;
   while (t > 0) {
-    if (t == n) {
-      mask |= low_mask(n);
-      break;
+    int lo = t - 1, hi = n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (B(mid, t) <= r) lo = mid;
+      else hi = mid - 1;
     }
-    uint64_t c = B(n - 1, t);
-    if (r >= c) {  // n-1 is in the subset; the tail part is reversed
-      mask |= 1ull << (n - 1);
-      r = B(n, t) - 1 - r;
-      --t;
-    }
-    --n;
+    mask |= 1ull << lo;
+    r = B(lo + 1, t) - 1 - r;
+    n = lo;
+    --t;
   }
   return mask;
 }
@@ -279,8 +283,14 @@ FP_HD Prefix prefix_unrank(const BT &B, uint64_t I, int k, int g, int b) {
   Prefix P;
   P.m = lo;
   uint64_t rem = I - prefixes_below(B, lo, g, NC);
-  P.qi = rem / NC;
-  uint64_t ci = rem - P.qi * NC;
+  uint64_t ci;
+  if constexpr (DB == 1) {  // b = 2: NC = 2^L
+    P.qi = rem >> L;
+    ci = rem & (NC - 1);
+  } else {
+    P.qi = rem / NC;
+    ci = rem - P.qi * NC;
+  }
   P.Q = rd_unrank(B, P.qi, P.m, L);
   P.d = counter_digits<DB>(ci, b, L);
   return P;

@@ -327,7 +327,7 @@ int prepare(int p, int n, int k, const uint8_t *G, const fpcode_opts &opts, Prep
   return FPCODE_OK;
 }
 
-void plan_tasks(Prepared *P, int ctas, int fixed_pl, int min_steps) {
+void plan_tasks(Prepared *P, int ctas, int fixed_pl, int min_steps, bool spread_tiny) {
   const uint64_t lanes = (uint64_t)fpk::kThreads;
   const uint64_t C = (uint64_t)std::max(1, ctas);
   const uint64_t b = (uint64_t)(P->p - 1);
@@ -360,6 +360,10 @@ void plan_tasks(Prepared *P, int ctas, int fixed_pl, int min_steps) {
     // up the following passes meanwhile; a lane's setup (unranking its first
     // prefix, summing its rows) then serves several prefixes
     const uint64_t umin = ((uint64_t)std::max(1, min_steps) + unit - 1) / unit;
+    if (spread_tiny && N <= lanes * C) {  // under one unit per lane of the grid: spread it wide
+      d.ntasks = (uint32_t)((N + lanes - 1) / lanes);
+      continue;
+    }
     if (N < lanes * C * umin) {
       d.pl = (int32_t)umin;
       d.ntasks = (uint32_t)((N + lanes * umin - 1) / (lanes * umin));
@@ -594,7 +598,7 @@ int fpcode_test_prefix_walk(uint64_t I, uint64_t steps, int k, int g, int p, int
 int fpcode_test_task_ranges(fpcode_prepared *prep, int pass, int ctas, int fixed_pl, int min_steps, uint64_t *lo,
                             uint64_t *hi, int max) {
   if (!prep || pass < 0 || pass >= (int)prep->host.passes.size() || !lo || !hi) return -1;
-  fph::plan_tasks(&prep->host, ctas, fixed_pl, min_steps);
+  fph::plan_tasks(&prep->host, ctas, fixed_pl, min_steps, min_steps <= fph::kMinStepsSingle);
   const fpk::PassDesc &d = prep->host.passes[pass];
   const int n = (int)std::min<uint64_t>(d.ntasks, (uint64_t)max);
   for (int t = 0; t < n; ++t) {

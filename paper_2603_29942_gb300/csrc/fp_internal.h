@@ -51,8 +51,11 @@ int prepare(int p, int n, int k, const uint8_t *G, const fpcode_opts &opts, Prep
 // tasks of min_steps prefixes per lane (fewer tasks than CTAs), the others
 // guided tasks.  min_steps trades the latency of one small code (1: spread
 // each pass over the whole grid) against throughput (a lane's setup cost
-// shared by more prefixes).
-void plan_tasks(Prepared *P, int ctas, int fixed_pl, int min_steps);
+// shared by more prefixes).  spread_tiny: a pass under one prefix unit per
+// lane of the grid still gets one unit per lane (the first passes of a
+// search run with a loose threshold, many exact leaves each, and sit on the
+// path to the first termination tests).
+void plan_tasks(Prepared *P, int ctas, int fixed_pl, int min_steps, bool spread_tiny);
 constexpr int kMinStepsSingle = 8;   // one code per launch
 constexpr int kMinStepsBatch = 32;   // many codes share the grid
 constexpr int kMinStepsServe = 1;    // streamed codes: latency first

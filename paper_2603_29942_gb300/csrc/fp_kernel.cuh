@@ -321,8 +321,8 @@ __device__ __forceinline__ void prefix_signature(const uint32_t (&s)[R * W], uin
 
 template <int P, int R, int W, int DB, int UNR>
 __device__ void task_prefixes(const SlotDesc &sd, const PassDesc &pd, int pass, const uint32_t *tab,
-                              const fpenum::BinomCols &B, uint64_t task, int U, SlotState *st, SlotAux *ax,
-                              unsigned long long &count) {
+                              const fpenum::BinomCols &B, uint64_t ulo, uint64_t uhi, int U, SlotState *st,
+                              SlotAux *ax, unsigned long long &count) {
   constexpr int RW = R * W;
   constexpr int RWP = Shape<R, W>::RWP;
   using F = LeafFilter<P, R, W>;
@@ -332,8 +332,6 @@ __device__ void task_prefixes(const SlotDesc &sd, const PassDesc &pd, int pass, 
   const int g = pd.g;
   const int L = g - 2;
   const uint32_t *sig = tab + k * b * RWP;  // pair signatures (Mersenne p)
-  uint64_t ulo, uhi;
-  task_range(pd, task, &ulo, &uhi);
   const uint64_t pu = (uhi - ulo + kThreads - 1) / kThreads;  // units per lane, same for the CTA
   const uint64_t unit = pd.unit;
   const uint64_t pl = pu * unit;                               // prefix steps
@@ -466,12 +464,12 @@ template <int P, int R, int W, int UNR = LeafFilter<P, R, W>::kUnroll>
 struct Fixed {
   static constexpr int DB = P == 3 ? 1 : (P == 5 || P == 7) ? 4 : 8;  // as the host's digit width
   static __device__ __forceinline__ void run(const SlotDesc &sd, const PassDesc &pd, int pass, const uint32_t *tab,
-                                             const fpenum::BinomCols &B, uint64_t task, int U, SlotState *st,
-                                             SlotAux *ax, unsigned long long &count) {
+                                             const fpenum::BinomCols &B, uint64_t ulo, uint64_t uhi, int U,
+                                             SlotState *st, SlotAux *ax, unsigned long long &count) {
     if (pd.g == 1) {
-      if (task == 0) task_rows<P, R, W>(sd, pass, tab, U, st, ax, count);
+      if (ulo == 0) task_rows<P, R, W>(sd, pass, tab, U, st, ax, count);
     } else {
-      task_prefixes<P, R, W, DB, UNR>(sd, pd, pass, tab, B, task, U, st, ax, count);
+      task_prefixes<P, R, W, DB, UNR>(sd, pd, pass, tab, B, ulo, uhi, U, st, ax, count);
     }
   }
 };
@@ -490,11 +488,11 @@ __host__ __device__ inline int variant_id(int p, int r, int W) {
 template <int WMAX>
 struct Multi357 {
   static __device__ __forceinline__ void run(const SlotDesc &sd, const PassDesc &pd, int pass, const uint32_t *tab,
-                                             const fpenum::BinomCols &B, uint64_t task, int U, SlotState *st,
-                                             SlotAux *ax, unsigned long long &count) {
+                                             const fpenum::BinomCols &B, uint64_t ulo, uint64_t uhi, int U,
+                                             SlotState *st, SlotAux *ax, unsigned long long &count) {
     switch (sd.variant) {
 #define FPK_CASE(id, P, R, W) \
-  case id: if constexpr (W <= WMAX) Fixed<P, R, W, 1>::run(sd, pd, pass, tab, B, task, U, st, ax, count); break;
+  case id: if constexpr (W <= WMAX) Fixed<P, R, W, 1>::run(sd, pd, pass, tab, B, ulo, uhi, U, st, ax, count); break;
       FPK_CASE(0, 3, 2, 1)
       FPK_CASE(1, 3, 2, 2)
       FPK_CASE(2, 3, 2, 3)
@@ -520,6 +518,7 @@ struct Claim {
   SlotDesc sd;
   PassDesc pd;              // the task's pass
   unsigned long long task;  // task index within the pass
+  uint64_t ulo, uhi;        // its unit range (g >= 2; g == 1: task, task + 1), computed once for the CTA
   int slot, pass, U, skip;
   unsigned int ndone;       // tasks of the pass this claim completes (skipped runs: more than one)
   unsigned int pad;
@@ -576,14 +575,20 @@ __device__ __forceinline__ void mark_exhausted(const CtlStatic &cs, int s, unsig
 // cc.P) of slot s.  A task the skip rule drops needs no work; every later
 // task of the pass is then droppable too, so the rest of the pass is taken
 // in the same claim by compare-and-swap on the code's own generation.
-__device__ __forceinline__ void take(SlotState *st, const KParams &kp, int s, unsigned long long w, uint64_t key,
-                                    Claim *o, ClaimCache &cc) {
+__device__ __forceinline__ void take(SlotState *st, const KParams &kp, bool serve, int s, unsigned long long w,
+                                    uint64_t key, Claim *o, ClaimCache &cc) {
   const unsigned long long t = w & kTaskMask;
   const int U = key == kNoKey ? cc.sd.n - cc.sd.k + 2 : (int)key_weight(key);
   const int mid = kp.mid_pass < 0 ? cc.sd.mid_pass_exit : kp.mid_pass;
   o->sd = cc.sd;
   o->pd = cc.pd;
   o->task = t - cc.pd.task_base;
+  if (cc.pd.g > 1) {
+    task_range(cc.pd, o->task, &o->ulo, &o->uhi);
+  } else {
+    o->ulo = o->task;
+    o->uhi = o->task + 1;
+  }
   o->slot = s;
   o->pass = cc.P;
   o->U = U;
@@ -591,7 +596,16 @@ __device__ __forceinline__ void take(SlotState *st, const KParams &kp, int s, un
   // this pass or an earlier one (passes run ahead of the termination test).
   o->skip = (mid && key != kNoKey && (int)key_pass(key) <= cc.P && U <= cc.pd.L_before) ? 1 : 0;
   o->ndone = 1;
-  if (o->skip) {
+  if (o->skip && !serve && !cc.sd.per_round_check && (int)key_pass(key) < cc.P) {
+    // With a test after every pass, a best codeword from a pass before P
+    // with U <= L_before(P) = L_after(P - 1) means the test after pass P - 1
+    // certifies the code, so no pass from P on is ever tested: the rest of
+    // the sequence is dropped, uncounted, by setting a bit above every task
+    // index (32-bit; the counter's field has 40 bits).  A one-shot launch
+    // never reuses the slot, so the bit cannot reach another code's counter.
+    atomicOr(&st->word, 1ull << 32);
+    o->ndone = 0;
+  } else if (o->skip) {
     const unsigned long long end = (unsigned long long)cc.pd.task_base + cc.pd.ntasks;
     unsigned long long cur = w + 1;
     for (int tries = 0; tries < 4; ++tries) {
@@ -637,7 +651,7 @@ __device__ __forceinline__ int claim(const SlotDesc *slots, SlotState *states, c
     }
     if ((w >> kGenShift) == cc.gen && cc.sd.npasses > 0 && !fin) {
       if (locate(cc, w & kTaskMask)) {
-        take(st, kp, s, w, key, o, cc);
+        take(st, kp, cs.serve != 0, s, w, key, o, cc);
         rr = s;
         wait_t0 = 0;
         cc.sleep_ns = 128;
@@ -692,7 +706,7 @@ __device__ __forceinline__ int claim(const SlotDesc *slots, SlotState *states, c
         mark_exhausted(cs, s, cc.gen);
         continue;
       }
-      take(st, kp, s, w, best_key(st), o, cc);
+      take(st, kp, cs.serve != 0, s, w, best_key(st), o, cc);
       rr = s;
       wait_t0 = 0;
       cc.sleep_ns = 128;
@@ -790,10 +804,12 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
   uint64_t *bcols = reinterpret_cast<uint64_t *>(smem_raw);  // binomial columns t < kBinomCols
   uint4 *tab4 = smem_raw + kBinomBytes / 16;
   uint32_t *tab = reinterpret_cast<uint32_t *>(tab4);
-  __shared__ Claim s_cl;
+  // Two claim buffers: thread 0 claims task i + 1 into one while thread 32
+  // counts task i off from the other (the two atomics round trips overlap).
+  __shared__ Claim s_claims[2];
   __shared__ ClaimCache s_cc;
   __shared__ int s_cmd, s_stage;
-  __shared__ unsigned long long s_count, s_staged_seq;
+  __shared__ unsigned long long s_counts[2], s_staged_seq;
   __shared__ int s_staged_slot, s_staged_j;
 
   const CtlStatic cs = *ctl;
@@ -821,7 +837,10 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
     if (sd0.pass_times) sd0.pass_times[kMaxPasses] = t_start;  // launch start
   }
   __syncthreads();
+  int cur = 0;           // claim buffer of the task about to be claimed
+  bool pending = false;  // the other buffer holds a task run but not yet counted off
   for (;;) {
+    Claim &s_cl = s_claims[cur];
     if (tid == 0) {
       const int cmd = claim(slots, states, cs, kp, cdyn, rr, wait_t0, t_start, &s_cl, s_cc);
       s_cmd = cmd;
@@ -834,9 +853,19 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
           s_staged_seq = s_cl.sd.seq;
         }
       }
-      s_count = 0;
+      s_counts[cur] = 0;
+    } else if (tid == 32 && pending) {
+      const Claim &pc = s_claims[cur ^ 1];
+      const unsigned long long pcount = s_counts[cur ^ 1];
+      SlotAux *pax = cs.aux + pc.slot;
+      if (pcount) {
+        atomicAdd(&states[pc.slot].enumerated, pcount);
+        atomicAdd(&pax->pass_count[pc.pass], pcount);
+      }
+      finish_task(cs, pc.sd, &states[pc.slot], pax, pc.slot, pc.pass, pc.pd, pc.ndone);
     }
     __syncthreads();
+    pending = false;
     const int cmd = s_cmd;
     if (cmd == kCmdExit) break;
     if (cmd == kCmdWait) {
@@ -852,18 +881,13 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
     }
     unsigned long long count = 0;
     SlotAux *ax = cs.aux + slot;
-    if (!s_cl.skip) V::run(s_cl.sd, s_cl.pd, s_cl.pass, tab, binom, s_cl.task, s_cl.U, &states[slot], ax, count);
+    if (!s_cl.skip) V::run(s_cl.sd, s_cl.pd, s_cl.pass, tab, binom, s_cl.ulo, s_cl.uhi, s_cl.U, &states[slot], ax, count);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) count += __shfl_xor_sync(0xffffffffu, count, o);
-    if ((tid & 31) == 0 && count) atomicAdd(&s_count, count);
+    if ((tid & 31) == 0 && count) atomicAdd(&s_counts[cur], count);
     __syncthreads();
-    if (tid == 0) {
-      if (s_count) {
-        atomicAdd(&states[slot].enumerated, s_count);
-        atomicAdd(&ax->pass_count[s_cl.pass], s_count);
-      }
-      finish_task(cs, s_cl.sd, &states[slot], ax, slot, s_cl.pass, s_cl.pd, s_cl.ndone);
-    }
+    pending = true;
+    cur ^= 1;
   }
 }
 

@@ -120,7 +120,7 @@ extern "C" int fpcode_min_distance_noalloc(int p, int n, int k, const uint8_t *G
   NA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   if (per_sm < 1) return FPCODE_EINVAL;
   const int ctas = sms * per_sm;
-  fph::plan_tasks(&P, ctas, 0, fph::kMinStepsSingle);
+  fph::plan_tasks(&P, ctas, 0, fph::kMinStepsSingle, true);
 
   // host image of the static part (starting at off_ctl)
   std::vector<unsigned char> img(off_state - off_ctl, 0);

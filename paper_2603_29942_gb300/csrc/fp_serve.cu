@@ -278,7 +278,7 @@ int fpcode_serve_submit(fpcode_server *s, const fpcode_desc *code, uint64_t *tic
     fph::set_error("serve: no device memory free for the tables");
     return FPCODE_EBUSY;
   }
-  fph::plan_tasks(P.get(), s->ctas, o.prefixes_per_lane, fph::kMinStepsServe);
+  fph::plan_tasks(P.get(), s->ctas, o.prefixes_per_lane, fph::kMinStepsServe, true);
   const uint64_t tk = s->next_ticket++;
   char *stg = s->staging + (size_t)slot * s->stage_per_slot;
   const size_t o_pass = a256(sizeof(fpk::SlotDesc));

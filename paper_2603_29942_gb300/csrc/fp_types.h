@@ -1,5 +1,6 @@
 // fp_types.h -- data shared by the host driver and the enumeration kernels.
 #pragma once
+#include <stddef.h>
 #include <stdint.h>
 
 #if defined(__CUDACC__)
@@ -102,19 +103,28 @@ struct SlotDesc {
 };
 static_assert(sizeof(SlotDesc) == 80, "SlotDesc layout");
 
-// Dynamic state of one code, device memory (all zero = fresh).
-struct SlotState {
+// Dynamic state of one code, device memory (all zero = fresh).  Three
+// 128-byte lines keep apart what is written at different rates: the task
+// counter (an atomic per claim), the best key and finished flag (written
+// rarely, read by every claim and every warp's threshold refresh), and the
+// accounting written once per task or at the end.  On one line, the reads
+// queued behind the claims' atomics at the L2.
+struct alignas(128) SlotState {
   unsigned long long word;        // (generation << 48) | next task of the whole schedule
+  unsigned long long pad_w[15];
   unsigned long long best_key;    // inverted packed witness key (0: none yet)
+  int32_t finished;               // 1: nothing left to do
+  int32_t pad_k[29];
   unsigned long long enumerated;  // codewords evaluated, passes past the stop included
   unsigned long long entered;     // codewords evaluated in the passes up to stop_pass
   int32_t frontier;               // next pass whose termination test is pending
   int32_t pad0;
   int32_t status;                 // 0 while running, then kDoneFlag | fpcode status
   int32_t stop_pass;              // last pass entered
-  int32_t finished;               // 1: nothing left to do
-  int32_t pad;
+  int32_t pad_a[24];
 };
+static_assert(sizeof(SlotState) == 384 && offsetof(SlotState, best_key) == 128 && offsetof(SlotState, enumerated) == 256,
+              "SlotState lines");
 
 // Per-pass bookkeeping of one code (zeroed with the state): the least
 // weight recorded in each pass (stored as 256 - w, 0: none), the running

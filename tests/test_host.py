@@ -226,6 +226,23 @@ def test_revolving_door(lib):
                     assert nxt is None
 
 
+def test_revolving_door_large_n(lib):
+    """Unranking at the kernel's sizes (n up to 64, t up to 23) inverts the
+    ranking, which walks the definition's recursion from the top."""
+    rng = np.random.default_rng(11)
+    for n in (20, 33, 40, 63, 64):
+        for t in (1, 2, 5, 12, 23):
+            if t > n:
+                continue
+            total = math.comb(n, t)
+            ranks = {0, total - 1, total // 2} | {int(x) for x in rng.integers(0, total, size=40, dtype=np.uint64)
+                                                 if int(x) < total}
+            for r in sorted(ranks):
+                T = B.fpcode_test_rd_unrank(r, n, t)
+                assert bin(T).count("1") == t and T < (1 << n)
+                assert B.fpcode_test_rd_rank(T, n, t) == r
+
+
 def _codeword_coeffs(k, g, p, I, x, c):
     m, Q, coefs = B.fpcode_test_prefix_unrank(I, k, g, p)
     v = [0] * k
@@ -354,7 +371,10 @@ def test_task_ranges_tile_each_pass(ctas, fixed_pl, min_steps, lib):
         ranges = B.fpcode_test_task_ranges(pr, i, ctas, fixed_pl, min_steps)
         if not fixed_pl and g > 1 and nprefix < 256 * ctas * min_steps:
             assert len(ranges) <= ctas
-            assert all(hi - lo >= 256 * min_steps for lo, hi in ranges[:-1])
+            if min_steps <= 8 and nprefix <= 256 * ctas:  # single code: a tiny pass is spread wide
+                assert all(hi - lo <= 256 * 256 for lo, hi in ranges)
+            else:
+                assert all(hi - lo >= 256 * min_steps for lo, hi in ranges[:-1])
         if g == 1:
             assert ranges == [(0, nprefix)]
             continue
