@@ -272,7 +272,8 @@ int enqueue_one(fpcode_prepared *prep, cudaStream_t st, const fpcode_opts &o) {
   fph::Prepared &P = prep->host;
   Layout L = make_layout({&P});
   FP_CUDA(cudaMemsetAsync(prep->dev + L.off_states, 0, L.dyn_bytes + L.aux_bytes, st));
-  if (prep->resume_from > 0) {  // continue after a checkpoint: next task, frontier, bound
+  const bool resumed = prep->resume_from > 0;
+  if (resumed) {  // continue after a checkpoint: next task, frontier, bound
     const fpk::PassDesc &d = P.passes[prep->resume_from];
     static thread_local unsigned long long word, key;
     static thread_local int32_t frontier, useq;
@@ -291,7 +292,12 @@ int enqueue_one(fpcode_prepared *prep, cudaStream_t st, const fpcode_opts &o) {
   }
   if (prep->init_u > 0) {  // the bound as a key past every real one (pass 255), stored inverted
     static thread_local unsigned long long seed;
-    seed = ~fpk::make_key((uint32_t)prep->init_u, 255u, (1ull << 34) - 1, 63u, 255u);
+    seed = ~fpk::bound_key((uint32_t)prep->init_u);
+    FP_CUDA(cudaMemcpyAsync(prep->dev + L.off_states + offsetof(SlotState, best_key), &seed, sizeof(seed),
+                            cudaMemcpyHostToDevice, st));
+  } else if (!resumed && P.seed_u > 0) {  // the g = 1 passes' least weight as a bound, stored inverted
+    static thread_local unsigned long long seed;
+    seed = ~fpk::bound_key((uint32_t)P.seed_u);
     FP_CUDA(cudaMemcpyAsync(prep->dev + L.off_states + offsetof(SlotState, best_key), &seed, sizeof(seed),
                             cudaMemcpyHostToDevice, st));
   }
@@ -395,6 +401,7 @@ int fpcode_prepared_single_pass(const fpcode_prepared *src, int pass, int u_init
   d.task_base = 0;
   prep->host.passes.assign(1, d);
   prep->host.complete = 0;
+  prep->host.seed_u = 0;  // the probe's bound is u_init
   prep->init_u = u_init;
   *out = prep;
   return FPCODE_OK;
@@ -615,11 +622,20 @@ int fpcode_min_distance_batch(int num, const fpcode_desc *codes, void *stream, c
     for (int i : idx)
       fph::plan_tasks(preps[i].get(), ctas, o.prefixes_per_lane, many ? fph::kMinStepsBatch : fph::kMinStepsSingle, !many);
     Layout L = make_layout(codesv);
-    s = ws_reserve(*c, L.total, std::max(L.static_bytes, L.dyn_bytes));
+    // pinned staging: the static image, then the codes' first states (each
+    // zero but its best key, the g = 1 passes' least key); later the read-back
+    const size_t st_off = (L.static_bytes + 255) & ~(size_t)255;
+    const size_t st_bytes = codesv.size() * sizeof(SlotState);
+    s = ws_reserve(*c, L.total, std::max(st_off + st_bytes, L.dyn_bytes));
     if (s) break;
     fill_static(L, codesv, *c, c->ws_pinned, c->ws, 0);
+    SlotState *first = reinterpret_cast<SlotState *>(c->ws_pinned + st_off);
+    std::memset(first, 0, st_bytes);
+    for (size_t q = 0; q < codesv.size(); ++q)
+      first[q].best_key = codesv[q]->seed_u > 0 ? ~fpk::bound_key((uint32_t)codesv[q]->seed_u) : 0ull;
     FP_CUDA(cudaMemcpyAsync(c->ws, c->ws_pinned, L.static_bytes, cudaMemcpyHostToDevice, st));
     FP_CUDA(cudaMemsetAsync(c->ws + L.off_states, 0, L.dyn_bytes + L.aux_bytes, st));
+    FP_CUDA(cudaMemcpyAsync(c->ws + L.off_states, first, st_bytes, cudaMemcpyHostToDevice, st));
     FP_CUDA(cudaEventRecord(e0, st));
     s = launch(fn, ctas, smem, st, c->ws, L, kparams(o, 0));
     if (s) break;
@@ -741,7 +757,7 @@ int fpcode_test_pass_times(fpcode_prepared *prep, void *stream, double *us, int 
 int fpcode_prepared_bytes(const fpcode_prepared *prep, uint64_t *h2d, uint64_t *d2h) {
   if (!prep) return FPCODE_EINVAL;
   Layout L = make_layout({&prep->host});
-  if (h2d) *h2d = L.static_bytes;
+  if (h2d) *h2d = L.static_bytes + (prep->host.seed_u > 0 ? 8 : 0);  // tables and descriptors, the first bound
   if (d2h) *d2h = L.dyn_bytes;
   return FPCODE_OK;
 }

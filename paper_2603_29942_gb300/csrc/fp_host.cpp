@@ -323,6 +323,24 @@ int prepare(int p, int n, int k, const uint8_t *G, const fpcode_opts &opts, Prep
     if (P->passes.size() > round_start && !truncated) P->passes.back().round_end = 1;
   }
   P->complete = truncated ? 0 : 1;
+  // The g = 1 passes are the rows of the Gamma_j themselves: their least
+  // weight is known now.  A search starts with it as its bound (a bound key,
+  // no codeword behind it), so the tasks that start at once (every early
+  // pass) filter their leaves against it instead of against n - k + 2.  The
+  // outcome is unchanged: the g = 1 passes still run, record that weight
+  // with its key, and the termination tests see only recorded weights.
+  P->seed_u = 0;
+  for (size_t q = 0; q < P->passes.size(); ++q) {
+    if (P->passes[q].g != 1) continue;
+    const int j = P->passes[q].j;
+    for (int x = 0; x < k; ++x) {
+      const uint8_t *row = &P->gam[((size_t)j * k + x) * n];
+      const int *red = &P->red[(size_t)j * nk];
+      int w = 1;
+      for (int c = 0; c < nk; ++c) w += row[red[c]] != 0;
+      if (P->seed_u == 0 || w < P->seed_u) P->seed_u = w;
+    }
+  }
   P->t_prepare_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return FPCODE_OK;
 }

@@ -35,6 +35,8 @@ struct Prepared {
   std::vector<fpk::PassDesc> passes;
   int complete = 0;              // schedule reaches the last level
   uint64_t code_hash = 0;        // FNV-1a of (p, n, k, per_round_check, defer) and G: the schedule's identity
+  int seed_u = 0;                // least weight of the g = 1 passes (rows of the Gamma_j), 0: none;
+                                 // a search starts with it as its bound
   int L0 = 0;                    // lower bound before any pass
   double t_prepare_ms = 0;
   size_t table_words_per_set() const { return (size_t)k * ((size_t)(p - 1) * rwpad + fpk::sig_words(p, r, W)); }
