@@ -292,12 +292,12 @@ int enqueue_one(fpcode_prepared *prep, cudaStream_t st, const fpcode_opts &o) {
   }
   if (prep->init_u > 0) {  // the bound as a key past every real one (pass 255), stored inverted
     static thread_local unsigned long long seed;
-    seed = ~fpk::bound_key((uint32_t)prep->init_u);
+    seed = ~fph::bound_key((uint32_t)prep->init_u);
     FP_CUDA(cudaMemcpyAsync(prep->dev + L.off_states + offsetof(SlotState, best_key), &seed, sizeof(seed),
                             cudaMemcpyHostToDevice, st));
   } else if (!resumed && P.seed_u > 0) {  // the g = 1 passes' least weight as a bound, stored inverted
     static thread_local unsigned long long seed;
-    seed = ~fpk::bound_key((uint32_t)P.seed_u);
+    seed = ~fph::bound_key((uint32_t)P.seed_u);
     FP_CUDA(cudaMemcpyAsync(prep->dev + L.off_states + offsetof(SlotState, best_key), &seed, sizeof(seed),
                             cudaMemcpyHostToDevice, st));
   }
@@ -632,7 +632,7 @@ int fpcode_min_distance_batch(int num, const fpcode_desc *codes, void *stream, c
     SlotState *first = reinterpret_cast<SlotState *>(c->ws_pinned + st_off);
     std::memset(first, 0, st_bytes);
     for (size_t q = 0; q < codesv.size(); ++q)
-      first[q].best_key = codesv[q]->seed_u > 0 ? ~fpk::bound_key((uint32_t)codesv[q]->seed_u) : 0ull;
+      first[q].best_key = codesv[q]->seed_u > 0 ? ~fph::bound_key((uint32_t)codesv[q]->seed_u) : 0ull;
     FP_CUDA(cudaMemcpyAsync(c->ws, c->ws_pinned, L.static_bytes, cudaMemcpyHostToDevice, st));
     FP_CUDA(cudaMemsetAsync(c->ws + L.off_states, 0, L.dyn_bytes + L.aux_bytes, st));
     FP_CUDA(cudaMemcpyAsync(c->ws + L.off_states, first, st_bytes, cudaMemcpyHostToDevice, st));

@@ -20,6 +20,12 @@ const fpenum::Binom &binom();  // host binomial table
 
 bool is_odd_prime(int p);
 
+// A bound u with no codeword behind it: the largest key of weight u, its
+// pass field past every pass.  Any record of weight <= u replaces it, and
+// the skip rule (which needs a key from a pass already entered) never fires
+// on it.
+inline uint64_t bound_key(uint32_t u) { return ((uint64_t)u << fpk::kKeyW) | ((1ull << fpk::kKeyW) - 1); }
+
 // Digit width of the packed coefficient counter for prime p (the kernels
 // use the same: 1 bit for p = 3, 4 for p = 5, 7, 8 otherwise).
 int digit_bits_of(int p);

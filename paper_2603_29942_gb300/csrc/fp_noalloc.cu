@@ -153,7 +153,7 @@ extern "C" int fpcode_min_distance_noalloc(int p, int n, int k, const uint8_t *G
   NA_CUDA(cudaMemcpyAsync(base + off_ctl, img.data(), img.size(), cudaMemcpyHostToDevice, st));
   NA_CUDA(cudaMemsetAsync(base + off_state, 0, dyn_bytes + aux_bytes, st));  // state starts at zero
   static thread_local unsigned long long seed;  // but for the g = 1 passes' least key, stored inverted
-  seed = P.seed_u > 0 ? ~fpk::bound_key((uint32_t)P.seed_u) : 0ull;
+  seed = P.seed_u > 0 ? ~fph::bound_key((uint32_t)P.seed_u) : 0ull;
   NA_CUDA(cudaMemcpyAsync(base + off_state + offsetof(fpk::SlotState, best_key), &seed, sizeof(seed),
                           cudaMemcpyHostToDevice, st));
   if (!P.passes.empty()) {

@@ -30,11 +30,6 @@ FPK_HD uint64_t make_key(uint32_t weight, uint32_t pass, uint64_t I, uint32_t x,
          (uint64_t)c;
 }
 FPK_HD uint32_t key_weight(uint64_t key) { return (uint32_t)(key >> kKeyW); }
-// A bound u with no codeword behind it: the largest key of weight u, its
-// pass field past every pass.  Any record of weight <= u replaces it, and
-// the skip rule (which needs a key from a pass already entered) never fires
-// on it.
-FPK_HD uint64_t bound_key(uint32_t u) { return ((uint64_t)u << kKeyW) | ((1ull << kKeyW) - 1); }
 FPK_HD uint32_t key_pass(uint64_t key) { return (uint32_t)(key >> kKeyP) & 0xFFu; }
 FPK_HD uint64_t key_prefix(uint64_t key) { return (key >> kKeyI) & ((1ull << 34) - 1); }
 FPK_HD uint32_t key_leaf(uint64_t key) { return (uint32_t)(key >> kKeyX) & 63u; }
