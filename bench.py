@@ -66,8 +66,8 @@ POPC_PER_CLK_SM = 16.0   # measured by fpcode_int_peaks on GB300 (and CUDA's doc
 # version that was profiled; any later change reports null.
 KERNEL_SOURCES = ["fp_kernel.cuh", "fp_enum.cuh", "fp_bitslice.cuh", "fp_types.h"]
 PROFILED_TRAFFIC = {
-    "f3_n80_k40": {"sources_sha256": "6be4ee33216410f8b0f595895950d0e8ea0dc2f590d32fbf9fd5d5c3299389e8",
-                   "bytes": 91136},
+    "f3_n80_k40": {"sources_sha256": "51126b809f0dcbaf48dee8d07cd7ad1d060e4701469834dde43f8375baf104aa",
+                   "bytes": 1334528},
 }
 
 

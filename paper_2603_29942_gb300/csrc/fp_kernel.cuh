@@ -804,12 +804,10 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
   uint64_t *bcols = reinterpret_cast<uint64_t *>(smem_raw);  // binomial columns t < kBinomCols
   uint4 *tab4 = smem_raw + kBinomBytes / 16;
   uint32_t *tab = reinterpret_cast<uint32_t *>(tab4);
-  // Two claim buffers: thread 0 claims task i + 1 into one while thread 32
-  // counts task i off from the other (the two atomics round trips overlap).
-  __shared__ Claim s_claims[2];
+  __shared__ Claim s_cl;
   __shared__ ClaimCache s_cc;
   __shared__ int s_cmd, s_stage;
-  __shared__ unsigned long long s_counts[2], s_staged_seq;
+  __shared__ unsigned long long s_count, s_staged_seq;
   __shared__ int s_staged_slot, s_staged_j;
 
   const CtlStatic cs = *ctl;
@@ -837,10 +835,7 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
     if (sd0.pass_times) sd0.pass_times[kMaxPasses] = t_start;  // launch start
   }
   __syncthreads();
-  int cur = 0;           // claim buffer of the task about to be claimed
-  bool pending = false;  // the other buffer holds a task run but not yet counted off
   for (;;) {
-    Claim &s_cl = s_claims[cur];
     if (tid == 0) {
       const int cmd = claim(slots, states, cs, kp, cdyn, rr, wait_t0, t_start, &s_cl, s_cc);
       s_cmd = cmd;
@@ -853,19 +848,9 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
           s_staged_seq = s_cl.sd.seq;
         }
       }
-      s_counts[cur] = 0;
-    } else if (tid == 32 && pending) {
-      const Claim &pc = s_claims[cur ^ 1];
-      const unsigned long long pcount = s_counts[cur ^ 1];
-      SlotAux *pax = cs.aux + pc.slot;
-      if (pcount) {
-        atomicAdd(&states[pc.slot].enumerated, pcount);
-        atomicAdd(&pax->pass_count[pc.pass], pcount);
-      }
-      finish_task(cs, pc.sd, &states[pc.slot], pax, pc.slot, pc.pass, pc.pd, pc.ndone);
+      s_count = 0;
     }
     __syncthreads();
-    pending = false;
     const int cmd = s_cmd;
     if (cmd == kCmdExit) break;
     if (cmd == kCmdWait) {
@@ -884,10 +869,15 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
     if (!s_cl.skip) V::run(s_cl.sd, s_cl.pd, s_cl.pass, tab, binom, s_cl.ulo, s_cl.uhi, s_cl.U, &states[slot], ax, count);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) count += __shfl_xor_sync(0xffffffffu, count, o);
-    if ((tid & 31) == 0 && count) atomicAdd(&s_counts[cur], count);
+    if ((tid & 31) == 0 && count) atomicAdd(&s_count, count);
     __syncthreads();
-    pending = true;
-    cur ^= 1;
+    if (tid == 0) {
+      if (s_count) {
+        atomicAdd(&states[slot].enumerated, s_count);
+        atomicAdd(&ax->pass_count[s_cl.pass], s_count);
+      }
+      finish_task(cs, s_cl.sd, &states[slot], ax, slot, s_cl.pass, s_cl.pd, s_cl.ndone);
+    }
   }
 }
 
