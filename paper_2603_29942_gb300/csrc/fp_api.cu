@@ -273,33 +273,35 @@ int enqueue_one(fpcode_prepared *prep, cudaStream_t st, const fpcode_opts &o) {
   Layout L = make_layout({&P});
   FP_CUDA(cudaMemsetAsync(prep->dev + L.off_states, 0, L.dyn_bytes + L.aux_bytes, st));
   const bool resumed = prep->resume_from > 0;
+  // the first state's values, staged in pinned memory (a copy from pageable
+  // memory would wait for the stream)
+  struct Stage {
+    unsigned long long word, key, bound;
+    int32_t frontier, useq;
+  };
+  Stage *sg = reinterpret_cast<Stage *>(prep->pinned + prep->stage_off);
+  static_assert(sizeof(Stage) <= 64, "staging block");
+  char *stp = prep->dev + L.off_states;
   if (resumed) {  // continue after a checkpoint: next task, frontier, bound
     const fpk::PassDesc &d = P.passes[prep->resume_from];
-    static thread_local unsigned long long word, key;
-    static thread_local int32_t frontier, useq;
-    word = (unsigned long long)d.task_base;
-    key = prep->resume_key == fpk::kNoKey ? 0ull : ~prep->resume_key;
-    frontier = prep->resume_from;
-    useq = prep->resume_key == fpk::kNoKey ? 0 : (int32_t)fpk::key_weight(prep->resume_key);
-    char *stp = prep->dev + L.off_states;
-    FP_CUDA(cudaMemcpyAsync(stp + offsetof(SlotState, word), &word, 8, cudaMemcpyHostToDevice, st));
-    FP_CUDA(cudaMemcpyAsync(stp + offsetof(SlotState, best_key), &key, 8, cudaMemcpyHostToDevice, st));
-    FP_CUDA(cudaMemcpyAsync(stp + offsetof(SlotState, frontier), &frontier, 4, cudaMemcpyHostToDevice, st));
+    sg->word = (unsigned long long)d.task_base;
+    sg->key = prep->resume_key == fpk::kNoKey ? 0ull : ~prep->resume_key;
+    sg->frontier = prep->resume_from;
+    sg->useq = prep->resume_key == fpk::kNoKey ? 0 : (int32_t)fpk::key_weight(prep->resume_key);
+    FP_CUDA(cudaMemcpyAsync(stp + offsetof(SlotState, word), &sg->word, 8, cudaMemcpyHostToDevice, st));
+    FP_CUDA(cudaMemcpyAsync(stp + offsetof(SlotState, best_key), &sg->key, 8, cudaMemcpyHostToDevice, st));
+    FP_CUDA(cudaMemcpyAsync(stp + offsetof(SlotState, frontier), &sg->frontier, 4, cudaMemcpyHostToDevice, st));
     FP_CUDA(cudaMemcpyAsync(prep->dev + L.off_aux + offsetof(fpk::SlotAux, useq_after) +
                                 (size_t)(prep->resume_from - 1) * sizeof(int32_t),
-                            &useq, 4, cudaMemcpyHostToDevice, st));
+                            &sg->useq, 4, cudaMemcpyHostToDevice, st));
     prep->resume_from = 0;  // one search
   }
-  if (prep->init_u > 0) {  // the bound as a key past every real one (pass 255), stored inverted
-    static thread_local unsigned long long seed;
-    seed = ~fph::bound_key((uint32_t)prep->init_u);
-    FP_CUDA(cudaMemcpyAsync(prep->dev + L.off_states + offsetof(SlotState, best_key), &seed, sizeof(seed),
-                            cudaMemcpyHostToDevice, st));
-  } else if (!resumed && P.seed_u > 0) {  // the g = 1 passes' least weight as a bound, stored inverted
-    static thread_local unsigned long long seed;
-    seed = ~fph::bound_key((uint32_t)P.seed_u);
-    FP_CUDA(cudaMemcpyAsync(prep->dev + L.off_states + offsetof(SlotState, best_key), &seed, sizeof(seed),
-                            cudaMemcpyHostToDevice, st));
+  // the bound as a key past every real one (pass 255), stored inverted: the
+  // probe's u_init, else the g = 1 passes' least weight
+  const int bound = prep->init_u > 0 ? prep->init_u : resumed ? 0 : P.seed_u;
+  if (bound > 0) {
+    sg->bound = ~fph::bound_key((uint32_t)bound);
+    FP_CUDA(cudaMemcpyAsync(stp + offsetof(SlotState, best_key), &sg->bound, 8, cudaMemcpyHostToDevice, st));
   }
   if (!P.passes.empty()) {
     FP_CUDA(cudaEventRecord((cudaEvent_t)prep->ev0, st));
@@ -430,7 +432,8 @@ int fpcode_prepared_upload(fpcode_prepared *prep, void *stream) {
   FP_CUDA(cudaGetDevice(&prep->device));
   Layout L = make_layout({&prep->host});
   FP_CUDA(cudaMalloc(&prep->dev, L.total));
-  FP_CUDA(cudaMallocHost(&prep->pinned, std::max(L.static_bytes, L.dyn_bytes)));
+  prep->stage_off = align256(std::max(L.static_bytes, L.dyn_bytes));
+  FP_CUDA(cudaMallocHost(&prep->pinned, prep->stage_off + 64));
   s = upload_one(prep, st, *c, prep->dev, prep->pinned);
   if (s) return s;
   FP_CUDA(cudaStreamSynchronize(st));
@@ -520,25 +523,32 @@ int fpcode_min_distance(int p, int n, int k, const uint8_t *G, void *stream, int
   if (s) return s;
   std::lock_guard<std::mutex> lk(c->ws_mu);
   Layout L = make_layout({&prep.host});
-  s = ws_reserve(*c, L.total, std::max(L.static_bytes, L.dyn_bytes));
+  // pinned: [static image][read-back][staging], so nothing waits between the
+  // upload and the launch
+  const size_t rb_off = align256(L.static_bytes), stage_off = rb_off + align256(L.dyn_bytes);
+  s = ws_reserve(*c, L.total, stage_off + 64);
   if (s) return s;
-  s = ensure_events(&prep);
-  if (s) return s;
+  if (!c->ev0) {  // events of the workspace searches, made once per device
+    cudaEvent_t a, b;
+    FP_CUDA(cudaEventCreate(&a));
+    FP_CUDA(cudaEventCreate(&b));
+    c->ev0 = a;
+    c->ev1 = b;
+  }
+  prep.ev0 = c->ev0;
+  prep.ev1 = c->ev1;
   prep.external = true;
   prep.dev = c->ws;
-  prep.pinned = c->ws_pinned;
-  s = upload_one(&prep, st, *c, prep.dev, prep.pinned);
+  s = upload_one(&prep, st, *c, prep.dev, c->ws_pinned);
   if (s) return s;
-  // the pinned staging buffer is reused for the read-back: wait for the upload copy
-  FP_CUDA(cudaStreamSynchronize(st));
+  prep.pinned = c->ws_pinned + rb_off;
+  prep.stage_off = stage_off - rb_off;
   prep.uploaded = true;
   s = enqueue_one(&prep, st, o);
   if (s) return s;
   fpcode_result res;
   s = finish_one(&prep, st, &res, witness);
-  if (prep.ev0) cudaEventDestroy((cudaEvent_t)prep.ev0);
-  if (prep.ev1) cudaEventDestroy((cudaEvent_t)prep.ev1);
-  prep.ev0 = prep.ev1 = nullptr;
+  prep.ev0 = prep.ev1 = nullptr;  // the context's
   (void)t0;
   if (s) return s;
   *d = res.d;

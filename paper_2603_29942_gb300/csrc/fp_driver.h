@@ -21,6 +21,7 @@ struct DevCtx {
   size_t ws_bytes = 0;
   char *ws_pinned = nullptr;
   size_t ws_pinned_bytes = 0;
+  void *ev0 = nullptr, *ev1 = nullptr;  // cudaEvent_t around the kernel of a workspace search
 };
 
 // Context of the current device (created on first use).

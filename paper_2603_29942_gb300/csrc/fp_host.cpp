@@ -77,6 +77,10 @@ struct Eliminator {
   void new_round() { owner.assign(k, -1); }
   // Take column c as a pivot if a free row has a nonzero entry there.
   bool take(int c) {
+    // locals: the byte stores below may alias any member as far as the
+    // compiler knows, which would keep it from counting (and vectorising)
+    // the loops
+    const int n = this->n, k = this->k, p = this->p;
     int r = -1;
     for (int q = 0; q < k; ++q)
       if (owner[q] < 0 && M[(size_t)q * n + c] != 0) {
@@ -89,6 +93,7 @@ struct Eliminator {
     for (int i = 0; i < n; ++i) row[i] = ms[row[i]];
     // multiples (p - f) * row, formed once per pivot, for the f that occur
     const uint16_t pp = (uint16_t)p;
+    const uint8_t p8 = (uint8_t)p;
     for (int q = 0; q < k; ++q) {
       if (q == r) continue;
       uint8_t *o = &M[(size_t)q * n];
@@ -100,9 +105,21 @@ struct Eliminator {
         for (int i = 0; i < n; ++i) mv[i] = mf[row[i]];
         have[f - 1] = 1;
       }
-      for (int i = 0; i < n; ++i) {
-        const uint16_t x = (uint16_t)(o[i] + mv[i]);
-        o[i] = (uint8_t)(x >= pp ? x - pp : x);
+      if (p < 128) {
+        // byte lanes: s = o + mv < 2p <= 255; s - p wraps above s exactly
+        // when s < p, so the smaller of the two is s mod p (vectorises)
+        uint8_t *__restrict__ od = o;
+        const uint8_t *__restrict__ md = mv;
+        for (int i = 0; i < n; ++i) {
+          const uint8_t x = (uint8_t)(od[i] + md[i]);
+          const uint8_t y = (uint8_t)(x - p8);
+          od[i] = x < y ? x : y;
+        }
+      } else {
+        for (int i = 0; i < n; ++i) {
+          const uint16_t x = (uint16_t)(o[i] + mv[i]);
+          o[i] = (uint8_t)(x >= pp ? x - pp : x);
+        }
       }
     }
     std::fill(have.begin(), have.end(), (char)0);

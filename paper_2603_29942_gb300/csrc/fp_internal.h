@@ -97,6 +97,7 @@ struct fpcode_prepared {
   size_t dev_bytes = 0;
   size_t off_ctl = 0, off_slot = 0, off_pass = 0, off_table = 0, off_state = 0, dyn_bytes = 0;
   char *pinned = nullptr; // read-back of the dynamic part
+  size_t stage_off = 0;   // pinned + stage_off: 64 bytes staging the first state's values (bound, resume)
   void *ev0 = nullptr, *ev1 = nullptr;  // cudaEvent_t around the kernel
   fpcode_opts run_opts{};
 };
