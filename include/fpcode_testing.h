@@ -57,6 +57,12 @@ int fpcode_prepared_shape(const fpcode_prepared *prep, int *m, int *kj, int *npa
 /* Gamma_j (k x n) and its pivot columns (k). */
 int fpcode_prepared_gamma(const fpcode_prepared *prep, int j, uint8_t *gamma, int *pivots);
 int fpcode_prepared_passes(const fpcode_prepared *prep, fpcode_pass_info *passes, int max);
+/* Stored bit-sliced multiple v * A_j[t] of the non-pivot part of row t of
+ * Gamma_j (v in 1..p-1): r * W words into `slices`, word w and slice i at
+ * [w * r + i]; and, when `sig` is given and p is 3 or 7, the row's pair
+ * signature words.  Returns the number of signature words (0: none), or a
+ * negative status. */
+int fpcode_test_prepared_row(const fpcode_prepared *prep, int j, int t, int v, uint32_t *slices, uint32_t *sig);
 /* The CTA task ranges [lo, hi), in prefixes, of pass `pass` when planned
  * for `ctas` CTAs (fixed_pl > 0: fixed tasks of 256 * fixed_pl prefixes; 0:
  * guided, with fixed tasks of at least min_steps prefixes per lane for a pass

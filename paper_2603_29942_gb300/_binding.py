@@ -158,6 +158,8 @@ def _declare(lib):
         "fpcode_prepared_shape": (ctypes.c_int, [_VP, _IP, _IP, _IP, _IP]),
         "fpcode_prepared_gamma": (ctypes.c_int, [_VP, ctypes.c_int, _U8P, _IP]),
         "fpcode_prepared_passes": (ctypes.c_int, [_VP, ctypes.POINTER(fpcode_pass_info), ctypes.c_int]),
+        "fpcode_test_prepared_row": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                    ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)]),
         "fpcode_test_task_ranges": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                    ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                                    ctypes.c_int]),
@@ -483,6 +485,18 @@ def fpcode_prepared_gamma(prep: Prepared, j: int):
     piv = (ctypes.c_int * prep.k)()
     _check(lib().fpcode_prepared_gamma(prep.handle, j, gam.ctypes.data_as(_U8P), piv), "fpcode_prepared_gamma")
     return gam, [piv[i] for i in range(prep.k)]
+
+
+def fpcode_test_prepared_row(prep: Prepared, j: int, t: int, v: int):
+    """(slices, signature words) stored for v * A_j[t]."""
+    r = max(1, int(prep.p).bit_length())
+    W = max(1, -(-(prep.n - prep.k) // 32))
+    sl = (ctypes.c_uint32 * (r * W))()
+    sg = (ctypes.c_uint32 * 64)()
+    nsig = lib().fpcode_test_prepared_row(prep.handle, j, t, v, sl, sg)
+    if nsig < 0:
+        raise FpcodeError(nsig, "fpcode_test_prepared_row")
+    return [int(x) for x in sl], [int(sg[i]) for i in range(nsig)]
 
 
 def fpcode_prepared_passes(prep: Prepared):

@@ -255,17 +255,24 @@ int prepare(int p, int n, int k, const uint8_t *G, const fpcode_opts &opts, Prep
   const size_t set_words = (size_t)k * ((size_t)(p - 1) * RWP + SIG);
   P->table.assign((size_t)m * set_words, 0u);
   const std::vector<uint8_t> &mul = E.mul;
-  std::vector<uint8_t> a(nk), y(nk);
-  // slice words of the values y[0..nk): word w, slice i at e[w * stride + i]
+  const int nk32 = W * 32;  // values padded with zeros to whole words
+  std::vector<uint8_t> a(nk32, 0), y(nk32, 0);
+  // slice words of the values y[0..nk): word w, slice i at e[w * stride + i].
+  // Eight symbols at a time: bit i of each byte, masked to the bytes' low
+  // bits, times 0x0102040810204080 lands byte b's bit at bit 56 + b with no
+  // carries (each product bit below 56 has one source), so the top byte is
+  // the eight bits in order.
   auto slice = [&](const std::vector<uint8_t> &vals, uint32_t *e, int nbits, int stride) {
-    for (int q0 = 0, w = 0; q0 < nk; q0 += 32, ++w) {
-      const int qn = std::min(32, nk - q0);
+    for (int w = 0; w < W; ++w)
       for (int i = 0; i < nbits; ++i) {
         uint32_t word = 0;
-        for (int b = 0; b < qn; ++b) word |= (uint32_t)((vals[q0 + b] >> i) & 1) << b;
+        for (int g8 = 0; g8 < 4; ++g8) {
+          uint64_t x;
+          std::memcpy(&x, &vals[(size_t)w * 32 + 8 * g8], 8);  // little-endian: symbol b in byte b
+          word |= (uint32_t)((((x >> i) & 0x0101010101010101ull) * 0x0102040810204080ull) >> 56) << (8 * g8);
+        }
         e[w * stride + i] = word;
       }
-    }
   };
   for (int j = 0; j < m; ++j)
     for (int t = 0; t < k; ++t) {
@@ -668,6 +675,20 @@ int fpcode_prepared_gamma(const fpcode_prepared *prep, int j, uint8_t *gamma, in
   if (pivots)
     for (int r = 0; r < P->k; ++r) pivots[r] = P->piv[(size_t)j * P->k + r];
   return FPCODE_OK;
+}
+
+int fpcode_test_prepared_row(const fpcode_prepared *prep, int j, int t, int v, uint32_t *slices, uint32_t *sig) {
+  const fph::Prepared *P = prep ? &prep->host : nullptr;
+  if (!P || j < 0 || j >= P->m || t < 0 || t >= P->k || v < 1 || v >= P->p || !slices) return FPCODE_EINVAL;
+  const size_t set_words = P->table_words_per_set();
+  const uint32_t *e = &P->table[(size_t)j * set_words + ((size_t)t * (P->p - 1) + (v - 1)) * P->rwpad];
+  std::memcpy(slices, e, (size_t)P->r * P->W * sizeof(uint32_t));
+  const int SIG = fpk::sig_words(P->p, P->r, P->W);
+  if (sig && SIG) {
+    const uint32_t *sg = &P->table[(size_t)j * set_words + (size_t)P->k * (P->p - 1) * P->rwpad + (size_t)t * SIG];
+    std::memcpy(sig, sg, (size_t)SIG * sizeof(uint32_t));
+  }
+  return SIG;
 }
 
 int fpcode_prepared_passes(const fpcode_prepared *prep, fpcode_pass_info *passes, int max) {

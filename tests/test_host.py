@@ -297,6 +297,42 @@ def test_prefix_walk_matches_unrank(k, g, p, lib):
 
 # ------------------------------------------------ preparation + schedule ----
 
+@pytest.mark.parametrize("p,n,k", [(3, 80, 40), (3, 30, 15), (7, 40, 20), (5, 70, 20), (7, 150, 30), (11, 40, 12),
+                                   (3, 140, 12)])
+def test_stored_rows_are_the_sliced_multiples(p, n, k, lib):
+    """Every stored table row is v * A_j[t] (the non-pivot part of row t of
+    Gamma_j, times v, mod p) in the bit-sliced natural encoding: word w,
+    slice i holds bit i of symbols 32w .. 32w + 31; for p = 3, 7 the pair
+    signature of representative c holds bits y_i xor y_{i+1} of y = c A_j[t]."""
+    code = inputs.single_code(77 + n, p, n, k)
+    pr = _prep(code)
+    m, _kj, _np, _c = B.fpcode_prepared_shape(pr)
+    r = p.bit_length()
+    W = -(-(n - k) // 32)
+    reps = {3: [1], 7: [1, 2, 4]}.get(p, [])
+
+    def sliced(vals, nbits):
+        out = []
+        for w in range(W):
+            for i in range(nbits):
+                out.append(sum(((int(vals[32 * w + b]) >> i) & 1) << b
+                               for b in range(32) if 32 * w + b < len(vals)))
+        return out
+
+    for j in range(m):
+        gam, piv = B.fpcode_prepared_gamma(pr, j)
+        red = [c for c in range(n) if c not in set(piv)]
+        for t in range(k):
+            a = [int(gam[t, c]) for c in red]
+            for v in range(1, p):
+                slices, sig = B.fpcode_test_prepared_row(pr, j, t, v)
+                assert slices == sliced([(v * x) % p for x in a], r), (j, t, v)
+            want = []
+            for c in reps:
+                y = [(c * x) % p for x in a]
+                want += sliced([(q ^ (q >> 1)) & ((1 << (r - 1)) - 1) for q in y], r - 1)
+            assert sig[:len(want)] == want and not any(sig[len(want):]), (j, t)
+
 def _prep(code, **kw):
     return B.fpcode_prepare(code.p, code.n, code.k, code.G, B.fpcode_opts_default(**kw))
 
