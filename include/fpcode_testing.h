@@ -100,9 +100,9 @@ int fpcode_prepared_single_pass(const fpcode_prepared *src, int pass, int u_init
  * arguments or a symbol >= p, FPCODE_ECUDA on a CUDA error. */
 int fpcode_bench_additions(int p, int sliced, int nvec, int nsym, int reps, const uint8_t *a, const uint8_t *b,
                            uint8_t *out, void *stream, double *ms);
-/* Bytes one search moves: host-to-device (tables, schedule, descriptors,
- * the first bound)
- * and device-to-host (final state). */
+/* Bytes one fpcode_min_distance call on this code moves: host-to-device
+ * (tables, schedule, descriptors, the first state and the zeroed per-pass
+ * bookkeeping, in one copy) and device-to-host (final state). */
 int fpcode_prepared_bytes(const fpcode_prepared *prep, uint64_t *h2d, uint64_t *d2h);
 
 #ifdef __cplusplus

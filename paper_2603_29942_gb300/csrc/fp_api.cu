@@ -196,6 +196,7 @@ void fill_static(const Layout &L, const std::vector<const fph::Prepared *> &code
     sd.per_round_check = P.opts.per_round_check;
     sd.mid_pass_exit = P.opts.mid_pass_exit;
     sd.complete = P.complete;
+    sd.seed_u = P.seed_u;
     sd.table = reinterpret_cast<const uint32_t *>(d + L.table_off[i]);
     sd.passes = reinterpret_cast<const PassDesc *>(d + L.pass_off[i]);
     std::memcpy(h + L.off_slots + i * sizeof(SlotDesc), &sd, sizeof(sd));
@@ -240,7 +241,10 @@ int smem_for(const std::vector<const fph::Prepared *> &codes) {
 
 // Upload one prepared code into device buffer `d` (static_bytes) via pinned
 // staging `h`; plan its tasks for the kernel's grid.
-int upload_one(fpcode_prepared *prep, cudaStream_t st, DevCtx &c, char *d, char *h) {
+// with_state: the host image also holds the first state (zeroed
+// bookkeeping, the bound in the best key) and one copy takes both, so the
+// next search needs no reset of its own.
+int upload_one(fpcode_prepared *prep, cudaStream_t st, DevCtx &c, char *d, char *h, bool with_state = false) {
   fph::Prepared &P = prep->host;
   const void *fn = kernel_for(P.variant);
   if (!fn) {
@@ -264,14 +268,22 @@ int upload_one(fpcode_prepared *prep, cudaStream_t st, DevCtx &c, char *d, char 
   fill_static(L, {&P}, c, h, d, 0);
   SlotDesc *sd = reinterpret_cast<SlotDesc *>(h + L.off_slots);
   sd->pass_times = reinterpret_cast<unsigned long long *>(d + L.off_times);
-  FP_CUDA(cudaMemcpyAsync(d, h, L.static_bytes, cudaMemcpyHostToDevice, st));
+  size_t bytes = L.static_bytes;
+  if (with_state) {
+    std::memset(h + L.off_states, 0, L.off_times - L.off_states);
+    bytes = L.off_times;
+    prep->state_ready = true;
+  }
+  FP_CUDA(cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, st));
   return FPCODE_OK;
 }
 
 int enqueue_one(fpcode_prepared *prep, cudaStream_t st, const fpcode_opts &o) {
   fph::Prepared &P = prep->host;
   Layout L = make_layout({&P});
-  FP_CUDA(cudaMemsetAsync(prep->dev + L.off_states, 0, L.dyn_bytes + L.aux_bytes, st));
+  const bool preloaded = prep->state_ready && prep->resume_from == 0 && prep->init_u == 0;
+  prep->state_ready = false;  // one search
+  if (!preloaded) FP_CUDA(cudaMemsetAsync(prep->dev + L.off_states, 0, L.dyn_bytes + L.aux_bytes, st));
   const bool resumed = prep->resume_from > 0;
   // the first state's values, staged in pinned memory (a copy from pageable
   // memory would wait for the stream)
@@ -296,11 +308,9 @@ int enqueue_one(fpcode_prepared *prep, cudaStream_t st, const fpcode_opts &o) {
                             &sg->useq, 4, cudaMemcpyHostToDevice, st));
     prep->resume_from = 0;  // one search
   }
-  // the bound as a key past every real one (pass 255), stored inverted: the
-  // probe's u_init, else the g = 1 passes' least weight
-  const int bound = prep->init_u > 0 ? prep->init_u : resumed ? 0 : P.seed_u;
-  if (bound > 0) {
-    sg->bound = ~fph::bound_key((uint32_t)bound);
+  // the probe's bound as a key past every real one (pass 255), stored inverted
+  if (prep->init_u > 0) {
+    sg->bound = ~fph::bound_key((uint32_t)prep->init_u);
     FP_CUDA(cudaMemcpyAsync(stp + offsetof(SlotState, best_key), &sg->bound, 8, cudaMemcpyHostToDevice, st));
   }
   if (!P.passes.empty()) {
@@ -523,9 +533,9 @@ int fpcode_min_distance(int p, int n, int k, const uint8_t *G, void *stream, int
   if (s) return s;
   std::lock_guard<std::mutex> lk(c->ws_mu);
   Layout L = make_layout({&prep.host});
-  // pinned: [static image][read-back][staging], so nothing waits between the
-  // upload and the launch
-  const size_t rb_off = align256(L.static_bytes), stage_off = rb_off + align256(L.dyn_bytes);
+  // pinned: [static image and first state][read-back][staging], so nothing
+  // waits between the upload and the launch
+  const size_t rb_off = align256(L.off_times), stage_off = rb_off + align256(L.dyn_bytes);
   s = ws_reserve(*c, L.total, stage_off + 64);
   if (s) return s;
   if (!c->ev0) {  // events of the workspace searches, made once per device
@@ -539,7 +549,7 @@ int fpcode_min_distance(int p, int n, int k, const uint8_t *G, void *stream, int
   prep.ev1 = c->ev1;
   prep.external = true;
   prep.dev = c->ws;
-  s = upload_one(&prep, st, *c, prep.dev, c->ws_pinned);
+  s = upload_one(&prep, st, *c, prep.dev, c->ws_pinned, true);
   if (s) return s;
   prep.pinned = c->ws_pinned + rb_off;
   prep.stage_off = stage_off - rb_off;
@@ -632,20 +642,11 @@ int fpcode_min_distance_batch(int num, const fpcode_desc *codes, void *stream, c
     for (int i : idx)
       fph::plan_tasks(preps[i].get(), ctas, o.prefixes_per_lane, many ? fph::kMinStepsBatch : fph::kMinStepsSingle, !many);
     Layout L = make_layout(codesv);
-    // pinned staging: the static image, then the codes' first states (each
-    // zero but its best key, the g = 1 passes' least key); later the read-back
-    const size_t st_off = (L.static_bytes + 255) & ~(size_t)255;
-    const size_t st_bytes = codesv.size() * sizeof(SlotState);
-    s = ws_reserve(*c, L.total, std::max(st_off + st_bytes, L.dyn_bytes));
+    s = ws_reserve(*c, L.total, std::max(L.static_bytes, L.dyn_bytes));
     if (s) break;
     fill_static(L, codesv, *c, c->ws_pinned, c->ws, 0);
-    SlotState *first = reinterpret_cast<SlotState *>(c->ws_pinned + st_off);
-    std::memset(first, 0, st_bytes);
-    for (size_t q = 0; q < codesv.size(); ++q)
-      first[q].best_key = codesv[q]->seed_u > 0 ? ~fph::bound_key((uint32_t)codesv[q]->seed_u) : 0ull;
     FP_CUDA(cudaMemcpyAsync(c->ws, c->ws_pinned, L.static_bytes, cudaMemcpyHostToDevice, st));
     FP_CUDA(cudaMemsetAsync(c->ws + L.off_states, 0, L.dyn_bytes + L.aux_bytes, st));
-    FP_CUDA(cudaMemcpyAsync(c->ws + L.off_states, first, st_bytes, cudaMemcpyHostToDevice, st));
     FP_CUDA(cudaEventRecord(e0, st));
     s = launch(fn, ctas, smem, st, c->ws, L, kparams(o, 0));
     if (s) break;
@@ -767,7 +768,7 @@ int fpcode_test_pass_times(fpcode_prepared *prep, void *stream, double *us, int 
 int fpcode_prepared_bytes(const fpcode_prepared *prep, uint64_t *h2d, uint64_t *d2h) {
   if (!prep) return FPCODE_EINVAL;
   Layout L = make_layout({&prep->host});
-  if (h2d) *h2d = L.static_bytes + (prep->host.seed_u > 0 ? 8 : 0);  // tables and descriptors, the first bound
+  if (h2d) *h2d = L.off_times;  // tables, descriptors, the first state and the zeroed bookkeeping
   if (d2h) *d2h = L.dyn_bytes;
   return FPCODE_OK;
 }

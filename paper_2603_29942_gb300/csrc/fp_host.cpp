@@ -348,11 +348,11 @@ int prepare(int p, int n, int k, const uint8_t *G, const fpcode_opts &opts, Prep
   }
   P->complete = truncated ? 0 : 1;
   // The g = 1 passes are the rows of the Gamma_j themselves: their least
-  // weight is known now.  A search starts with it as its bound (a bound key,
-  // no codeword behind it), so the tasks that start at once (every early
-  // pass) filter their leaves against it instead of against n - k + 2.  The
-  // outcome is unchanged: the g = 1 passes still run, record that weight
-  // with its key, and the termination tests see only recorded weights.
+  // weight is known now.  A search starts with it as its bound (the claims
+  // cap U with it; no key stands behind it), so the tasks that start at once
+  // (every early pass) filter their leaves against it instead of against
+  // n - k + 2.  The outcome is unchanged: the g = 1 passes still run, record
+  // that weight with its key, and the termination tests see only records.
   P->seed_u = 0;
   for (size_t q = 0; q < P->passes.size(); ++q) {
     if (P->passes[q].g != 1) continue;

@@ -42,7 +42,7 @@ struct Prepared {
   int complete = 0;              // schedule reaches the last level
   uint64_t code_hash = 0;        // FNV-1a of (p, n, k, per_round_check, defer) and G: the schedule's identity
   int seed_u = 0;                // least weight of the g = 1 passes (rows of the Gamma_j), 0: none;
-                                 // a search starts with it as its bound
+                                 // a search starts with it as its bound (SlotDesc.seed_u)
   int L0 = 0;                    // lower bound before any pass
   double t_prepare_ms = 0;
   size_t table_words_per_set() const { return (size_t)k * ((size_t)(p - 1) * rwpad + fpk::sig_words(p, r, W)); }
@@ -98,6 +98,7 @@ struct fpcode_prepared {
   size_t off_ctl = 0, off_slot = 0, off_pass = 0, off_table = 0, off_state = 0, dyn_bytes = 0;
   char *pinned = nullptr; // read-back of the dynamic part
   size_t stage_off = 0;   // pinned + stage_off: 64 bytes staging the first state's values (bound, resume)
+  bool state_ready = false;  // the upload also wrote the first state: the next search skips its reset
   void *ev0 = nullptr, *ev1 = nullptr;  // cudaEvent_t around the kernel
   fpcode_opts run_opts{};
 };

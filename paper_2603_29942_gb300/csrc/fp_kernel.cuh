@@ -578,7 +578,13 @@ __device__ __forceinline__ void mark_exhausted(const CtlStatic &cs, int s, unsig
 __device__ __forceinline__ void take(SlotState *st, const KParams &kp, bool serve, int s, unsigned long long w,
                                     uint64_t key, Claim *o, ClaimCache &cc) {
   const unsigned long long t = w & kTaskMask;
-  const int U = key == kNoKey ? cc.sd.n - cc.sd.k + 2 : (int)key_weight(key);
+  // the bound: the best recorded weight, else n - k + 2 (the skip rule uses
+  // this one: it needs a recorded key); the g = 1 passes' least weight
+  // (known before the search) caps the bound the task filters against, so
+  // the tasks that start at once filter against it.  No key stands behind
+  // the cap until the g = 1 passes record it.
+  const int Ukey = key == kNoKey ? cc.sd.n - cc.sd.k + 2 : (int)key_weight(key);
+  const int U = cc.sd.seed_u > 0 ? min(Ukey, cc.sd.seed_u) : Ukey;
   const int mid = kp.mid_pass < 0 ? cc.sd.mid_pass_exit : kp.mid_pass;
   o->sd = cc.sd;
   o->pd = cc.pd;
@@ -594,7 +600,7 @@ __device__ __forceinline__ void take(SlotState *st, const KParams &kp, bool serv
   o->U = U;
   // Early exit inside a pass: sound only if the best codeword comes from
   // this pass or an earlier one (passes run ahead of the termination test).
-  o->skip = (mid && key != kNoKey && (int)key_pass(key) <= cc.P && U <= cc.pd.L_before) ? 1 : 0;
+  o->skip = (mid && key != kNoKey && (int)key_pass(key) <= cc.P && Ukey <= cc.pd.L_before) ? 1 : 0;
   o->ndone = 1;
   if (o->skip && !serve && !cc.sd.per_round_check && (int)key_pass(key) < cc.P) {
     // With a test after every pass, a best codeword from a pass before P

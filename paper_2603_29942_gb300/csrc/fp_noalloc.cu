@@ -144,6 +144,7 @@ extern "C" int fpcode_min_distance_noalloc(int p, int n, int k, const uint8_t *G
   sd.per_round_check = P.opts.per_round_check;
   sd.mid_pass_exit = P.opts.mid_pass_exit;
   sd.complete = P.complete;
+  sd.seed_u = P.seed_u;
   sd.table = reinterpret_cast<const uint32_t *>(base + off_table);
   sd.passes = reinterpret_cast<const fpk::PassDesc *>(base + off_pass);
   std::memcpy(&img[off_slot - off_ctl], &sd, sizeof(sd));
@@ -152,10 +153,6 @@ extern "C" int fpcode_min_distance_noalloc(int p, int n, int k, const uint8_t *G
 
   NA_CUDA(cudaMemcpyAsync(base + off_ctl, img.data(), img.size(), cudaMemcpyHostToDevice, st));
   NA_CUDA(cudaMemsetAsync(base + off_state, 0, dyn_bytes + aux_bytes, st));  // state starts at zero
-  static thread_local unsigned long long seed;  // but for the g = 1 passes' least key, stored inverted
-  seed = P.seed_u > 0 ? ~fph::bound_key((uint32_t)P.seed_u) : 0ull;
-  NA_CUDA(cudaMemcpyAsync(base + off_state + offsetof(fpk::SlotState, best_key), &seed, sizeof(seed),
-                          cudaMemcpyHostToDevice, st));
   if (!P.passes.empty()) {
     const fpk::SlotDesc *slots = reinterpret_cast<const fpk::SlotDesc *>(base + off_slot);
     fpk::SlotState *states = reinterpret_cast<fpk::SlotState *>(base + off_state);

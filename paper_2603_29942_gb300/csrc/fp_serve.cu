@@ -300,6 +300,7 @@ int fpcode_serve_submit(fpcode_server *s, const fpcode_desc *code, uint64_t *tic
   sd.per_round_check = P->opts.per_round_check;
   sd.mid_pass_exit = P->opts.mid_pass_exit;
   sd.complete = P->complete;
+  sd.seed_u = P->seed_u;
   sd.table = reinterpret_cast<const uint32_t *>(d_tab);
   sd.passes = reinterpret_cast<const fpk::PassDesc *>(d_pass);
   sd.seq = tk;
@@ -318,7 +319,6 @@ int fpcode_serve_submit(fpcode_server *s, const fpcode_desc *code, uint64_t *tic
                           sizeof(fpk::SlotAux), cudaMemcpyHostToDevice, s->cst));
   fpk::SlotState fresh{};
   fresh.word = (unsigned long long)(tk & fpk::kGenMask) << fpk::kGenShift;
-  fresh.best_key = P->seed_u > 0 ? ~fph::bound_key((uint32_t)P->seed_u) : 0ull;  // the g = 1 passes' bound
   std::memcpy(stg + o_state, &fresh, sizeof(fresh));
   SV_CUDA(cudaMemcpyAsync(s->dev + s->off_states + (size_t)slot * sizeof(fpk::SlotState), stg + o_state,
                           sizeof(fpk::SlotState), cudaMemcpyHostToDevice, s->cst));

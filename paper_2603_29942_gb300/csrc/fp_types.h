@@ -96,12 +96,14 @@ struct SlotDesc {
   int32_t per_round_check;
   int32_t mid_pass_exit;
   int32_t complete;              // 1: the schedule runs to the last level
+  int32_t seed_u;                // > 0: least weight of the g = 1 passes, the search's first bound
+  int32_t pad_s[3];
   const uint32_t *table;         // m * k * (p-1) * rwpad words, device
   const PassDesc *passes;        // npasses entries, device
   uint64_t seq;                  // serving: ticket of the code in this slot
   unsigned long long *pass_times;  // optional: %globaltimer at each pass end (device)
 };
-static_assert(sizeof(SlotDesc) == 80, "SlotDesc layout");
+static_assert(sizeof(SlotDesc) == 96, "SlotDesc layout");
 
 // Dynamic state of one code, device memory (all zero = fresh).  Three
 // 128-byte lines keep apart what is written at different rates: the task
