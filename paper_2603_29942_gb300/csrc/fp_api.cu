@@ -91,6 +91,8 @@ const void *kernel_for(int variant) {
     case 0: return fpk::kernel_p3(W);
     case 1: return fpk::kernel_p5(W);
     case 2: return fpk::kernel_p7(W);
+    case 8: return fpk::kernel_mersenne(31, W);
+    case 9: return fpk::kernel_mersenne(127, W);
     default: return fpk::kernel_generic(cls - 3 + 4, W);
   }
 }
@@ -709,6 +711,7 @@ __global__ void bitslice_kernel(int op, int p, int count, const uint32_t *a, con
     case FPCODE_OP_ADD:
       if (p == 3) fpbs::add_exact<3, R>(xa, ya, za, p);
       else if (p == 7) fpbs::add_exact<7, R>(xa, ya, za, p);
+      else if (p == 31 || p == 127) fpbs::add_mersenne<R>(xa, ya, za);  // R = r of p here
       else fpbs::add_generic<R>(xa, ya, za, p);
       for (int q = 0; q < R; ++q) z[q] = za[q];
       break;

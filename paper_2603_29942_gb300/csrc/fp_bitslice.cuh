@@ -102,13 +102,47 @@ FP_HD void add_generic(const uint32_t *a, const uint32_t *b, uint32_t *s, int p)
   for (int i = 0; i < R; ++i) s[i] = (borrow & sum[i]) | (~borrow & diff[i]);
 }
 
-// Dispatch on a compile-time prime P (3 and 7 use Alg. 3 / Alg. 4).
+// ---------------------------------------------------------------------------
+// Exact addition for a Mersenne prime p = 2^R - 1 (p = 31, 127): the
+// end-around-carry form (Alg. 1's reduction unrolled over the R slices, as
+// Alg. 4 is for R = 3).  The R-bit ripple sum x of a and b leaves a carry c
+// out of bit R - 1; 2^R = 1 mod p, so c is added back at bit 0.  That second
+// ripple cannot carry out: c = 1 means a + b >= 2^R, so x = a + b - 2^R <=
+// 2^R - 4.  Last, x = 2^R - 1 (all ones, only when a + b = p) is 0 mod p.
+// ---------------------------------------------------------------------------
+template <int R>
+FP_HD void add_mersenne(const uint32_t *a, const uint32_t *b, uint32_t *s) {
+  uint32_t x[R];
+  uint32_t c = 0;
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const uint32_t t = a[i] ^ b[i];
+    x[i] = t ^ c;
+    c = (a[i] & b[i]) | (t & c);
+  }
+#pragma unroll
+  for (int i = 0; i < R; ++i) {  // + the end-around carry
+    const uint32_t t = x[i] & c;
+    x[i] ^= c;
+    c = t;
+  }
+  uint32_t ones = x[0];
+#pragma unroll
+  for (int i = 1; i < R; ++i) ones &= x[i];
+#pragma unroll
+  for (int i = 0; i < R; ++i) s[i] = x[i] ^ ones;
+}
+
+// Dispatch on a compile-time prime P (3 and 7 use Alg. 3 / Alg. 4, the
+// Mersenne primes 31 and 127 the end-around-carry form).
 template <int P, int R>
 FP_HD void add_exact(const uint32_t *a, const uint32_t *b, uint32_t *s, int p) {
   if (P == 3) {
     add_p3(a[0], a[1], b[0], b[1], s[0], s[1]);
   } else if (P == 7) {
     add_p7(a[0], a[1], a[2], b[0], b[1], b[2], s[0], s[1], s[2]);
+  } else if (P > 7 && P == (1 << R) - 1) {
+    add_mersenne<R>(a, b, s);
   } else {
     add_generic<R>(a, b, s, P ? P : p);
   }

@@ -200,7 +200,7 @@ int prepare(int p, int n, int k, const uint8_t *G, const fpcode_opts &opts, Prep
   P->r = fpbs::bits_for(p);
   P->W = std::max(1, ceil_div(n - k, 32));
   P->rwpad = (P->r * P->W + 3) & ~3;
-  P->variant = (p == 3 ? 0 : p == 5 ? 1 : p == 7 ? 2 : 3 + (P->r - 4)) * 4 + (P->W - 1);
+  P->variant = fpk::variant_id(p, P->r, P->W);
   if (P->table_bytes_per_set() > 96 * 1024) {
     set_error("bit-sliced multiples of one information set exceed 96 KiB (k (p-1) r W too large)");
     return FPCODE_EINVAL;
@@ -538,6 +538,8 @@ int fpcode_test_bitslice_host(int op, int p, const uint32_t *a, const uint32_t *
       if (!b) return FPCODE_EINVAL;
       if (p == 3) fpbs::add_exact<3, 2>(a, b, out, p);
       else if (p == 7) fpbs::add_exact<7, 3>(a, b, out, p);
+      else if (p == 31) fpbs::add_exact<31, 5>(a, b, out, p);
+      else if (p == 127) fpbs::add_exact<127, 7>(a, b, out, p);
       else {
         switch (r) {
           case 3: fpbs::add_generic<3>(a, b, out, p); break;

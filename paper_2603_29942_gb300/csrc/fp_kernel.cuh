@@ -474,12 +474,6 @@ struct Fixed {
   }
 };
 
-// Variant id: prime class * 4 + (W - 1); classes 0: p = 3, 1: p = 5,
-// 2: p = 7, 3 + (r - 4): other primes with r bits (r = 4..8).
-__host__ __device__ inline int variant_id(int p, int r, int W) {
-  int cls = p == 3 ? 0 : p == 5 ? 1 : p == 7 ? 2 : 3 + (r - 4);
-  return cls * 4 + (W - 1);
-}
 
 // Batched launches over codes with p in {3, 5, 7}: dispatch per task.  The
 // narrow kernel (WMAX = 2: n - k <= 64) holds half the variants and so

@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "../../include/fpcode.h"
+#include "fp_driver.h"
 #include "fp_internal.h"
 #include "fp_kernel.cuh"
 #include "fp_kernels.h"
@@ -65,15 +66,6 @@ int noalloc_setup(int dev, unsigned char **out) {
   return FPCODE_OK;
 }
 
-const void *kernel_of(int variant) {
-  const int cls = variant / 4, W = variant % 4 + 1;
-  switch (cls) {
-    case 0: return fpk::kernel_p3(W);
-    case 1: return fpk::kernel_p5(W);
-    case 2: return fpk::kernel_p7(W);
-    default: return fpk::kernel_generic(cls - 3 + 4, W);
-  }
-}
 
 }  // namespace
 
@@ -111,7 +103,7 @@ extern "C" int fpcode_min_distance_noalloc(int p, int n, int k, const uint8_t *G
   s = noalloc_setup(dev, &base);
   if (s) return s;
 
-  const void *fn = kernel_of(P.variant);
+  const void *fn = fpd::kernel_for(P.variant);
   if (!fn) return FPCODE_EINVAL;
   const int smem = (int)(((std::max<size_t>(16, P.table_bytes_per_set()) + 15) & ~(size_t)15) + fpk::kBinomBytes);
   if (smem > 48 * 1024) NA_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));

@@ -64,6 +64,14 @@ FPK_HD int sig_words(int p, int r, int W) {
 }
 FPK_HD int pair_rep(int p, int q) { return p == 7 ? (1 << q) : q + 1; }
 
+// Variant id: prime class * 4 + (W - 1); classes 0: p = 3, 1: p = 5,
+// 2: p = 7, 3 + (r - 4): other primes with r bits (r = 4..8), 8: p = 31,
+// 9: p = 127 (the Mersenne primes above 7, with their own exact add).
+FPK_HD int variant_id(int p, int r, int W) {
+  int cls = p == 3 ? 0 : p == 5 ? 1 : p == 7 ? 2 : p == 31 ? 8 : p == 127 ? 9 : 3 + (r - 4);
+  return cls * 4 + (W - 1);
+}
+
 // Unit range [lo, hi) of CTA task t of a pass with g >= 2 (a unit is
 // d.unit consecutive prefixes; every unit starts where the lowest digits of
 // the coefficient counter are zero, so all lanes of a warp take the same

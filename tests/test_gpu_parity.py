@@ -142,6 +142,23 @@ def _random_codes(seed, count):
         yield inputs.Code(p, n, k, G)
 
 
+@pytest.mark.parametrize("p,n,k,budget", [(31, 24, 6, 5 * 10 ** 7), (31, 50, 6, 5 * 10 ** 7), (31, 70, 10, 5 * 10 ** 7),
+                                          (127, 30, 5, 5 * 10 ** 7), (127, 80, 4, 5 * 10 ** 7),
+                                          (127, 110, 6, 5 * 10 ** 7)])
+def test_mersenne_prime_kernels_parity(p, n, k, budget):
+    """p = 31 and 127 run their own kernels (the end-around-carry exact add):
+    the same status, d, counts, L and U as the oracle, W = 1..4, certified
+    and budget-limited searches, and a valid witness."""
+    code = inputs.single_code(500 + n, p, n, k)
+    r = oracle.bz(code, threads=4, budget=budget)
+    res, _ = run(code, budget=budget)
+    assert res.status == status_of_oracle(r.status)
+    assert res.counts == r.counts and (res.L, res.U) == (r.L, r.U)
+    if r.status == oracle.OK:
+        assert res.d == r.d
+        check_witness(code, res.d, res.witness)
+
+
 @pytest.mark.parametrize("seed", range(6))
 def test_random_codes_parity(seed):
     """Random codes over several primes, word counts W = 1..4, rank-deficient
