@@ -415,12 +415,14 @@ void plan_tasks(Prepared *P, int ctas, int fixed_pl, int min_steps, bool spread_
       d.ntasks = (uint32_t)((N + lanes - 1) / lanes);
       continue;
     }
-    // guided: phase h has C tasks over half of what is left, until a task of
-    // the last phase holds about one unit per lane
-    uint32_t H = 1;
-    while (H < 12 && (N >> H) / C >= lanes) ++H;
+    // guided rows (task_range): tasks shrink as the pass drains, down to one
+    // unit per lane
+    uint32_t H = 0;
+    d.ntasks = (uint32_t)fpk::guided_phases((N + lanes - 1) / lanes, C, [&](uint64_t, uint64_t) {
+      ++H;
+      return false;
+    });
     d.phases = H;
-    d.ntasks = (uint32_t)(H * C);
   }
   // one task sequence over all passes
   uint64_t base = 0;

@@ -72,12 +72,29 @@ FPK_HD int variant_id(int p, int r, int W) {
   return cls * 4 + (W - 1);
 }
 
+// Guided tasks of a pass work in rows of kThreads units (one unit per lane
+// of a CTA), so every lane of a task but those of the pass's last row is
+// busy.  While more than C = plan_ctas rows are left, a phase gives each of
+// C tasks ceil(left / 2C) rows (tasks shrink as the pass drains); the last
+// rows go one per task.  Calls f(phase tasks, rows per task) per phase
+// until it returns true; returns the tasks of the pass.
+template <class F>
+FPK_HD uint64_t guided_phases(uint64_t rows, uint64_t C, F f) {
+  uint64_t left = rows, tasks = 0;
+  while (left > C) {
+    const uint64_t per = (left + 2 * C - 1) / (2 * C);  // >= 1 here
+    if (f(C, per)) return tasks;
+    tasks += C;
+    left -= C * per;
+  }
+  f(left, (uint64_t)1);
+  return tasks + left;
+}
+
 // Unit range [lo, hi) of CTA task t of a pass with g >= 2 (a unit is
 // d.unit consecutive prefixes; every unit starts where the lowest digits of
 // the coefficient counter are zero, so all lanes of a warp take the same
-// Gray steps).  Guided tasks: phase h (plan_ctas tasks) covers
-// [N - (N >> h), N - (N >> (h+1))) of the N units, the last phase the rest,
-// so tasks shrink as the pass drains.
+// Gray steps): fixed tasks of kThreads * pl units, or guided rows.
 FPK_HD void task_range(const PassDesc &d, uint64_t t, uint64_t *lo, uint64_t *hi) {
   const uint64_t N = d.nprefix / d.unit;
   if (d.pl > 0 || d.phases == 0) {
@@ -86,13 +103,20 @@ FPK_HD void task_range(const PassDesc &d, uint64_t t, uint64_t *lo, uint64_t *hi
     *hi = *lo + chunk < N ? *lo + chunk : N;
     return;
   }
-  const uint64_t C = d.plan_ctas;
-  const uint64_t h = t / C, i = t % C;
-  const uint64_t plo = N - (N >> h);
-  const uint64_t phi = (h + 1 == d.phases) ? N : N - (N >> (h + 1));
-  const uint64_t size = phi - plo;
-  *lo = plo + size * i / C;
-  *hi = plo + size * (i + 1) / C;
+  const uint64_t rows = (N + kThreads - 1) / kThreads;
+  uint64_t row0 = 0, nrow = 1;
+  guided_phases(rows, d.plan_ctas, [&](uint64_t tasks, uint64_t per) {
+    if (t < tasks) {
+      row0 += t * per;
+      nrow = per;
+      return true;
+    }
+    t -= tasks;
+    row0 += tasks * per;
+    return false;
+  });
+  *lo = row0 * kThreads;
+  *hi = (row0 + nrow) * kThreads < N ? (row0 + nrow) * kThreads : N;
 }
 static_assert(sizeof(PassDesc) == 80, "PassDesc layout");
 
