@@ -63,7 +63,8 @@ struct KParams {
 // Launch-wide dynamic flags (zeroed before each launch).
 struct CtlDyn {
   int32_t err;   // 1: a hand-off wait gave up; 2: time limit reached
-  int32_t pad[3];
+  int32_t pad;
+  unsigned long long last_busy;  // serving: %globaltimer of a recent claim that found work (max over CTAs)
 };
 
 // Shared memory: binomial columns C(n, t), t < kBinomCols, then the staged
@@ -527,6 +528,7 @@ struct ClaimCache {
   SlotDesc sd;
   PassDesc pd;
   unsigned int sleep_ns;
+  unsigned long long busy_note;  // serving: when this CTA last raised last_busy
 };
 
 // Pass of global task t: the cached pass, the next one, else a binary
@@ -717,12 +719,19 @@ __device__ __forceinline__ int claim(const SlotDesc *slots, SlotState *states, c
   if (ld_vol(&cd->err)) return kCmdExit;
   if (wait_t0 == 0) {
     wait_t0 = now;
-  } else {
-    unsigned long long lim = live ? kp.wait_limit_ns : kp.idle_limit_ns;
-    if (now - wait_t0 > lim) {
-      if (live) atomicExch(&cd->err, 1);
+  } else if (live) {
+    if (now - wait_t0 > kp.wait_limit_ns) {
+      atomicExch(&cd->err, 1);
       return kCmdExit;
     }
+  } else {
+    // serving, nothing to do: the kernel leaves once no CTA has found work
+    // for the idle limit, all CTAs together (a CTA leaving on its own idle
+    // time would shrink the kernel while a few CTAs keep taking the small
+    // codes, and a large code arriving then ran on those few)
+    const unsigned long long busy = ld_vol(&cd->last_busy);
+    const unsigned long long since = busy > wait_t0 ? busy : wait_t0;
+    if (now > since && now - since > kp.idle_limit_ns) return kCmdExit;
   }
   __nanosleep(cc.sleep_ns);  // back off: idle probes must not crowd the state's cache lines
   if (cc.sleep_ns < 4096) cc.sleep_ns <<= 1;
@@ -823,6 +832,7 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
     s_cc.P = -1;
     s_cc.gen = 0;
     s_cc.sleep_ns = 128;
+    s_cc.busy_note = 0;
   }
   {
     static_assert(kBinomBytes == sizeof(cs.binom->cols), "staged binomial columns");
@@ -839,6 +849,13 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
     if (tid == 0) {
       const int cmd = claim(slots, states, cs, kp, cdyn, rr, wait_t0, t_start, &s_cl, s_cc);
       s_cmd = cmd;
+      if (cmd == kCmdRun && cs.serve) {  // keep the serving kernel whole (at most one note per 0.5 ms)
+        const unsigned long long now = globaltimer();
+        if (now - s_cc.busy_note > 500000ull) {
+          atomicMax(&cdyn->last_busy, now);
+          s_cc.busy_note = now;
+        }
+      }
       if (cmd == kCmdRun) {
         s_stage = (!s_cl.skip && (s_cl.slot != s_staged_slot || s_cl.pd.j != s_staged_j ||
                                   s_cl.sd.seq != s_staged_seq)) ? 1 : 0;
