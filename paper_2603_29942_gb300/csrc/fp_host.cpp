@@ -130,6 +130,24 @@ struct Eliminator {
 
 int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
+// s = a + b mod p on W words of r slices each (word-major: slice i of word w
+// at [w * r + i]), by the exact bit-sliced add.
+template <int RR>
+void add_words_r(const uint32_t *a, const uint32_t *b, uint32_t *s, int W, int p) {
+  for (int w = 0; w < W; ++w) fpbs::add_generic<RR>(a + w * RR, b + w * RR, s + w * RR, p);
+}
+void add_sliced_words(int r, const uint32_t *a, const uint32_t *b, uint32_t *s, int W, int p) {
+  switch (r) {
+    case 2: add_words_r<2>(a, b, s, W, p); break;
+    case 3: add_words_r<3>(a, b, s, W, p); break;
+    case 4: add_words_r<4>(a, b, s, W, p); break;
+    case 5: add_words_r<5>(a, b, s, W, p); break;
+    case 6: add_words_r<6>(a, b, s, W, p); break;
+    case 7: add_words_r<7>(a, b, s, W, p); break;
+    default: add_words_r<8>(a, b, s, W, p); break;
+  }
+}
+
 uint64_t sat_mul(uint64_t a, uint64_t b) {
   if (a == 0 || b == 0) return 0;
   if (a > ~0ull / b) return ~0ull;
@@ -235,8 +253,11 @@ int prepare(int p, int n, int k, const uint8_t *G, const fpcode_opts &opts, Prep
     for (int r = 0; r < k; ++r) rows[r] = r;
     std::sort(rows.begin(), rows.end(), [&](int a, int b) { return E.owner[a] < E.owner[b]; });
     std::vector<char> is_piv(n, 0);
-    for (int r : rows) {
-      for (int c = 0; c < n; ++c) P->gam.push_back((uint8_t)E.M[(size_t)r * n + c]);
+    const size_t g0 = P->gam.size();
+    P->gam.resize(g0 + (size_t)k * n);
+    for (int q = 0; q < k; ++q) {
+      const int r = rows[q];
+      std::memcpy(&P->gam[g0 + (size_t)q * n], &E.M[(size_t)r * n], (size_t)n);
       P->piv.push_back(E.owner[r]);
       is_piv[E.owner[r]] = 1;
     }
@@ -254,9 +275,8 @@ int prepare(int p, int n, int k, const uint8_t *G, const fpcode_opts &opts, Prep
   const int SIG = fpk::sig_words(p, R, W);
   const size_t set_words = (size_t)k * ((size_t)(p - 1) * RWP + SIG);
   P->table.assign((size_t)m * set_words, 0u);
-  const std::vector<uint8_t> &mul = E.mul;
   const int nk32 = W * 32;  // values padded with zeros to whole words
-  std::vector<uint8_t> a(nk32, 0), y(nk32, 0);
+  std::vector<uint8_t> a(nk32, 0);
   // slice words of the values y[0..nk): word w, slice i at e[w * stride + i].
   // Eight symbols at a time: bit i of each byte, masked to the bytes' low
   // bits, times 0x0102040810204080 lands byte b's bit at bit 56 + b with no
@@ -274,27 +294,25 @@ int prepare(int p, int n, int k, const uint8_t *G, const fpcode_opts &opts, Prep
         e[w * stride + i] = word;
       }
   };
+  // Row t's multiples: v = 1 sliced from the symbols, then v A = (v-1) A + A
+  // by the exact bit-sliced add; a pair signature word i is slice i xor
+  // slice i+1 of the representative's multiple.
   for (int j = 0; j < m; ++j)
     for (int t = 0; t < k; ++t) {
       const uint8_t *row = &P->gam[((size_t)j * k + t) * n];
       const int *red = &P->red[(size_t)j * nk];
       for (int q = 0; q < nk; ++q) a[q] = row[red[q]];
-      for (int v = 1; v < p; ++v) {
-        uint32_t *e = &P->table[(size_t)j * set_words + ((size_t)t * (p - 1) + (v - 1)) * RWP];
-        const uint8_t *mv = &mul[(size_t)v * p];
-        for (int q = 0; q < nk; ++q) y[q] = mv[a[q]];
-        slice(y, e, R, R);
-      }
+      uint32_t *e0 = &P->table[(size_t)j * set_words + (size_t)t * (p - 1) * RWP];
+      slice(a, e0, R, R);
+      for (int v = 2; v < p; ++v) add_sliced_words(R, e0 + (size_t)(v - 2) * RWP, e0, e0 + (size_t)(v - 1) * RWP, W, p);
       if (SIG) {
         uint32_t *sg = &P->table[(size_t)j * set_words + (size_t)k * (p - 1) * RWP + (size_t)t * SIG];
         const int npair = (p - 1) / 2;
         for (int pq = 0; pq < npair; ++pq) {
-          const uint8_t *mc = &mul[(size_t)fpk::pair_rep(p, pq) * p];
-          for (int q = 0; q < nk; ++q) {
-            const int v = mc[a[q]];
-            y[q] = (uint8_t)((v ^ (v >> 1)) & ((1 << (R - 1)) - 1));  // bit i: y_i xor y_{i+1}
-          }
-          slice(y, sg + (size_t)pq * W * (R - 1), R - 1, R - 1);
+          const uint32_t *ec = e0 + (size_t)(fpk::pair_rep(p, pq) - 1) * RWP;
+          for (int w = 0; w < W; ++w)
+            for (int i = 0; i + 1 < R; ++i)
+              sg[(size_t)pq * W * (R - 1) + (size_t)w * (R - 1) + i] = ec[w * R + i] ^ ec[w * R + i + 1];
         }
       }
     }

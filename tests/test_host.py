@@ -298,7 +298,7 @@ def test_prefix_walk_matches_unrank(k, g, p, lib):
 # ------------------------------------------------ preparation + schedule ----
 
 @pytest.mark.parametrize("p,n,k", [(3, 80, 40), (3, 30, 15), (7, 40, 20), (5, 70, 20), (7, 150, 30), (11, 40, 12),
-                                   (3, 140, 12)])
+                                   (3, 140, 12), (31, 60, 10), (127, 40, 6), (251, 20, 4)])
 def test_stored_rows_are_the_sliced_multiples(p, n, k, lib):
     """Every stored table row is v * A_j[t] (the non-pivot part of row t of
     Gamma_j, times v, mod p) in the bit-sliced natural encoding: word w,
