@@ -43,7 +43,7 @@ struct PassDesc {
   int32_t round_end;  // last pass of round g (per-round termination check)
   int32_t pl;         // > 0: fixed tasks of kThreads * pl units; 0: guided
   uint32_t ntasks;    // CTA tasks in the pass
-  uint32_t phases;    // guided: phases of plan_ctas tasks, each half the last (0: 256-prefix tasks)
+  uint32_t phases;    // guided: number of phases (guided_phases), 0: fixed tasks of kThreads units
   uint64_t nprefix;   // prefixes (g >= 2) or rows (g == 1)
   uint64_t size;      // codewords in the pass: C(k,g)(p-1)^(g-1)
   uint64_t NC;        // (p-1)^(g-2) coefficient vectors per prefix subset
