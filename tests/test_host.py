@@ -424,6 +424,30 @@ def test_task_ranges_tile_each_pass(ctas, fixed_pl, min_steps, lib):
             assert sizes[0] + 256 >= sizes[-1]  # tasks shrink as the pass drains (up to one unit)
 
 
+def test_guided_tasks_are_whole_rows_and_shrink(lib):
+    """A guided pass is cut into rows of one prefix unit per lane (256
+    units): every task but the pass's last holds whole rows, and task sizes
+    never grow along the pass, ending on one-row tasks."""
+    code = inputs.single("f3_n80_k40")
+    pr = _prep(code)
+    passes = B.fpcode_prepared_passes(pr)
+    seen = 0
+    for i, (g, _j, _Lb, _La, _re, _size, nprefix) in enumerate(passes[:14]):
+        if g < 2:
+            continue
+        for ctas in (608, 152):
+            ranges = B.fpcode_test_task_ranges(pr, i, ctas, 0, 8)
+            sizes = [hi - lo for lo, hi in ranges]
+            if nprefix < 256 * ctas * 8:
+                continue  # fixed tasks of a small pass
+            seen += 1
+            unit = sizes[-2] // 256  # a one-row task
+            assert all(sz % (256 * unit) == 0 for sz in sizes[:-1]), (i, ctas)
+            assert all(a >= b for a, b in zip(sizes[:-1], sizes[1:-1])), (i, ctas)
+            assert sizes[-2] == 256 * unit and sizes[-1] <= 256 * unit
+    assert seen >= 4
+
+
 def test_schedule_stays_within_staged_binomial_columns():
     """A level g needs binomial columns up to g - 1 in shared memory (24 are
     staged).  k = 24 over F_3 schedules every level up to g = 24; for larger
