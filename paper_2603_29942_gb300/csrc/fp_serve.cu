@@ -48,11 +48,20 @@ constexpr int kMaxPassesPerSlot = fpk::kMaxPasses;
 constexpr size_t kServeTableSet = 32 * 1024;      // shared memory per CTA: largest table of one set
 constexpr size_t kServeTableCode = 256 * 1024;    // largest table of one code
 
+// A slot whose code has concluded is reused only after this quiet time.
+// Tasks of later passes may still be running when a code concludes (they
+// ran ahead of its termination test); each stops within 16 of its Gray
+// steps (it reads the finished flag that often) and then counts itself off
+// in the slot's bookkeeping.  Reusing the slot earlier could let such a
+// count or record land in the next code's bookkeeping.
+constexpr auto kSlotQuiet = std::chrono::milliseconds(1);
+
 struct Slot {
   bool busy = false;
   uint64_t ticket = 0;
   size_t arena_off = 0, arena_bytes = 0;
   std::unique_ptr<fph::Prepared> prep;
+  std::chrono::steady_clock::time_point free_at{};  // not reused before (kSlotQuiet after its completion)
 };
 
 }  // namespace
@@ -264,13 +273,14 @@ int fpcode_serve_submit(fpcode_server *s, const fpcode_desc *code, uint64_t *tic
     return FPCODE_OK;
   }
   int slot = -1;
+  const auto now = std::chrono::steady_clock::now();
   for (int i = 0; i < s->S; ++i)
-    if (!s->slots[i].busy) {
+    if (!s->slots[i].busy && now >= s->slots[i].free_at) {
       slot = i;
       break;
     }
   if (slot < 0) {
-    fph::set_error("serve: no free slot");
+    fph::set_error("serve: no free slot (or none quiet yet)");
     return FPCODE_EBUSY;
   }
   size_t aoff = 0;
@@ -365,6 +375,7 @@ int fpcode_serve_poll(fpcode_server *s, fpcode_result *out, uint64_t *tickets, u
     tickets[n++] = sl.ticket;
     arena_free(s, sl.arena_off, sl.arena_bytes);
     sl.busy = false;
+    sl.free_at = std::chrono::steady_clock::now() + kSlotQuiet;
     sl.prep.reset();
     --s->running;
   }
