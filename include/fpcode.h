@@ -8,8 +8,10 @@
  * of exactly g rows with nonzero coefficients is enumerated; g grows until
  * the lower bound L meets the best weight U found.  Codewords are held in
  * the paper's bit-sliced natural encoding (Sec. 2, Sec. 4.1), so F_p
- * addition is a boolean formula over 32-bit words (Alg. 3, Alg. 4) and a
- * weight is the popcount of the OR of the slices (Sec. 4.3).
+ * addition is a boolean formula over 32-bit words (Alg. 3 for p = 3,
+ * Alg. 4 for p = 7 and its end-around-carry form for p = 31 and 127, a
+ * ripple add with a conditional subtraction of p otherwise) and a weight is
+ * the popcount of the OR of the slices (Sec. 4.3).
  *
  * Conventions for every call:
  *   - Returns an fpcode status (FPCODE_OK = 0).  Outputs are written only on
