@@ -89,8 +89,10 @@ struct Eliminator {
       }
     if (r < 0) return false;
     uint8_t *row = &M[(size_t)r * n];
-    const uint8_t *ms = &mul[(size_t)inv[row[c]] * p];
-    for (int i = 0; i < n; ++i) row[i] = ms[row[i]];
+    if (row[c] != 1) {  // scale the pivot row to a leading 1
+      const uint8_t *ms = &mul[(size_t)inv[row[c]] * p];
+      for (int i = 0; i < n; ++i) row[i] = ms[row[i]];
+    }
     // multiples (p - f) * row, formed once per pivot, for the f that occur
     const uint16_t pp = (uint16_t)p;
     const uint8_t p8 = (uint8_t)p;
