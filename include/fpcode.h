@@ -197,8 +197,9 @@ int fpcode_min_distance(int p, int n, int k, const uint8_t *G, void *stream, int
  * loading the library keeps until exit; a code whose tables, schedule and
  * state need more than that is rejected with FPCODE_EINVAL (message in
  * fpcode_last_error) -- use fpcode_min_distance for it.  The first call on
- * a device looks up the array's device address (make it before any stream
- * capture).  Calls share the array: calls that overlap on the GPU race, and
+ * a device looks up the array's device address and writes a table into it
+ * (make it before any stream capture; a cudaDeviceReset after it is not
+ * supported).  Calls share the array: calls that overlap on the GPU race, and
  * calls from this process are serialised on the host.  Same arguments and
  * results as fpcode_min_distance. */
 int fpcode_min_distance_noalloc(int p, int n, int k, const uint8_t *G, void *stream, int *d, uint8_t *witness);

@@ -37,6 +37,7 @@ struct CtlStatic {
   Completion *done_host;  // serving: host-mapped completion records (else null)
   SlotAux *aux;           // per-slot pass minima and counts (zeroed with the states)
   uint32_t *slot_flags;   // per slot, padded to a multiple of four: see kSlotFinished
+  uint32_t *inflight;     // serving: claims in flight per slot (kInflightStride apart); null otherwise
   int32_t nslots;
   int32_t serve;          // serving: slots appear while the kernel runs
 };
@@ -567,6 +568,22 @@ __device__ __forceinline__ void mark_exhausted(const CtlStatic &cs, int s, unsig
   atomicCAS(&cs.slot_flags[s], g, g | kSlotExhausted);
 }
 
+// Serving: a claim enters the slot before it reads the finished flag and
+// leaves it after its task's last write.  With the full fences on both
+// sides (here and in conclude), either the claim sees the code finished or
+// the concluding CTA sees the claim in flight and waits for it: no task of
+// a code writes into a slot after the code's completion is posted, so the
+// host may hand the slot to the next code at once.
+__device__ __forceinline__ void slot_enter(const CtlStatic &cs, int s) {
+  if (cs.inflight) {
+    atomicAdd(&cs.inflight[s * kInflightStride], 1u);
+    __threadfence();
+  }
+}
+__device__ __forceinline__ void slot_leave(const CtlStatic &cs, int s) {
+  if (cs.inflight) atomicSub(&cs.inflight[s * kInflightStride], 1u);
+}
+
 // Thread 0: fill in the claim of task t (global index, already located in
 // cc.P) of slot s.  A task the skip rule drops needs no work; every later
 // task of the pass is then droppable too, so the rest of the pass is taken
@@ -641,6 +658,7 @@ __device__ __forceinline__ int claim(const SlotDesc *slots, SlotState *states, c
     const int s = cc.slot;
     SlotState *st = &states[s];
     unsigned long long w = atomicAdd(&st->word, 1ull);
+    slot_enter(cs, s);
     int fin = ld_vol(&st->finished);
     uint64_t key = best_key(st);
     if ((w >> kGenShift) != cc.gen) {
@@ -651,7 +669,7 @@ __device__ __forceinline__ int claim(const SlotDesc *slots, SlotState *states, c
       fin = ld_vol(&st->finished);
       key = best_key(st);
     }
-    if ((w >> kGenShift) == cc.gen && cc.sd.npasses > 0 && !fin) {
+    if ((w >> kGenShift) == cc.gen && cc.sd.npasses > 0 && fin != fin_tag(cc.gen)) {
       if (locate(cc, w & kTaskMask)) {
         take(st, kp, cs.serve != 0, s, w, key, o, cc);
         rr = s;
@@ -661,6 +679,7 @@ __device__ __forceinline__ int claim(const SlotDesc *slots, SlotState *states, c
       }
       mark_exhausted(cs, s, cc.gen);
     }
+    slot_leave(cs, s);
   }
   bool live = false;
   // four slot flags per load, from the group of the slot served last
@@ -695,6 +714,7 @@ __device__ __forceinline__ int claim(const SlotDesc *slots, SlotState *states, c
       }
       if (!kp.lookahead && cc.P > ld_vol(&st->frontier)) continue;  // one pass at a time
       w = atomicAdd(&st->word, 1ull);
+      slot_enter(cs, s);
       if ((w >> kGenShift) != cc.gen) {
         // the slot now holds a newer code; its descriptor was written before
         // its state, so re-reading it gives the code this task belongs to
@@ -702,10 +722,18 @@ __device__ __forceinline__ int claim(const SlotDesc *slots, SlotState *states, c
         cc.sd = load_cg(&slots[s]);
         cc.gen = cc.sd.seq & kGenMask;
         cc.P = -1;
-        if (cc.gen != (w >> kGenShift)) continue;
+        if (cc.gen != (w >> kGenShift)) {
+          slot_leave(cs, s);
+          continue;
+        }
       }
       if (!locate(cc, w & kTaskMask)) {
         mark_exhausted(cs, s, cc.gen);
+        slot_leave(cs, s);
+        continue;
+      }
+      if (ld_vol(&st->finished) == fin_tag(cc.gen)) {  // concluded since the check above: nothing to do
+        slot_leave(cs, s);
         continue;
       }
       take(st, kp, cs.serve != 0, s, w, best_key(st), o, cc);
@@ -741,9 +769,9 @@ __device__ __forceinline__ int claim(const SlotDesc *slots, SlotState *states, c
 constexpr int kFrontierDone = 1 << 30;  // frontier value once the code is concluded
 
 // Finish the code: certified at pass sp, or out of passes.
-__device__ __forceinline__ void conclude(const CtlStatic &cs, const SlotDesc &sd, SlotState *st, SlotAux *ax,
-                                        int slot, int sp, bool certified) {
-  const int status = (certified || sd.complete) ? 0 : 4 /* FPCODE_EBUDGET */;
+__device__ __forceinline__ void conclude(const CtlStatic &cs, const KParams &kp, CtlDyn *cd, const SlotDesc &sd,
+                                        SlotState *st, SlotAux *ax, int slot, int sp, bool certified) {
+  int status = (certified || sd.complete) ? 0 : 4 /* FPCODE_EBUDGET */;
   unsigned long long entered = 0;
   for (int P = 0; P <= sp; ++P) entered += atomicAdd(&ax->pass_count[P], 0ull);
   const uint64_t key = ~(uint64_t)atomicOr(&st->best_key, 0ull);
@@ -751,8 +779,27 @@ __device__ __forceinline__ void conclude(const CtlStatic &cs, const SlotDesc &sd
   st->stop_pass = sp;
   st->status = kDoneFlag | status;
   __threadfence();
-  atomicExch(&st->finished, 1);
+  atomicExch(&st->finished, fin_tag(sd.seq));
   atomicOr(&cs.slot_flags[slot], kSlotFinished);
+  if (cs.inflight) {
+    // serving: wait until no other claim of this slot is in flight (this
+    // CTA's own is the one left).  Tasks that ran ahead stop within 16 Gray
+    // steps of reading the flag; claims made from now on see it and leave
+    // without a write.  Only then is the outcome posted, and the host may
+    // hand the slot to the next code.  Bounded: past the wait limit the
+    // code reports a timeout and the host keeps the slot until the kernel
+    // has exited.
+    __threadfence();
+    const unsigned long long t0 = globaltimer();
+    while (*(volatile const uint32_t *)&cs.inflight[slot * kInflightStride] > 1u) {
+      if (globaltimer() - t0 > kp.wait_limit_ns) {
+        status = 5;  // FPCODE_ETIMEOUT
+        atomicExch(&cd->err, 1);
+        break;
+      }
+      __nanosleep(256);
+    }
+  }
   if (cs.done_host) {  // serving: post the outcome; the host may reuse the slot after seq
     Completion *c = cs.done_host + slot;
     c->best_key = key;
@@ -770,8 +817,9 @@ __device__ __forceinline__ void conclude(const CtlStatic &cs, const SlotDesc &sd
 // it, and moves the frontier on.  Two CTAs may test the same pass: they
 // read the same final values and write the same results, and the
 // compare-and-swap on the frontier lets exactly one move it.
-__device__ __forceinline__ void finish_task(const CtlStatic &cs, const SlotDesc &sd, SlotState *st, SlotAux *ax,
-                                            int slot, int P, const PassDesc &pd, unsigned int ndone) {
+__device__ __forceinline__ void finish_task(const CtlStatic &cs, const KParams &kp, CtlDyn *cd, const SlotDesc &sd,
+                                            SlotState *st, SlotAux *ax, int slot, int P, const PassDesc &pd,
+                                            unsigned int ndone) {
   __threadfence();
   const unsigned int done = atomicAdd(&ax->pass_done[P], ndone) + ndone;
   if (done != pd.ntasks) return;
@@ -792,7 +840,7 @@ __device__ __forceinline__ void finish_task(const CtlStatic &cs, const SlotDesc 
     const bool certified = check && pf.L_after >= useq;
     if (certified || f + 1 >= sd.npasses) {
       // the frontier jumps past every pass, so no later pass is ever tested
-      if (atomicCAS(&st->frontier, f, kFrontierDone) == f) conclude(cs, sd, st, ax, slot, f, certified);
+      if (atomicCAS(&st->frontier, f, kFrontierDone) == f) conclude(cs, kp, cd, sd, st, ax, slot, f, certified);
       return;
     }
     ax->useq_after[f] = useq;  // a second tester writes the same value here
@@ -893,7 +941,11 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
         atomicAdd(&states[slot].enumerated, s_count);
         atomicAdd(&ax->pass_count[s_cl.pass], s_count);
       }
-      finish_task(cs, s_cl.sd, &states[slot], ax, slot, s_cl.pass, s_cl.pd, s_cl.ndone);
+      finish_task(cs, kp, cdyn, s_cl.sd, &states[slot], ax, slot, s_cl.pass, s_cl.pd, s_cl.ndone);
+      if (cs.inflight) {
+        __threadfence();  // the task's writes before it leaves the slot
+        slot_leave(cs, slot);
+      }
     }
   }
 }

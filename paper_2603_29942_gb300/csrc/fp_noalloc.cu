@@ -12,7 +12,8 @@
 // Host code never uses the array's name as an address: on the first call
 // on a device (with that device current) the address is fetched once with
 // cudaGetSymbolAddress and cached per device; that first call should
-// therefore come before any stream capture.  Every call shares the array
+// therefore come before any stream capture, and a cudaDeviceReset after it
+// is not supported.  Every call shares the array
 // and it keeps the last call's contents, so calls that overlap on the GPU
 // (different streams or threads on the same device) race; a mutex
 // serialises calls from this process on the host side.  The state words the
@@ -53,7 +54,10 @@ size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
   } while (0)
 
 // Once per device, with the device current: fetch the array's device
-// address and write the binomial table at its start.
+// address and write the binomial table at its start.  The address and the
+// table are kept for the life of the device's context: a cudaDeviceReset
+// after the first call on that device is not supported (the table written
+// once would be gone).
 int noalloc_setup(int dev, unsigned char **out) {
   if (!g_noalloc_ready[dev]) {
     void *ptr = nullptr;
@@ -97,20 +101,25 @@ extern "C" int fpcode_min_distance_noalloc(int p, int n, int k, const uint8_t *G
 
   int dev = 0;
   NA_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) return FPCODE_EINVAL;
+  if (dev < 0 || dev >= kMaxDevices) {
+    fph::set_error("fpcode_min_distance_noalloc: device index out of range");
+    return FPCODE_EINVAL;
+  }
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
   unsigned char *base = nullptr;
   s = noalloc_setup(dev, &base);
   if (s) return s;
 
   const void *fn = fpd::kernel_for(P.variant);
-  if (!fn) return FPCODE_EINVAL;
+  if (!fn) {
+    fph::set_error("fpcode_min_distance_noalloc: no kernel for this (p, n - k)");
+    return FPCODE_EINVAL;
+  }
   const int smem = (int)(((std::max<size_t>(16, P.table_bytes_per_set()) + 15) & ~(size_t)15) + fpk::kBinomBytes);
-  if (smem > 48 * 1024) NA_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   int per_sm = 0, sms = 0;
-  NA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, fpk::kThreads, (size_t)smem));
+  s = fpd::occupancy(fn, smem, P.opts.ctas_per_sm, &per_sm);  // sets the message when nothing fits
+  if (s) return s;
   NA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  if (per_sm < 1) return FPCODE_EINVAL;
   const int ctas = sms * per_sm;
   fph::plan_tasks(&P, ctas, 0, fph::kMinStepsSingle, true);
 
@@ -150,10 +159,7 @@ extern "C" int fpcode_min_distance_noalloc(int p, int n, int k, const uint8_t *G
     fpk::SlotState *states = reinterpret_cast<fpk::SlotState *>(base + off_state);
     const fpk::CtlStatic *ctl = reinterpret_cast<const fpk::CtlStatic *>(base + off_ctl);
     fpk::CtlDyn *dyn = reinterpret_cast<fpk::CtlDyn *>(base + off_state + dyn_bytes - sizeof(fpk::CtlDyn));
-    fpk::KParams kp{};
-    kp.wait_limit_ns = (unsigned long long)(o.wait_limit_s * 1e9);
-    kp.mid_pass = o.mid_pass_exit ? 1 : 0;
-    kp.lookahead = o.lookahead ? 1 : 0;
+    fpk::KParams kp = fpd::kparams(o, 0);  // the same limits as the allocating entry point
     void *args[] = {(void *)&slots, (void *)&states, (void *)&ctl, (void *)&dyn, (void *)&kp};
     NA_CUDA(cudaLaunchKernel(fn, dim3(ctas), dim3(fpk::kThreads), args, (size_t)smem, st));
   }

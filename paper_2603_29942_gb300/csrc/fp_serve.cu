@@ -7,8 +7,8 @@
 // host, takes a free slot and arena space (FPCODE_EBUSY if either is
 // missing: admission by device memory), and writes the slot on a private
 // non-blocking copy stream -- tables, schedule and descriptor first, the
-// zeroed state last, so a running kernel only sees a slot once it is
-// complete.  The kernel (serving mode) keeps claiming tasks of every live
+// zeroed state after them and the task counter that makes it claimable
+// last, so a running kernel only sees a slot once it is complete.  The kernel (serving mode) keeps claiming tasks of every live
 // slot, interleaving old and new codes; when a code certifies, its CTA
 // writes the outcome to the mapped completion record, which poll() reads
 // without any CUDA call.  The kernel exits after a short idle period and
@@ -48,20 +48,28 @@ constexpr int kMaxPassesPerSlot = fpk::kMaxPasses;
 constexpr size_t kServeTableSet = 32 * 1024;      // shared memory per CTA: largest table of one set
 constexpr size_t kServeTableCode = 256 * 1024;    // largest table of one code
 
-// A slot whose code has concluded is reused only after this quiet time.
-// Tasks of later passes may still be running when a code concludes (they
-// ran ahead of its termination test); each stops within 16 of its Gray
-// steps (it reads the finished flag that often) and then counts itself off
-// in the slot's bookkeeping.  Reusing the slot earlier could let such a
-// count or record land in the next code's bookkeeping.
-constexpr auto kSlotQuiet = std::chrono::milliseconds(1);
+// A slot is handed to the next code as soon as its completion is posted.
+// The kernel posts it only once no other claim of the slot is in flight
+// (the per-slot count in `inflight`, see conclude in fp_kernel.cuh): tasks
+// of later passes that ran ahead of the termination test have stopped and
+// counted themselves off by then, so none of them can write into the next
+// code's bookkeeping.  A code whose wait for them gave up reports
+// FPCODE_ETIMEOUT, and its slot stays out of use until the kernel exits.
+//
+// The task counter that makes a slot claimable is written in two steps: a
+// transition value first (the new generation with a task index no schedule
+// reaches, so claims that read it find nothing to do and never wrap into a
+// real index), then the rest of the fresh state, then the counter at task
+// 0, then the slot's flag word.  A claim therefore never sees a claimable
+// counter next to a state that is still being written.
+constexpr uint64_t kTaskTransit = 1ull << 39;
 
 struct Slot {
   bool busy = false;
+  bool held = false;  // its last code's drain timed out: unusable until the kernel has exited
   uint64_t ticket = 0;
   size_t arena_off = 0, arena_bytes = 0;
   std::unique_ptr<fph::Prepared> prep;
-  std::chrono::steady_clock::time_point free_at{};  // not reused before (kSlotQuiet after its completion)
 };
 
 }  // namespace
@@ -77,7 +85,7 @@ struct fpcode_server {
   int smem = 0, ctas = 0, S = 0;
   char *dev = nullptr;
   size_t off_ctl = 0, off_slots = 0, off_passes = 0, off_arena = 0, arena_bytes = 0, off_states = 0,
-         off_dyn = 0, off_aux = 0, off_flags = 0, total = 0;
+         off_dyn = 0, off_aux = 0, off_flags = 0, off_inflight = 0, total = 0;
   fpk::Completion *done_host = nullptr, *done_dev = nullptr;
   char *staging = nullptr;  // pinned, one region per slot
   char *zeros = nullptr;    // pinned, never written: the source that clears a slot's bookkeeping
@@ -129,6 +137,8 @@ int ensure_kernel(fpcode_server *s) {
     if (q == cudaSuccess) s->kernel_live = false;
     else if (q != cudaErrorNotReady) SV_CUDA(q);
   }
+  if (!s->kernel_live)  // no task of any code is in flight: held slots are free again
+    for (auto &sl : s->slots) sl.held = false;
   if (s->kernel_live || s->running == 0) return FPCODE_OK;
   SV_CUDA(cudaStreamWaitEvent(s->kst, s->copies_done, 0));
   SV_CUDA(cudaMemsetAsync(s->dev + s->off_dyn, 0, sizeof(fpk::CtlDyn), s->kst));
@@ -203,13 +213,16 @@ int fpcode_serve_create(const fpcode_serve_opts *opts, void *stream, fpcode_serv
   off = a256(off + S * sizeof(fpk::SlotAux));
   s->off_flags = off;
   off = a256(off + (S + 3) / 4 * 16);
+  s->off_inflight = off;
+  off = a256(off + S * fpk::kInflightStride * sizeof(uint32_t));
   s->total = off;
   SV_CUDA(cudaMalloc(&s->dev, s->total));
   SV_CUDA(cudaHostAlloc(&s->done_host, S * sizeof(fpk::Completion), cudaHostAllocMapped));
   std::memset(s->done_host, 0, S * sizeof(fpk::Completion));
   SV_CUDA(cudaHostGetDevicePointer((void **)&s->done_dev, s->done_host, 0));
   s->stage_per_slot =
-      a256(sizeof(fpk::SlotDesc)) + a256(kMaxPassesPerSlot * sizeof(fpk::PassDesc)) + 256 + kServeTableCode;
+      a256(sizeof(fpk::SlotDesc)) + a256(kMaxPassesPerSlot * sizeof(fpk::PassDesc)) + a256(sizeof(fpk::SlotState) + 32) +
+      kServeTableCode;
   const size_t init_bytes = s->off_arena;  // ctl + descriptors + schedules
   const size_t flag_bytes = (S + 3) / 4 * 16;
   SV_CUDA(cudaMallocHost(&s->staging, std::max(S * s->stage_per_slot,
@@ -226,6 +239,7 @@ int fpcode_serve_create(const fpcode_serve_opts *opts, void *stream, fpcode_serv
   cs.done_host = s->done_dev;
   cs.aux = reinterpret_cast<fpk::SlotAux *>(s->dev + s->off_aux);
   cs.slot_flags = reinterpret_cast<uint32_t *>(s->dev + s->off_flags);
+  cs.inflight = reinterpret_cast<uint32_t *>(s->dev + s->off_inflight);
   cs.nslots = s->S;
   cs.serve = 1;
   std::memcpy(s->staging + s->off_ctl, &cs, sizeof(cs));
@@ -240,6 +254,8 @@ int fpcode_serve_create(const fpcode_serve_opts *opts, void *stream, fpcode_serv
   for (size_t i = 0; i < flag_bytes / 4; ++i) flags[i] = fpk::kSlotFinished;  // no code in any slot
   SV_CUDA(cudaMemcpyAsync(s->dev + s->off_flags, flags, flag_bytes, cudaMemcpyHostToDevice, s->cst));
   SV_CUDA(cudaMemsetAsync(s->dev + s->off_dyn, 0, sizeof(fpk::CtlDyn), s->cst));
+  // in-flight claim counts: zero once, never reset while the server lives
+  SV_CUDA(cudaMemsetAsync(s->dev + s->off_inflight, 0, S * fpk::kInflightStride * sizeof(uint32_t), s->cst));
   SV_CUDA(cudaStreamSynchronize(s->cst));
   s->slots.resize(S);
   s->free_ext.push_back({0, s->arena_bytes});
@@ -273,14 +289,13 @@ int fpcode_serve_submit(fpcode_server *s, const fpcode_desc *code, uint64_t *tic
     return FPCODE_OK;
   }
   int slot = -1;
-  const auto now = std::chrono::steady_clock::now();
   for (int i = 0; i < s->S; ++i)
-    if (!s->slots[i].busy && now >= s->slots[i].free_at) {
+    if (!s->slots[i].busy && !s->slots[i].held) {
       slot = i;
       break;
     }
   if (slot < 0) {
-    fph::set_error("serve: no free slot (or none quiet yet)");
+    fph::set_error("serve: no free slot");
     return FPCODE_EBUSY;
   }
   size_t aoff = 0;
@@ -293,7 +308,7 @@ int fpcode_serve_submit(fpcode_server *s, const fpcode_desc *code, uint64_t *tic
   char *stg = s->staging + (size_t)slot * s->stage_per_slot;
   const size_t o_pass = a256(sizeof(fpk::SlotDesc));
   const size_t o_state = o_pass + a256(kMaxPassesPerSlot * sizeof(fpk::PassDesc));
-  const size_t o_tab = o_state + 256;
+  const size_t o_tab = o_state + a256(sizeof(fpk::SlotState) + 32);
   char *d_desc = s->dev + s->off_slots + (size_t)slot * sizeof(fpk::SlotDesc);
   char *d_pass = s->dev + s->off_passes + (size_t)slot * kMaxPassesPerSlot * sizeof(fpk::PassDesc);
   char *d_tab = s->dev + s->off_arena + aoff;
@@ -322,21 +337,30 @@ int fpcode_serve_submit(fpcode_server *s, const fpcode_desc *code, uint64_t *tic
   SV_CUDA(cudaMemcpyAsync(d_pass, stg + o_pass, P->passes.size() * sizeof(fpk::PassDesc), cudaMemcpyHostToDevice,
                           s->cst));
   SV_CUDA(cudaMemcpyAsync(d_desc, stg, sizeof(sd), cudaMemcpyHostToDevice, s->cst));
-  // per-pass minima and counts, before the state.  Admissions use copies
-  // only: a memset is a kernel, and it could not start while the serving
-  // kernel holds every SM.
+  // the task counter at the transition value: claims that read it find no
+  // task (and do not touch the slot's bookkeeping)
+  char *d_state = s->dev + s->off_states + (size_t)slot * sizeof(fpk::SlotState);
+  fpk::SlotState fresh{};
+  fresh.word = ((unsigned long long)(tk & fpk::kGenMask) << fpk::kGenShift) | kTaskTransit;
+  std::memcpy(stg + o_state, &fresh, sizeof(fresh));
+  SV_CUDA(cudaMemcpyAsync(d_state, stg + o_state, sizeof(fresh.word), cudaMemcpyHostToDevice, s->cst));
+  // per-pass minima and counts, and the rest of the state.  Admissions use
+  // copies only: a memset is a kernel, and it could not start while the
+  // serving kernel holds every SM.
   SV_CUDA(cudaMemcpyAsync(s->dev + s->off_aux + (size_t)slot * sizeof(fpk::SlotAux), s->zeros,
                           sizeof(fpk::SlotAux), cudaMemcpyHostToDevice, s->cst));
-  fpk::SlotState fresh{};
-  fresh.word = (unsigned long long)(tk & fpk::kGenMask) << fpk::kGenShift;
-  std::memcpy(stg + o_state, &fresh, sizeof(fresh));
-  SV_CUDA(cudaMemcpyAsync(s->dev + s->off_states + (size_t)slot * sizeof(fpk::SlotState), stg + o_state,
-                          sizeof(fpk::SlotState), cudaMemcpyHostToDevice, s->cst));
-  // the flag word last: until it changes, claims skip the slot
-  const uint32_t flag = fpk::slot_flag_gen(tk & fpk::kGenMask);
-  std::memcpy(stg + o_state + sizeof(fpk::SlotState), &flag, sizeof(flag));
-  SV_CUDA(cudaMemcpyAsync(s->dev + s->off_flags + (size_t)slot * 4, stg + o_state + sizeof(fpk::SlotState),
-                          sizeof(flag), cudaMemcpyHostToDevice, s->cst));
+  constexpr size_t kRest = offsetof(fpk::SlotState, best_key);  // the lines after the counter's
+  SV_CUDA(cudaMemcpyAsync(d_state + kRest, stg + o_state + kRest, sizeof(fpk::SlotState) - kRest,
+                          cudaMemcpyHostToDevice, s->cst));
+  // then the counter at task 0: the code is claimable from here on
+  unsigned long long *w0 = reinterpret_cast<unsigned long long *>(stg + o_state + sizeof(fpk::SlotState));
+  *w0 = (unsigned long long)(tk & fpk::kGenMask) << fpk::kGenShift;
+  SV_CUDA(cudaMemcpyAsync(d_state, w0, sizeof(*w0), cudaMemcpyHostToDevice, s->cst));
+  // the flag word last: until it changes, slot scans skip the slot
+  uint32_t *flag = reinterpret_cast<uint32_t *>(stg + o_state + sizeof(fpk::SlotState) + 8);
+  *flag = fpk::slot_flag_gen(tk & fpk::kGenMask);
+  SV_CUDA(cudaMemcpyAsync(s->dev + s->off_flags + (size_t)slot * 4, flag, sizeof(*flag), cudaMemcpyHostToDevice,
+                          s->cst));
   SV_CUDA(cudaEventRecord(s->copies_done, s->cst));
   Slot &sl = s->slots[slot];
   sl.busy = true;
@@ -373,9 +397,10 @@ int fpcode_serve_poll(fpcode_server *s, fpcode_result *out, uint64_t *tickets, u
     oc.stop_pass = c->stop_pass;
     fph::decode_result(*sl.prep, oc, &out[n], witnesses ? witnesses + (size_t)n * FPCODE_MAX_N : nullptr);
     tickets[n++] = sl.ticket;
+    // posted after the slot's claims drained: its tables are no longer read
     arena_free(s, sl.arena_off, sl.arena_bytes);
     sl.busy = false;
-    sl.free_at = std::chrono::steady_clock::now() + kSlotQuiet;
+    sl.held = oc.status == FPCODE_ETIMEOUT;
     sl.prep.reset();
     --s->running;
   }

@@ -147,7 +147,7 @@ struct alignas(128) SlotState {
   unsigned long long word;        // (generation << 48) | next task of the whole schedule
   unsigned long long pad_w[15];
   unsigned long long best_key;    // inverted packed witness key (0: none yet)
-  int32_t finished;               // 1: nothing left to do
+  int32_t finished;               // 0 while running; fin_tag(generation) once nothing is left to do
   int32_t pad_k[29];
   unsigned long long enumerated;  // codewords evaluated, passes past the stop included
   unsigned long long entered;     // codewords evaluated in the passes up to stop_pass
@@ -186,5 +186,16 @@ constexpr int32_t kRunning = -1;
 constexpr uint64_t kTaskMask = (1ull << 40) - 1;
 constexpr int kGenShift = 48;
 constexpr uint64_t kGenMask = 0xFFFFull;
+
+// SlotState.finished of a concluded code: its generation in the high half,
+// so that a claim of the next code in the slot never reads a predecessor's
+// flag as its own (one-shot launches: generation 0, the value 1).
+FPK_HD int32_t fin_tag(uint64_t gen) { return (int32_t)(((gen & kGenMask) << 16) | 1u); }
+
+// Serving: per-slot count of claims in flight, on its own 32-byte sector.
+// It is never reset while the server lives: every claim adds one before it
+// reads the finished flag and takes it back after its last write, so the
+// count stays balanced across the codes that follow one another in a slot.
+constexpr int kInflightStride = 8;  // u32 words per slot
 
 }  // namespace fpk

@@ -70,6 +70,42 @@ def test_serve_alone_equals_mix():
     B.fpcode_serve_destroy(srv)
 
 
+def test_serve_slot_reuse_back_to_back():
+    """One slot, codes submitted one after another with no pause: each code
+    goes into the slot the moment its predecessor's result is posted.  A
+    search's later passes are taken ahead of its termination tests (F_7
+    [40,20] certifies after the g = 5 passes while CTAs already run tasks of
+    its 3 * 10^8-codeword g = 6 passes), so the slot is handed over while
+    those tasks are being dropped.  With mid-pass exit off every count is
+    deterministic: a single count-off or record of the previous code landing
+    in the next one's bookkeeping would change its per-pass codewords,
+    counts or bound.  Each result equals the code's search alone, field by
+    field, on a sequence that alternates long and short searches."""
+    search = B.fpcode_opts_default(mid_pass_exit=0)
+    srv = B.fpcode_serve_create(B.fpcode_serve_opts_default(slots=1, search=search))
+    small, _ = inputs.serve_codes(count=6)
+    big = [inputs.single("f7_n40_k20"), inputs.single("f3_n80_k40")]
+    seq = [big[0], small[0], big[0], big[1], small[1], big[0], small[2], big[1], big[0], small[3], small[4], big[0]]
+    budget = 10 ** 7
+    got = []
+    for c in seq:
+        b = 0 if any(c is x for x in big) else budget
+        t = B.fpcode_serve_submit(srv, c, budget=b)
+        assert t is not None  # the only slot was handed back with the previous result
+        t0 = time.time()
+        out = []
+        while not out and time.time() - t0 < 60:
+            out = B.fpcode_serve_poll(srv)
+        assert len(out) == 1 and out[0][0] == t
+        got.append((c, b, out[0][1]))
+    B.fpcode_serve_destroy(srv)
+    for c, b, r in got:
+        pr = B.fpcode_prepare(c.p, c.n, c.k, c.G, B.fpcode_opts_default(budget=b, mid_pass_exit=0))
+        ref = B.fpcode_min_distance_ex(pr)
+        _check(c, r, ref)
+        assert r.enumerated == ref.enumerated == sum(ref.counts)
+
+
 def test_serve_admission_by_memory():
     """With room for about one code's tables, later requests wait (EBUSY)
     and are admitted once earlier codes finish."""
