@@ -82,7 +82,17 @@ typedef struct fpcode_opts {
   double wait_limit_s; /* bound on one device wait at a pass hand-off
                           (default 10 s); past it the kernel exits with
                           FPCODE_ETIMEOUT instead of spinning */
-  int reserved[4];
+  int pair_leaves;     /* 1 (default): a single code with p = 3 or 7 whose
+                          pair table fits (40 KiB per information set)
+                          enumerates each codeword of a pass g >= 2 as a
+                          stem of g - 2 rows held exactly plus a pair of
+                          rows (y, x) from a table of A[y] + c A[x], and
+                          bounds S + B and S - B with one popcount (the
+                          isometric last addition of Sec. 4.3 carried to
+                          the last two rows); 0: one-row leaves.  Batches
+                          and servers use one-row leaves.  d, L, U and the
+                          per-level counts do not depend on it. */
+  int reserved[3];
 } fpcode_opts;
 
 typedef struct fpcode_result {
@@ -160,7 +170,8 @@ typedef struct fpcode_checkpoint {
   int p, n, k;
   int passes_done;     /* passes 0 .. passes_done - 1 of the schedule are complete */
   uint64_t best_key;   /* packed key of the best codeword found (all ones: none) */
-  uint64_t code_hash;  /* FNV-1a of (p, n, k, per_round_check, defer) and G */
+  uint64_t code_hash;  /* FNV-1a of (p, n, k, per_round_check, defer, pair
+                          leaves taken) and G: the schedule and key layout */
 } fpcode_checkpoint;
 
 /* After fpcode_search_finish returned FPCODE_EBUDGET: the checkpoint of that

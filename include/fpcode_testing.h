@@ -63,7 +63,7 @@ int fpcode_prepared_passes(const fpcode_prepared *prep, fpcode_pass_info *passes
  * signature words.  Returns the number of signature words (0: none), or a
  * negative status. */
 int fpcode_test_prepared_row(const fpcode_prepared *prep, int j, int t, int v, uint32_t *slices, uint32_t *sig);
-/* The CTA task ranges [lo, hi), in prefixes, of pass `pass` when planned
+/* The CTA task ranges [lo, hi), in prefixes (pair-leaf passes: stems), of pass `pass` when planned
  * for `ctas` CTAs (fixed_pl > 0: fixed tasks of 256 * fixed_pl prefixes; 0:
  * guided, with fixed tasks of at least min_steps prefixes per lane for a pass
  * too small to give every lane of the grid that many; with min_steps <= 8,
@@ -71,6 +71,23 @@ int fpcode_test_prepared_row(const fpcode_prepared *prep, int j, int t, int v, u
  * unit per lane).  Returns the number of tasks (at most max written). */
 int fpcode_test_task_ranges(fpcode_prepared *prep, int pass, int ctas, int fixed_pl, int min_steps, uint64_t *lo,
                             uint64_t *hi, int max);
+/* Pair leaves (fpcode_opts.pair_leaves): words per pair-table entry of the
+ * prepared code (0: one-row leaves).  With `pass` >= 0 and a stem J of that
+ * pass, *entries receives the pair entries the stem is evaluated against,
+ * (p-1) C(k-1-q, 2) with q the stem's largest row (g = 2: all pairs).
+ * Returns the words per entry, or a negative status. */
+int fpcode_test_pair_mode(const fpcode_prepared *prep, int pass, uint64_t J, uint32_t *entries);
+/* Stored pair-table entry e of Gamma_j (pair leaves): its pair_sigp words
+ * (the signature words of B = A_j[y] + c A_j[x], word w's r - 1 words at
+ * [w * (r - 1)], then zeros), followed by slice 0 of B (W words).  `sig`
+ * holds up to 12 words.  Returns the number of words, or a negative
+ * status. */
+int fpcode_test_pair_entry(const fpcode_prepared *prep, int j, uint32_t e, uint32_t *sig);
+/* Coefficients (k ints, 0 for rows outside the codeword) of the codeword of
+ * Gamma_j that packed key `key` stands for, as the witness is rebuilt; *g
+ * and *j receive its level and information set.  Returns 0, or -1 if the
+ * key names no codeword of the schedule. */
+int fpcode_test_key_coefficients(const fpcode_prepared *prep, uint64_t key, int *g, int *j, int *coef);
 /* Microseconds from the start of the last search on `prep` to the end of
  * each of its passes (-1: not reached), for up to max passes.  Returns the
  * number of passes written, or -1. */

@@ -38,7 +38,8 @@ class fpcode_opts(ctypes.Structure):
         ("budget", ctypes.c_uint64),
         ("timeout_s", ctypes.c_double),
         ("wait_limit_s", ctypes.c_double),
-        ("reserved", ctypes.c_int * 4),
+        ("pair_leaves", ctypes.c_int),
+        ("reserved", ctypes.c_int * 3),
     ]
 
 
@@ -172,6 +173,9 @@ def _declare(lib):
                                                   ctypes.POINTER(ctypes.c_double)]),
         "fpcode_search_resume": (ctypes.c_int, [_VP, ctypes.POINTER(fpcode_checkpoint), _VP,
                                                 ctypes.POINTER(fpcode_opts)]),
+        "fpcode_test_pair_mode": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint32)]),
+        "fpcode_test_key_coefficients": (ctypes.c_int, [_VP, ctypes.c_uint64, _IP, _IP, _IP]),
+        "fpcode_test_pair_entry": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]),
     }
     found = []
     for name, (res, args) in sig.items():
@@ -602,6 +606,37 @@ def fpcode_test_task_ranges(prep: Prepared, pass_index: int, ctas: int, fixed_pl
     if n < 0:
         raise FpcodeError(EINVAL, "fpcode_test_task_ranges")
     return [(int(lo[i]), int(hi[i])) for i in range(min(n, cap))]
+
+
+def fpcode_test_pair_mode(prep: Prepared, pass_index: int = -1, J: int = 0):
+    """Words per pair-table entry (0: one-row leaves); with a pass and a
+    stem J of it, also the number of pair entries the stem is evaluated
+    against."""
+    e = ctypes.c_uint32(0)
+    w = lib().fpcode_test_pair_mode(prep.handle, int(pass_index), int(J), ctypes.byref(e))
+    if w < 0:
+        raise FpcodeError(-w, "fpcode_test_pair_mode")
+    return w if pass_index < 0 else (w, int(e.value))
+
+
+def fpcode_test_pair_entry(prep: Prepared, j: int, e: int) -> list[int]:
+    """The stored words of pair-table entry e of information set j: its
+    signature (pair_sigp words), then slice 0 of B (W words)."""
+    sig = (ctypes.c_uint32 * 16)()
+    n = lib().fpcode_test_pair_entry(prep.handle, int(j), int(e), sig)
+    if n < 0:
+        raise FpcodeError(-n, "fpcode_test_pair_entry")
+    return [int(sig[i]) for i in range(n)]
+
+
+def fpcode_test_key_coefficients(prep: Prepared, key: int):
+    """(g, j, coefficients) of the codeword a packed key stands for, or None."""
+    g = ctypes.c_int(0)
+    j = ctypes.c_int(0)
+    coef = (ctypes.c_int * prep.k)()
+    if lib().fpcode_test_key_coefficients(prep.handle, ctypes.c_uint64(key), ctypes.byref(g), ctypes.byref(j), coef):
+        return None
+    return g.value, j.value, [int(x) for x in coef]
 
 
 def fpcode_test_pass_times(prep: Prepared, stream=None) -> list[float]:

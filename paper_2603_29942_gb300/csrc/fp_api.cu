@@ -99,7 +99,11 @@ const void *kernel_for(int variant) {
 
 // CTAs per SM for a kernel with `smem` bytes of dynamic shared memory.
 int occupancy(const void *fn, int smem, int override_per_sm, int *per_sm) {
-  if (smem > 48 * 1024) FP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  cudaFuncAttributes fa{};
+  FP_CUDA(cudaFuncGetAttributes(&fa, fn));
+  // dynamic and static shared memory together past 48 KiB need the opt-in
+  if ((size_t)smem + fa.sharedSizeBytes > 48 * 1024)
+    FP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   int n = 0;
   FP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, fpk::kThreads, (size_t)smem));
   if (n < 1) {
@@ -153,9 +157,9 @@ Layout make_layout(const std::vector<const fph::Prepared *> &codes) {
   L.off_slots = o;
   o = align256(o + ns * sizeof(SlotDesc));
   L.off_passes = o;
-  for (auto *P : codes) {
+  for (auto *P : codes) {  // each code's passes, then its pair-leaf segments (read as passes + npasses)
     L.pass_off.push_back(o);
-    o = align256(o + P->passes.size() * sizeof(PassDesc));
+    o = align256(o + P->passes.size() * sizeof(PassDesc) + P->segs.size() * sizeof(fpk::PairSeg));
   }
   L.off_tables = o;
   for (auto *P : codes) {
@@ -199,10 +203,15 @@ void fill_static(const Layout &L, const std::vector<const fph::Prepared *> &code
     sd.mid_pass_exit = P.opts.mid_pass_exit;
     sd.complete = P.complete;
     sd.seed_u = P.seed_u;
+    sd.pair_sigp = P.pair ? P.pair_sigp : 0;
+    sd.pair_quick_max = P.pair_quick_max;
     sd.table = reinterpret_cast<const uint32_t *>(d + L.table_off[i]);
     sd.passes = reinterpret_cast<const PassDesc *>(d + L.pass_off[i]);
     std::memcpy(h + L.off_slots + i * sizeof(SlotDesc), &sd, sizeof(sd));
     std::memcpy(h + L.pass_off[i], P.passes.data(), P.passes.size() * sizeof(PassDesc));
+    if (!P.segs.empty())
+      std::memcpy(h + L.pass_off[i] + P.passes.size() * sizeof(PassDesc), P.segs.data(),
+                  P.segs.size() * sizeof(fpk::PairSeg));
     std::memcpy(h + L.table_off[i], P.table.data(), P.table.size() * sizeof(uint32_t));
   }
 }
@@ -241,12 +250,12 @@ int smem_for(const std::vector<const fph::Prepared *> &codes) {
   return (int)(((s + 15) & ~(size_t)15) + fpk::kBinomBytes);
 }
 
-// Upload one prepared code into device buffer `d` (static_bytes) via pinned
-// staging `h`; plan its tasks for the kernel's grid.
 // with_state: the host image also holds the first state (zeroed
 // bookkeeping, the bound in the best key) and one copy takes both, so the
 // next search needs no reset of its own.
-int upload_one(fpcode_prepared *prep, cudaStream_t st, DevCtx &c, char *d, char *h, bool with_state = false) {
+// Grid and task plan of one code (before its layout: the plan's pair-leaf
+// segments are part of the static image).
+int plan_one(fpcode_prepared *prep, const DevCtx &c) {
   fph::Prepared &P = prep->host;
   const void *fn = kernel_for(P.variant);
   if (!fn) {
@@ -259,6 +268,13 @@ int upload_one(fpcode_prepared *prep, cudaStream_t st, DevCtx &c, char *d, char 
   if (s) return s;
   prep->ctas = c.sms * per_sm;
   fph::plan_tasks(&P, prep->ctas, P.opts.prefixes_per_lane, fph::kMinStepsSingle, true);
+  return FPCODE_OK;
+}
+
+// Upload one planned code (plan_one) into device buffer `d` via pinned
+// staging `h`.
+int upload_one(fpcode_prepared *prep, cudaStream_t st, DevCtx &c, char *d, char *h, bool with_state = false) {
+  fph::Prepared &P = prep->host;
   Layout L = make_layout({&P});
   prep->off_ctl = L.off_ctl;
   prep->off_slot = L.off_slots;
@@ -377,6 +393,7 @@ void fpcode_opts_default(fpcode_opts *o) {
   o->mid_pass_exit = 1;
   o->lookahead = 1;
   o->wait_limit_s = 10.0;
+  o->pair_leaves = 1;
 }
 
 const char *fpcode_last_error(void) { return fph::last_error(); }
@@ -442,6 +459,8 @@ int fpcode_prepared_upload(fpcode_prepared *prep, void *stream) {
   s = ensure_events(prep);
   if (s) return s;
   FP_CUDA(cudaGetDevice(&prep->device));
+  s = plan_one(prep, *c);
+  if (s) return s;
   Layout L = make_layout({&prep->host});
   FP_CUDA(cudaMalloc(&prep->dev, L.total));
   prep->stage_off = align256(std::max(L.static_bytes, L.dyn_bytes));
@@ -534,6 +553,8 @@ int fpcode_min_distance(int p, int n, int k, const uint8_t *G, void *stream, int
   s = get_ctx(&c);
   if (s) return s;
   std::lock_guard<std::mutex> lk(c->ws_mu);
+  s = plan_one(&prep, *c);
+  if (s) return s;
   Layout L = make_layout({&prep.host});
   // pinned: [static image and first state][read-back][staging], so nothing
   // waits between the upload and the launch
@@ -587,6 +608,7 @@ int fpcode_min_distance_batch(int num, const fpcode_desc *codes, void *stream, c
         if (i >= num) break;
         preps[i].reset(new fph::Prepared());
         fpcode_opts oi = o;
+        oi.pair_leaves = 0;  // the batched kernels take one-row leaves
         if (codes[i].budget) oi.budget = codes[i].budget;
         status[i] = fph::prepare(codes[i].p, codes[i].n, codes[i].k, codes[i].G, oi, preps[i].get());
       }

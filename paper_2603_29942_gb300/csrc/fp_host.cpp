@@ -4,6 +4,7 @@
 // Brouwer-Zimmermann search (Sec. 3.1, Alg. 6) and the exact rebuild of a
 // witness codeword from its packed key.  Plain C++17, no CUDA.
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <cstring>
 #include <string>
@@ -198,7 +199,24 @@ int prepare(int p, int n, int k, const uint8_t *G, const fpcode_opts &opts, Prep
   P->n = n;
   P->k = k;
   P->opts = opts;
-  {  // identity of the code and of the options that shape its schedule
+  P->r = fpbs::bits_for(p);
+  P->W = std::max(1, ceil_div(n - k, 32));
+  P->rwpad = (P->r * P->W + 3) & ~3;
+  P->variant = fpk::variant_id(p, P->r, P->W);
+  // pair leaves: p = 3, 7 (pair signatures of the natural encoding), a
+  // stem below the pair (k >= 3), and a pair table that fits
+  P->pair = false;
+  P->pair_sigp = 0;
+  if (opts.pair_leaves && (p == 3 || p == 7) && k >= 3) {
+    const int sigw = P->W * (P->r - 1);
+    P->pair = true;
+    P->pair_sigp = sigw <= 1 ? 1 : sigw <= 2 ? 2 : sigw <= 4 ? 4 : 8;
+    if (P->pair_words_per_set() * 4 > kPairTableMaxBytes) {
+      P->pair = false;
+      P->pair_sigp = 0;
+    }
+  }
+  {  // identity of the code and of the options that shape its schedule and keys
     uint64_t h = 1469598103934665603ull;
     auto mix = [&h](uint64_t v) {
       for (int b = 0; b < 8; ++b) {
@@ -211,16 +229,13 @@ int prepare(int p, int n, int k, const uint8_t *G, const fpcode_opts &opts, Prep
     mix((uint64_t)k);
     mix((uint64_t)opts.per_round_check);
     mix((uint64_t)opts.defer);
+    mix((uint64_t)(P->pair ? 1 : 0));
     for (size_t i = 0; i < (size_t)k * n; ++i) {
       h ^= G[i];
       h *= 1099511628211ull;
     }
     P->code_hash = h;
   }
-  P->r = fpbs::bits_for(p);
-  P->W = std::max(1, ceil_div(n - k, 32));
-  P->rwpad = (P->r * P->W + 3) & ~3;
-  P->variant = fpk::variant_id(p, P->r, P->W);
   if (P->table_bytes_per_set() > 96 * 1024) {
     set_error("bit-sliced multiples of one information set exceed 96 KiB (k (p-1) r W too large)");
     return FPCODE_EINVAL;
@@ -274,8 +289,8 @@ int prepare(int p, int n, int k, const uint8_t *G, const fpcode_opts &opts, Prep
   // --- bit-sliced multiples v * A_j[t] of the non-pivot part, then the
   //     pair signatures (Mersenne p) ---
   const int m = P->m, nk = n - k, R = P->r, RWP = P->rwpad, W = P->W;
-  const int SIG = fpk::sig_words(p, R, W);
-  const size_t set_words = (size_t)k * ((size_t)(p - 1) * RWP + SIG);
+  const int SIG = P->pair ? 0 : fpk::sig_words(p, R, W);
+  const size_t set_words = P->table_words_per_set();
   P->table.assign((size_t)m * set_words, 0u);
   const int nk32 = W * 32;  // values padded with zeros to whole words
   std::vector<uint8_t> a(nk32, 0);
@@ -319,6 +334,46 @@ int prepare(int p, int n, int k, const uint8_t *G, const fpcode_opts &opts, Prep
       }
     }
 
+  // Pair table of each set (pair leaves): for y from k - 2 down to 0, x
+  // from y + 1 up, c from 1 to p - 1: the pair signature words
+  // B_i xor B_{i+1} of B = A[y] + c A[x] (exact bit-sliced add), word w's
+  // r - 1 words at [w * (r - 1)], padded to pair_sigp words.
+  if (P->pair) {
+    const int b = p - 1, SP = P->pair_sigp;
+    const size_t NE = P->pair_entries();
+    std::vector<uint32_t> Bv((size_t)R * W);
+    for (int j = 0; j < m; ++j) {
+      const uint32_t *rows = &P->table[(size_t)j * set_words];
+      uint32_t *pt = &P->table[(size_t)j * set_words + (size_t)k * b * RWP];
+      uint32_t *p0 = pt + ((NE * (size_t)SP + 3) & ~(size_t)3);  // slice 0 of each entry
+      size_t e = 0;
+      for (int y = k - 2; y >= 0; --y)
+        for (int x = y + 1; x < k; ++x)
+          for (int c = 1; c <= b; ++c, ++e) {
+            add_sliced_words(R, rows + (size_t)y * b * RWP, rows + ((size_t)x * b + (c - 1)) * RWP, Bv.data(), W, p);
+            for (int w = 0; w < W; ++w) {
+              for (int i = 0; i + 1 < R; ++i) pt[e * SP + (size_t)w * (R - 1) + i] = Bv[w * R + i] ^ Bv[w * R + i + 1];
+              p0[e * W + w] = Bv[w * R];
+            }
+          }
+    }
+    // The one-popcount bound ORs the words of a pair mask before counting,
+    // so a bit of it covers one position per word.  A position is set in a
+    // pair mask with chance rho (p = 3: 4/9, p = 7: 36/49, for random
+    // symbols); take the one-popcount bound only for thresholds 3.5
+    // standard deviations under its mean, where a warp's vote rarely fires.
+    const double rho = p == 3 ? 4.0 / 9.0 : 36.0 / 49.0;
+    double mean = 0, var = 0;
+    for (int bit = 0; bit < 32; ++bit) {
+      int cnt = 0;
+      for (int w = 0; w < W; ++w) cnt += 32 * w + bit < nk;
+      const double q = 1.0 - std::pow(1.0 - rho, cnt);
+      mean += q;
+      var += q * (1.0 - q);
+    }
+    P->pair_quick_max = W > 1 ? std::max(0, (int)std::floor(mean - 3.5 * std::sqrt(var) + 0.5)) : 255;
+  }
+
   // --- pass schedule ---
   P->passes.clear();
   std::vector<int> e(m, 0);
@@ -335,7 +390,16 @@ int prepare(int p, int n, int k, const uint8_t *G, const fpcode_opts &opts, Prep
         const uint64_t size = pass_size(p, k, h);
         uint64_t nprefix = (uint64_t)k;
         uint64_t NC = 1;
-        if (h >= 2) {
+        uint64_t limit = fpk::kMaxPrefix;
+        if (h >= 2 && P->pair) {
+          // stems: one (the empty stem) for g = 2; else (p-1)/2 * C(k-2, g-2) (p-1)^(g-3)
+          limit = fpk::kMaxPrefix >> 1;  // the stem index fits 33 bits of the key
+          nprefix = 1;
+          if (h >= 3) {
+            for (int i = 0; i < h - 3; ++i) NC = sat_mul(NC, (uint64_t)(p - 1));
+            nprefix = sat_mul(sat_mul(binom().c[k - 2][h - 2], NC), (uint64_t)((p - 1) / 2));
+          }
+        } else if (h >= 2) {
           for (int i = 0; i < h - 2; ++i) NC = sat_mul(NC, (uint64_t)(p - 1));
           nprefix = sat_mul(binom().c[k - 1][h - 1], NC);
         }
@@ -344,7 +408,7 @@ int prepare(int p, int n, int k, const uint8_t *G, const fpcode_opts &opts, Prep
         // if the search gets there): prefix indices must fit the key, the
         // coefficient counter 64 bits, the binomials of an unrank the staged
         // columns t < kBinomCols, the pass index 8 bits
-        if (over_budget || size == ~0ull || nprefix >= fpk::kMaxPrefix || h > gmax_digits ||
+        if (over_budget || size == ~0ull || nprefix >= limit || h > gmax_digits ||
             h > fpenum::kBinomCols || (int)P->passes.size() >= fpk::kMaxPasses) {
           truncated = true;
           break;
@@ -389,17 +453,121 @@ int prepare(int p, int n, int k, const uint8_t *G, const fpcode_opts &opts, Prep
   return FPCODE_OK;
 }
 
+namespace {
+
+// Task plan of pair-leaf pass d (g >= 2) for a grid of C CTAs, appended to
+// P->segs.  Stems come in blocks (h, q) -- h outer, q = the stem's largest
+// row ascending -- whose stems all have E(q) = (p-1) C(k-1-q, 2) entries.
+// A lane's work for one stem is its share of the entries plus the stem
+// step.  Tasks are guided by work: a block's tasks aim at a per-lane load
+// of half the pass's remaining work spread over every lane of the grid
+// (at least kMinTaskLane).  A stem whose entries alone exceed that target,
+// or a block with too few stems to give every group one, splits its
+// entries over 2^lsplit lanes (interleaved entry chunks, so a warp's loads
+// stay broadcasts or consecutive words).  Each block is a segment of its
+// own, so the groups of a task have equal work.
+constexpr uint64_t kStemCost = 8;      // a stem step, in entry evaluations
+constexpr uint64_t kMinTaskLane = 96;  // least per-lane work of a task, in entry evaluations
+constexpr uint64_t kSpreadLane = 64;   // a pass of at most this much work per lane of the grid is spread wide
+
+void plan_pair_pass(Prepared *P, fpk::PassDesc &d, uint64_t C) {
+  const int k = P->k, b = P->p - 1, g = d.g;
+  const int H = g == 2 ? 1 : b / 2;
+  const uint64_t lanes = (uint64_t)fpk::kThreads;
+  struct Blk {
+    int h, q;
+    uint64_t n;  // stems
+    uint64_t E;  // entries per stem
+  };
+  std::vector<Blk> blks;
+  if (g == 2) {
+    blks.push_back({1, -1, 1, (uint64_t)fpk::pair_entries_above(k, -1, b)});
+  } else {
+    for (int h = 1; h <= H; ++h)
+      for (int q = g - 3; q <= k - 3; ++q)
+        blks.push_back({h, q, binom().c[q][g - 3] * d.NC, (uint64_t)fpk::pair_entries_above(k, q, b)});
+  }
+  long double rem = 0;
+  for (auto &x : blks) rem += (long double)x.n * (long double)(x.E + kStemCost);
+  // A small pass (the first passes of a search, which run before records
+  // exist and send most entries down the exact path) is spread as wide as
+  // the grid allows: one stem per group, a stem's entries over as many
+  // lanes as keeps two loads per lane.
+  const bool spread = rem <= (long double)(C * lanes * kSpreadLane);
+  const uint64_t T_spread = std::max<uint64_t>(2, (uint64_t)(rem / (long double)(C * lanes)) + 1);
+  // Stems of one group start on the same phase of the coefficient counter
+  // (units of (p-1)^t stems, t <= g - 3), so the lanes of a warp take the
+  // same Gray steps and rebuild their sums at the same stem.
+  const int L = g >= 3 ? g - 3 : 0;
+  d.seg_off = (uint32_t)P->segs.size();
+  uint32_t tasks = 0;
+  int cur_l = -1, cur_spg = -1;  // shape of the open segment
+  uint64_t cur_n = 0;            // its stems so far
+  auto close = [&]() {
+    if (cur_l < 0) return;
+    const uint64_t per = (lanes >> cur_l) * (uint64_t)cur_spg;
+    tasks += (uint32_t)((cur_n + per - 1) / per);
+    P->segs.back().task_end = tasks;
+  };
+  for (auto &x : blks) {
+    const uint64_t T =
+        spread ? T_spread : std::max<uint64_t>(kMinTaskLane, (uint64_t)(rem / (long double)(2 * C * lanes)));
+    int l = 0;
+    // split a stem's entries while one lane's share exceeds the target, or
+    // while the block cannot give every group a stem (at least two entry
+    // pairs per lane per stem)
+    while (l < 8 && x.E >> (l + 1) >= 4 &&
+           (((x.E + (1ull << l) - 1) >> l) + kStemCost > T || (lanes >> l) > x.n))
+      ++l;
+    const uint64_t per_stem = ((x.E + (1ull << l) - 1) >> l) + kStemCost;
+    uint64_t want = spread ? 1 : std::max<uint64_t>(1, (T + per_stem / 2) / per_stem);
+    uint64_t unit = 1;
+    for (int t = 0; t < L && unit * (uint64_t)b <= want; ++t) unit *= (uint64_t)b;
+    want = std::min<uint64_t>(65535 / unit * unit, want / unit * unit);
+    const int spg = (int)want;
+    {  // one segment per block: every stem of a task has the same entries, so its groups finish together
+      close();
+      fpk::PairSeg s{};
+      s.task_end = 0;
+      s.spg = (uint16_t)spg;
+      s.q = x.q < 0 ? (uint8_t)255 : (uint8_t)x.q;
+      s.hsplit = (uint8_t)(((x.h - 1) << 4) | l);
+      P->segs.push_back(s);
+      cur_l = l;
+      cur_spg = spg;
+      cur_n = 0;
+    }
+    cur_n += x.n;
+    rem -= (long double)x.n * (long double)(x.E + kStemCost);
+  }
+  close();
+  d.nseg = (uint32_t)P->segs.size() - d.seg_off;
+  d.ntasks = tasks;
+  d.pl = 0;
+  d.phases = 0;
+  d.unit = 1;
+}
+
+}  // namespace
+
 void plan_tasks(Prepared *P, int ctas, int fixed_pl, int min_steps, bool spread_tiny) {
   const uint64_t lanes = (uint64_t)fpk::kThreads;
   const uint64_t C = (uint64_t)std::max(1, ctas);
   const uint64_t b = (uint64_t)(P->p - 1);
+  P->segs.clear();
   for (auto &d : P->passes) {
     d.phases = 0;
     d.plan_ctas = (uint32_t)C;
     d.unit = 1;
+    d.seg_off = 0;
+    d.nseg = 0;
     if (d.g == 1) {
       d.pl = 1;
       d.ntasks = 1;
+      continue;
+    }
+    if (P->pair) {
+      plan_pair_pass(P, d, C);
       continue;
     }
     if (fixed_pl > 0) {
@@ -452,14 +620,47 @@ void plan_tasks(Prepared *P, int ctas, int fixed_pl, int min_steps, bool spread_
   }
 }
 
-namespace {
-
 // Coefficients (length k) of the codeword a key stands for.
 bool key_coefficients(const Prepared &P, uint64_t key, int *g_out, int *j_out, std::vector<int> &coef) {
   const int pass = (int)fpk::key_pass(key);
   if (pass >= (int)P.passes.size()) return false;
   const fpk::PassDesc &d = P.passes[pass];
   coef.assign(P.k, 0);
+  if (P.pair && d.g >= 2) {
+    // stem J: h and the prefix over rows 0..k-2 at level g - 1; entry e:
+    // (y, x, c); sign 1: the codeword S - B, i.e. y and x negated
+    const int b = P.p - 1, g = d.g;
+    const uint64_t J = fpk::pair_key_stem(key);
+    const uint32_t e = fpk::pair_key_entry(key);
+    const int sign = (int)fpk::pair_key_sign(key);
+    if (J >= d.nprefix || e >= (uint32_t)b * (uint32_t)(P.k * (P.k - 1) / 2) || (g == 2 && sign)) return false;
+    int y, x, c;
+    fpk::pair_entry_rows(P.k, b, e, &y, &x, &c);
+    int q = -1;
+    if (g >= 3) {
+      const int L = g - 3;
+      const uint64_t N1 = binom().c[P.k - 2][g - 2] * d.NC;
+      const int h = (int)(J / N1) + 1;
+      const uint64_t I1 = J % N1;
+      const int DB = digit_bits(P.p);
+      fpenum::Prefix pf = DB == 1 ? fpenum::prefix_unrank<1>(binom(), I1, P.k - 1, g - 1, b)
+                                  : fpenum::prefix_unrank<4>(binom(), I1, P.k - 1, g - 1, b);
+      q = pf.m;
+      coef[q] = h;
+      uint64_t Q = pf.Q;
+      for (int s = 0; s < L; ++s) {
+        const int r = fpenum::ctz64(Q);
+        Q &= Q - 1;
+        coef[r] = (DB == 1 ? fpenum::gray_digit<1>(pf.d, s, b, L) : fpenum::gray_digit<4>(pf.d, s, b, L)) + 1;
+      }
+    }
+    if (y <= q) return false;  // entries of this stem have y > q
+    coef[y] = sign ? P.p - 1 : 1;
+    coef[x] = sign ? P.p - c : c;
+    *g_out = g;
+    *j_out = d.j;
+    return true;
+  }
   const int x = (int)fpk::key_leaf(key);
   const int c = (int)fpk::key_coef(key);
   if (x >= P.k || c < 1 || c >= P.p) return false;
@@ -489,8 +690,6 @@ bool key_coefficients(const Prepared &P, uint64_t key, int *g_out, int *j_out, s
   *j_out = d.j;
   return true;
 }
-
-}  // namespace
 
 int decode_result(const Prepared &P, const DeviceOutcome &o, fpcode_result *res, uint8_t *witness) {
   std::memset(res, 0, sizeof(*res));
@@ -671,6 +870,9 @@ int fpcode_test_task_ranges(fpcode_prepared *prep, int pass, int ctas, int fixed
     if (d.g == 1) {
       lo[t] = 0;
       hi[t] = d.nprefix;
+    } else if (d.nseg > 0) {
+      int ls = 0;
+      fpk::pair_task(d, &prep->host.segs[d.seg_off], prep->host.k, fph::binom(), (uint64_t)t, &lo[t], &hi[t], &ls);
     } else {
       fpk::task_range(d, (uint64_t)t, &lo[t], &hi[t]);
       lo[t] *= d.unit;
@@ -679,6 +881,33 @@ int fpcode_test_task_ranges(fpcode_prepared *prep, int pass, int ctas, int fixed
     }
   }
   return (int)d.ntasks;
+}
+
+int fpcode_test_pair_mode(const fpcode_prepared *prep, int pass, uint64_t J, uint32_t *entries) {
+  if (!prep) return -FPCODE_EINVAL;
+  const fph::Prepared &P = prep->host;
+  if (pass >= 0) {
+    if (pass >= (int)P.passes.size() || !entries || !P.pair) return -FPCODE_EINVAL;
+    const fpk::PassDesc &d = P.passes[pass];
+    if (d.g < 2 || J >= d.nprefix) return -FPCODE_EINVAL;
+    int q = -1;
+    if (d.g >= 3) {
+      const uint64_t N1 = fph::binom().c[P.k - 2][d.g - 2] * d.NC;
+      const int b = P.p - 1;
+      q = fph::digit_bits_of(P.p) == 1 ? fpenum::prefix_unrank<1>(fph::binom(), J % N1, P.k - 1, d.g - 1, b).m
+                                       : fpenum::prefix_unrank<4>(fph::binom(), J % N1, P.k - 1, d.g - 1, b).m;
+    }
+    *entries = fpk::pair_entries_above(P.k, q, P.p - 1);
+  }
+  return P.pair ? P.pair_sigp : 0;
+}
+
+int fpcode_test_key_coefficients(const fpcode_prepared *prep, uint64_t key, int *g, int *j, int *coef) {
+  if (!prep || !g || !j || !coef) return -1;
+  std::vector<int> c;
+  if (!fph::key_coefficients(prep->host, key, g, j, c)) return -1;
+  for (int t = 0; t < prep->host.k; ++t) coef[t] = c[t];
+  return 0;
 }
 
 int fpcode_prepared_shape(const fpcode_prepared *prep, int *m, int *kj, int *npasses, int *complete) {
@@ -707,12 +936,25 @@ int fpcode_test_prepared_row(const fpcode_prepared *prep, int j, int t, int v, u
   const size_t set_words = P->table_words_per_set();
   const uint32_t *e = &P->table[(size_t)j * set_words + ((size_t)t * (P->p - 1) + (v - 1)) * P->rwpad];
   std::memcpy(slices, e, (size_t)P->r * P->W * sizeof(uint32_t));
-  const int SIG = fpk::sig_words(P->p, P->r, P->W);
+  const int SIG = P->pair ? 0 : fpk::sig_words(P->p, P->r, P->W);  // pair leaves keep no row signatures
   if (sig && SIG) {
     const uint32_t *sg = &P->table[(size_t)j * set_words + (size_t)P->k * (P->p - 1) * P->rwpad + (size_t)t * SIG];
     std::memcpy(sig, sg, (size_t)SIG * sizeof(uint32_t));
   }
   return SIG;
+}
+
+int fpcode_test_pair_entry(const fpcode_prepared *prep, int j, uint32_t e, uint32_t *sig) {
+  const fph::Prepared *P = prep ? &prep->host : nullptr;
+  if (!P || !P->pair || j < 0 || j >= P->m || !sig) return -FPCODE_EINVAL;
+  const uint32_t ne = (uint32_t)(P->p - 1) * (uint32_t)(P->k * (P->k - 1) / 2);
+  if (e >= ne) return -FPCODE_EINVAL;
+  const size_t set_words = P->table_words_per_set();
+  const uint32_t *pt = &P->table[(size_t)j * set_words + (size_t)P->k * (P->p - 1) * P->rwpad];
+  std::memcpy(sig, pt + (size_t)e * P->pair_sigp, (size_t)P->pair_sigp * sizeof(uint32_t));
+  const uint32_t *p0 = pt + ((P->pair_entries() * (size_t)P->pair_sigp + 3) & ~(size_t)3);
+  std::memcpy(sig + P->pair_sigp, p0 + (size_t)e * P->W, (size_t)P->W * sizeof(uint32_t));
+  return P->pair_sigp + P->W;
 }
 
 int fpcode_prepared_passes(const fpcode_prepared *prep, fpcode_pass_info *passes, int max) {

@@ -37,15 +37,31 @@ struct Prepared {
   std::vector<uint8_t> gam;      // m * k * n: Gamma_j, rows in pivot order
   std::vector<int> piv;          // m * k pivot columns (increasing)
   std::vector<int> red;          // m * (n - k) non-pivot columns (increasing)
-  std::vector<uint32_t> table;   // m * k * (p-1) * rwpad bit-sliced multiples
+  std::vector<uint32_t> table;   // per set: k * (p-1) * rwpad bit-sliced multiples, then its signatures
   std::vector<fpk::PassDesc> passes;
+  // Pair leaves (fp_types.h): passes with g >= 2 read a table of pair
+  // signatures of A[y] + c A[x] and the segments of the task plan.
+  bool pair = false;
+  int pair_sigp = 0;             // words per pair entry (a power of two)
+  std::vector<fpk::PairSeg> segs;  // all passes' segments (PassDesc.seg_off, nseg)
   int complete = 0;              // schedule reaches the last level
-  uint64_t code_hash = 0;        // FNV-1a of (p, n, k, per_round_check, defer) and G: the schedule's identity
+  uint64_t code_hash = 0;        // FNV-1a of (p, n, k, per_round_check, defer, pair) and G: schedule and key layout
   int seed_u = 0;                // least weight of the g = 1 passes (rows of the Gamma_j), 0: none;
                                  // a search starts with it as its bound (SlotDesc.seed_u)
   int L0 = 0;                    // lower bound before any pass
   double t_prepare_ms = 0;
-  size_t table_words_per_set() const { return (size_t)k * ((size_t)(p - 1) * rwpad + fpk::sig_words(p, r, W)); }
+  size_t pair_entries() const { return (size_t)(p - 1) * ((size_t)k * (k - 1) / 2); }
+  // pair signatures (pair_sigp words an entry), then slice 0 of each entry
+  // (W words), each part padded to whole 16-byte vectors
+  size_t pair_words_per_set() const {
+    return pair ? ((pair_entries() * (size_t)pair_sigp + 3) & ~(size_t)3) + ((pair_entries() * (size_t)W + 3) & ~(size_t)3)
+                : 0;
+  }
+  int pair_quick_max = 0;        // thresholds up to this take the one-popcount pair bound
+  size_t table_words_per_set() const {
+    return pair ? (size_t)k * (size_t)(p - 1) * rwpad + pair_words_per_set()
+                : (size_t)k * ((size_t)(p - 1) * rwpad + fpk::sig_words(p, r, W));
+  }
   size_t table_bytes_per_set() const { return table_words_per_set() * 4; }
 };
 
@@ -64,6 +80,10 @@ int prepare(int p, int n, int k, const uint8_t *G, const fpcode_opts &opts, Prep
 // search run with a loose threshold, many exact leaves each, and sit on the
 // path to the first termination tests).
 void plan_tasks(Prepared *P, int ctas, int fixed_pl, int min_steps, bool spread_tiny);
+
+// Pair-leaf table limit per information set: with the binomial columns it
+// keeps four 256-thread CTAs resident per SM.
+constexpr size_t kPairTableMaxBytes = 40 * 1024;
 constexpr int kMinStepsSingle = 8;   // one code per launch
 constexpr int kMinStepsBatch = 32;   // many codes share the grid
 constexpr int kMinStepsServe = 1;    // streamed codes: latency first
@@ -76,6 +96,9 @@ struct DeviceOutcome {
   int stop_pass;         // last pass entered (-1: none)
 };
 int decode_result(const Prepared &P, const DeviceOutcome &o, fpcode_result *res, uint8_t *witness);
+// Coefficients (length k) of the codeword a packed key stands for, with its
+// level and information set; false if the key names none.
+bool key_coefficients(const Prepared &P, uint64_t key, int *g_out, int *j_out, std::vector<int> &coef);
 
 }  // namespace fph
 

@@ -75,6 +75,10 @@ constexpr int kBinomBytes = kBinomCols * (fpenum::kMaxK + 1) * 8;  // 12480, a m
 
 // Words of one information set's table: multiples, then pair signatures.
 __device__ __forceinline__ int table_words(const SlotDesc &sd) {
+  if (sd.pair_sigp > 0) {  // row multiples, then the pair signatures and slice 0 of each entry (16-byte padded)
+    const int ne = (sd.p - 1) * (sd.k * (sd.k - 1) / 2);
+    return sd.k * (sd.p - 1) * sd.rwpad + ((ne * sd.pair_sigp + 3) & ~3) + ((ne * sd.W + 3) & ~3);
+  }
   return sd.k * ((sd.p - 1) * sd.rwpad + sig_words(sd.p, sd.r, sd.W));
 }
 
@@ -155,8 +159,8 @@ constexpr int kSlotRows = 10;
 
 template <int P, int R, int W, int DB>
 __device__ __forceinline__ void build_sum(uint32_t (&s)[R * W], const uint32_t *tab, const fpenum::Prefix &pf,
-                                          int L, int b, int p, uint64_t &qrows) {
-  set_row<P, R, W>(s, tab, pf.m, 1, p);
+                                          int L, int b, int p, uint64_t &qrows, int hm = 1) {
+  set_row<P, R, W>(s, tab, pf.m, hm, p);  // the largest row, coefficient hm (1 for a one-row-leaf prefix)
   uint64_t Q = pf.Q;
   qrows = 0;
   for (int slot = 0; slot < L; ++slot) {
@@ -459,15 +463,324 @@ __device__ void task_prefixes(const SlotDesc &sd, const PassDesc &pd, int pass, 
   count += count32;
 }
 
+// ---------------------------------------------------------------------------
+// Task of a pair-leaf pass (g >= 2, p = 3 or 7; the enumeration is described
+// in fp_types.h).  The CTA's stems [Ja, Jb) go to 256 >> lsplit groups of
+// 1 << lsplit lanes, a contiguous run of stems per group; the lanes of a
+// group hold the same exact stem sum S and split the stem's pair entries in
+// interleaved chunks (lane sub takes chunks sub, sub + 2^lsplit, ...), so a
+// warp's table loads are broadcasts or consecutive words.  Per entry: one
+// pair bound (LOP3s and one popcount) for the two codewords S + B and S - B;
+// the warp votes every few loads, and only a vote that finds a bound under
+// the threshold runs the exact path, whose candidates are reduced to one
+// key per warp before the atomic record.  The best weight recorded anywhere
+// is read once per stem (the load issued before the stem's entries, used
+// after them).
+// ---------------------------------------------------------------------------
+template <int P, int R, int W>
+struct PairShape {
+  static constexpr int SW = W * (R - 1);                                    // signature words of an entry
+  static constexpr int SP = SW <= 1 ? 1 : SW <= 2 ? 2 : SW <= 4 ? 4 : 8;  // padded (the host's pair_sigp)
+  static constexpr int EPL = SP <= 2 ? 2 : 1;                               // entries per load
+  static constexpr int LW = SP * EPL;                                       // words per load
+  static constexpr int UNR = LW <= 4 ? 4 : 2;                               // loads per vote
+  static_assert(UNR * EPL <= 8, "PairQueue holds 8 entries per lane per vote");
+};
+
+// A warp's queue of pair-leaf candidates: (entry << 5) | lane.
+struct PairQueue {
+  uint32_t n;
+  uint32_t item[32 * 8 + 32];  // fewer than 32 left over, then 32 lanes x at most 8 entries of one vote
+};
+
+template <int LW>
+__device__ __forceinline__ void load_words(const uint32_t *tab, uint32_t i, uint32_t (&e)[LW]) {
+  if constexpr (LW == 2) {
+    const uint2 v = reinterpret_cast<const uint2 *>(tab)[i];
+    e[0] = v.x;
+    e[1] = v.y;
+  } else {
+    load_entry<LW>(tab, (int)i, e);
+  }
+}
+
+// Pair bound of S (signature a) and entry signature e: positions where both
+// S + B and S - B are nonzero; QUICK: one popcount of the words' OR (weaker,
+// used while the threshold is well under the bound's mean).
+template <int R, int W, bool QUICK>
+__device__ __forceinline__ int pair_lb(const uint32_t (&a)[W * (R - 1)], const uint32_t *e) {
+  if constexpr (QUICK && W > 1) {
+    uint32_t u = 0;
+#pragma unroll
+    for (int q = 0; q < W * (R - 1); ++q) u |= a[q] ^ e[q];
+    return __popc(u);
+  } else {
+    int lb = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      uint32_t f = 0;
+#pragma unroll
+      for (int i = 0; i + 1 < R; ++i) f |= a[w * (R - 1) + i] ^ e[w * (R - 1) + i];
+      lb += __popc(f);
+    }
+    return lb;
+  }
+}
+
+// Exact path of entry e of stem J: B from its signature words `sig` and
+// its slice 0 (`b0`, W words): slice i+1 = slice i xor signature word i.
+// The redundant weights of S + B (isometric subtraction against -B, the
+// complement of B where it is nonzero) and S - B; the least key under the
+// threshold joins `best`.
+template <int P, int R, int W>
+__device__ __forceinline__ void pair_exact(const uint32_t (&s)[R * W], const uint32_t *sig, const uint32_t *b0, int g,
+                                           int pass, uint64_t J, uint32_t e, int thr, uint64_t &best) {
+  int wp = 0, wm = 0;
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    uint32_t Bw[R], nb[R];
+    Bw[0] = b0[w];
+#pragma unroll
+    for (int i = 0; i + 1 < R; ++i) Bw[i + 1] = Bw[i] ^ sig[w * (R - 1) + i];
+    fpbs::neg_mersenne<R>(Bw, nb);
+    wp += __popc(fpbs::nz_sub<R>(&s[w * R], nb));
+    wm += __popc(fpbs::nz_sub<R>(&s[w * R], Bw));
+  }
+  if (wp < thr) best = min(best, (uint64_t)make_pair_key((uint32_t)(g + wp), (uint32_t)pass, J, e, 0));
+  if (g >= 3 && wm < thr) best = min(best, (uint64_t)make_pair_key((uint32_t)(g + wm), (uint32_t)pass, J, e, 1));
+}
+
+template <int P, int R, int W, int DB>
+__device__ void task_pairs(const SlotDesc &sd, const PassDesc &pd, int pass, const uint32_t *tab,
+                           const fpenum::BinomCols &B, uint64_t Ja, uint64_t Jb, int shape, int U, SlotState *st,
+                           SlotAux *ax, unsigned long long &count) {
+  using S = PairShape<P, R, W>;
+  constexpr int RW = R * W;
+  constexpr int SW = S::SW, SP = S::SP, EPL = S::EPL, LW = S::LW, UNR = S::UNR;
+  constexpr unsigned FULL = 0xffffffffu;
+  constexpr int b = P - 1;
+  const int k = sd.k;
+  const int g = pd.g;
+  const int lane = threadIdx.x & 31;
+  const uint32_t *ptab = tab + k * b * sd.rwpad;  // pair signatures
+  const uint32_t *p0tab = ptab + (((b * (k * (k - 1) / 2)) * SP + 3) & ~3);  // slice 0 of each entry
+  const int lsplit = shape & 15;
+  const int sub = (int)threadIdx.x & ((1 << lsplit) - 1);
+  const uint64_t spg = (uint64_t)(shape >> 4);  // the plan's stems per group: aligned to the coefficient counter
+  uint64_t J = Ja + (uint64_t)(threadIdx.x >> lsplit) * spg;
+  const uint64_t Jend = J + spg < Jb ? J + spg : Jb;
+  const uint32_t nstem = J < Jend ? (uint32_t)(Jend - J) : 0u;
+  int thr = U - g + 1;  // record weights <= U: redundant weight < U - g + 1
+
+  uint32_t s[RW];
+#pragma unroll
+  for (int q = 0; q < RW; ++q) s[q] = 0;
+  uint32_t a[SW];
+#pragma unroll
+  for (int q = 0; q < SW; ++q) a[q] = 0;
+  // the stem: h and the prefix over rows 0..k-2 at level g - 1 (g >= 3)
+  const int L = g - 3;
+  const uint64_t NC = pd.NC;
+  const uint64_t N1 = g >= 3 ? B(k - 2, g - 2) * NC : 1;
+  fpenum::Prefix pf;
+  pf.m = -1;
+  pf.qi = 0;
+  pf.Q = 0;
+  pf.d = 0;
+  uint64_t ci = 0, nq = 1, qrows = 0, I1 = 0;
+  int h = 1;
+  if (nstem && g >= 3) {
+    h = (int)(J / N1) + 1;
+    I1 = J - (uint64_t)(h - 1) * N1;
+    pf = fpenum::prefix_unrank<DB>(B, I1, k - 1, g - 1, b);
+    ci = I1 - fpenum::prefixes_below(B, pf.m, g - 1, NC) - pf.qi * NC;
+    nq = B(pf.m, L);
+    build_sum<P, R, W, DB>(s, tab, pf, L, b, P, qrows, h);
+  }
+  const unsigned long long cpe = g >= 3 ? 2ull : 1ull;  // codewords per entry
+  const uint32_t nmax = __reduce_max_sync(FULL, nstem);
+  // the warp's candidate queue: up to UNR * EPL entries per lane per vote
+  __shared__ PairQueue s_pq[kWarps];
+  PairQueue *wq = &s_pq[threadIdx.x >> 5];
+  if (lane == 0) wq->n = 0;
+  __syncwarp();
+  // the code's finished flag and best key, read by lane 0 and taken up once
+  // the warp has done kPollWork entries since (the loads' latency hides
+  // behind them)
+  constexpr uint32_t kPollWork = 192;
+  int pfin = 0;
+  unsigned long long pkey = 0;
+  if (lane == 0) {
+    pfin = ld_vol(&st->finished);
+    pkey = ld_vol(&st->best_key);
+  }
+  uint32_t since = 0;
+  for (uint32_t it = 0; it < nmax; ++it) {
+    const bool act = it < nstem;
+    if constexpr (SW > 0) prefix_signature<R, W>(s, a);
+    const uint32_t E = act ? pair_entries_above(k, pf.m, b) : 0u;  // pf.m = -1 for g = 2
+    const uint32_t nch = E / EPL;  // E is a multiple of EPL: even for p = 3, a multiple of 6 for p = 7
+    const uint32_t its = nch > (uint32_t)sub ? ((nch - (uint32_t)sub + (1u << lsplit) - 1) >> lsplit) : 0u;
+    const uint32_t its_lo = __reduce_min_sync(FULL, its), its_hi = __reduce_max_sync(FULL, its);
+    // Candidates (entries whose bound is under the threshold) go to the
+    // warp's queue as (entry, lane); the warp checks them 32 at a time, each
+    // lane taking one and fetching the owner's stem sum by shuffle, so the
+    // exact path costs the warp one pass per 32 candidates instead of one
+    // per vote that found any.  One record per warp, only if some lane found
+    // a codeword under the threshold.
+    auto check = [&](uint32_t first, uint32_t cnt) {
+      const bool have = (uint32_t)lane < cnt;
+      const uint32_t item = have ? wq->item[first + lane] : 0u;
+      const int src = (int)(item & 31u);
+      const uint32_t ec = item >> 5;
+      uint32_t so[RW];
+#pragma unroll
+      for (int q = 0; q < RW; ++q) so[q] = __shfl_sync(FULL, s[q], src);
+      const uint64_t Jo = (uint64_t)__shfl_sync(FULL, (unsigned long long)J, src);
+      uint64_t best = kNoKey;
+      if (have) {
+        uint32_t ew[SP];
+#pragma unroll
+        for (int q = 0; q < SP; ++q) ew[q] = ptab[ec * SP + q];
+        pair_exact<P, R, W>(so, ew, p0tab + ec * W, g, pass, Jo, ec, thr, best);
+      }
+      if (__any_sync(FULL, best != kNoKey)) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) best = min(best, (uint64_t)__shfl_xor_sync(FULL, (unsigned long long)best, o));
+        if (lane == 0) record(st, ax, pass, best);
+        thr = min(thr, (int)key_weight(best) - g + 1);
+      }
+    };
+    // after a vote that found candidates: check full rounds of 32 from the
+    // queue's end, keep the rest for the stem's end
+    auto drain_full = [&]() {
+      __syncwarp();
+      uint32_t n = wq->n;
+      while (n >= 32) {
+        n -= 32;
+        check(n, 32);
+      }
+      __syncwarp();
+      if (lane == 0) wq->n = n;
+      __syncwarp();
+    };
+    auto push = [&](uint32_t e) { wq->item[atomicAdd(&wq->n, 1u)] = (e << 5) | (uint32_t)lane; };
+    auto entries = [&](auto quick_tag) {
+      constexpr bool QUICK = decltype(quick_tag)::value;
+      uint32_t i = 0;
+      for (; i + UNR <= its_lo; i += UNR) {  // every lane has UNR more loads
+        int lb[UNR * EPL];
+        int lbm = 1 << 20;
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+          uint32_t e[LW];
+          load_words<LW>(ptab, (uint32_t)sub + ((i + u) << lsplit), e);
+#pragma unroll
+          for (int v = 0; v < EPL; ++v) {
+            lb[u * EPL + v] = pair_lb<R, W, QUICK>(a, &e[v * SP]);
+            lbm = min(lbm, lb[u * EPL + v]);
+          }
+        }
+        if (__any_sync(FULL, lbm < thr)) {
+          if (lbm < thr) {
+#pragma unroll
+            for (int u = 0; u < UNR; ++u)
+#pragma unroll
+              for (int v = 0; v < EPL; ++v)
+                if (lb[u * EPL + v] < thr) push(((uint32_t)sub + ((i + u) << lsplit)) * EPL + v);
+          }
+          drain_full();
+        }
+      }
+      for (; i < its_hi; ++i) {  // the rest: lanes with fewer loads sit out
+        const bool on = i < its;
+        const uint32_t ch = on ? (uint32_t)sub + (i << lsplit) : 0u;
+        uint32_t e[LW];
+        load_words<LW>(ptab, ch, e);
+        int lb[EPL];
+        int lbm = 1 << 20;
+#pragma unroll
+        for (int v = 0; v < EPL; ++v) {
+          lb[v] = on ? pair_lb<R, W, QUICK>(a, &e[v * SP]) : (1 << 20);
+          lbm = min(lbm, lb[v]);
+        }
+        if (__any_sync(FULL, lbm < thr)) {
+#pragma unroll
+          for (int v = 0; v < EPL; ++v)
+            if (lb[v] < thr) push(ch * EPL + v);
+          drain_full();
+        }
+      }
+    };
+    if constexpr (W > 1) {
+      if (thr <= sd.pair_quick_max) entries(BoolTag<true>{});  // thr is the same on every lane of the warp
+      else entries(BoolTag<false>{});
+    } else {
+      entries(BoolTag<false>{});
+    }
+    // the stem's last candidates (the queue refers to this stem's sums)
+    __syncwarp();
+    if (const uint32_t n = wq->n) {
+      check(0, n);
+      __syncwarp();
+      if (lane == 0) wq->n = 0;
+      __syncwarp();
+    }
+    if (act && sub == 0) count += (unsigned long long)E * cpe;
+    since += its_hi * EPL + 8;
+    if (since >= kPollWork) {
+      // the code finished: drop the rest; else take up the best weight recorded anywhere
+      if (__shfl_sync(FULL, pfin, 0)) break;
+      const uint64_t key = ~(uint64_t)__shfl_sync(FULL, pkey, 0);
+      if (key != kNoKey) thr = min(thr, (int)key_weight(key) - g + 1);
+      if (lane == 0) {
+        pfin = ld_vol(&st->finished);
+        pkey = ld_vol(&st->best_key);
+      }
+      since = 0;
+    }
+    // next stem
+    if (act && it + 1 < nstem) {
+      if (I1 + 1 < N1) {
+        int dir;
+        const int slot = fpenum::prefix_advance<DB>(B, pf, ci, nq, NC, b, L, &dir);
+        if (slot >= 0) {
+          const int qq = slot < kSlotRows ? (int)(qrows >> (6 * slot)) & 63 : fpenum::nth_member(pf.Q, slot);
+          add_row<P, R, W>(s, tab, qq, dir > 0 ? 1 : b, P);  // c -> c+1: +A; c -> c-1: +(p-1)A
+        } else {
+          build_sum<P, R, W, DB>(s, tab, pf, L, b, P, qrows, h);
+        }
+        ++I1;
+      } else {  // next h: the first prefix again, largest row coefficient h + 1
+        ++h;
+        I1 = 0;
+        pf = fpenum::prefix_unrank<DB>(B, 0, k - 1, g - 1, b);
+        ci = 0;
+        nq = B(pf.m, L);
+        build_sum<P, R, W, DB>(s, tab, pf, L, b, P, qrows, h);
+      }
+      ++J;
+    }
+  }
+}
+
 // One kernel variant: prime P (0: any, from the descriptor), r slices, W
 // words per slice; UNR leaves per vote in the leaf loop (1: the plain loop,
-// whose smaller code suits the batched kernels).
-template <int P, int R, int W, int UNR = LeafFilter<P, R, W>::kUnroll>
+// whose smaller code suits the batched kernels); PAIRS: pair-leaf passes
+// for codes prepared with them (p = 3, 7, single-code kernels).
+template <int P, int R, int W, int UNR = LeafFilter<P, R, W>::kUnroll, bool PAIRS = false>
 struct Fixed {
   static constexpr int DB = P == 3 ? 1 : (P == 5 || P == 7) ? 4 : 8;  // as the host's digit width
   static __device__ __forceinline__ void run(const SlotDesc &sd, const PassDesc &pd, int pass, const uint32_t *tab,
-                                             const fpenum::BinomCols &B, uint64_t ulo, uint64_t uhi, int U,
-                                             SlotState *st, SlotAux *ax, unsigned long long &count) {
+                                             const fpenum::BinomCols &B, uint64_t ulo, uint64_t uhi, int lsplit,
+                                             int U, SlotState *st, SlotAux *ax, unsigned long long &count) {
+    if constexpr (PAIRS && (P == 3 || P == 7)) {
+      if (sd.pair_sigp > 0 && pd.g >= 2) {
+        task_pairs<P, R, W, DB>(sd, pd, pass, tab, B, ulo, uhi, lsplit, U, st, ax, count);
+        return;
+      }
+    }
+    (void)lsplit;
     if (pd.g == 1) {
       if (ulo == 0) task_rows<P, R, W>(sd, pass, tab, U, st, ax, count);
     } else {
@@ -484,11 +797,11 @@ struct Fixed {
 template <int WMAX>
 struct Multi357 {
   static __device__ __forceinline__ void run(const SlotDesc &sd, const PassDesc &pd, int pass, const uint32_t *tab,
-                                             const fpenum::BinomCols &B, uint64_t ulo, uint64_t uhi, int U,
-                                             SlotState *st, SlotAux *ax, unsigned long long &count) {
+                                             const fpenum::BinomCols &B, uint64_t ulo, uint64_t uhi, int lsplit,
+                                             int U, SlotState *st, SlotAux *ax, unsigned long long &count) {
     switch (sd.variant) {
 #define FPK_CASE(id, P, R, W) \
-  case id: if constexpr (W <= WMAX) Fixed<P, R, W, 1>::run(sd, pd, pass, tab, B, ulo, uhi, U, st, ax, count); break;
+  case id: if constexpr (W <= WMAX) Fixed<P, R, W, 1>::run(sd, pd, pass, tab, B, ulo, uhi, lsplit, U, st, ax, count); break;
       FPK_CASE(0, 3, 2, 1)
       FPK_CASE(1, 3, 2, 2)
       FPK_CASE(2, 3, 2, 3)
@@ -514,10 +827,18 @@ struct Claim {
   SlotDesc sd;
   PassDesc pd;              // the task's pass
   unsigned long long task;  // task index within the pass
-  uint64_t ulo, uhi;        // its unit range (g >= 2; g == 1: task, task + 1), computed once for the CTA
+  uint64_t ulo, uhi;        // its unit range (g >= 2; pair-leaf passes: stems; g == 1: task, task + 1)
   int slot, pass, U, skip;
   unsigned int ndone;       // tasks of the pass this claim completes (skipped runs: more than one)
-  unsigned int pad;
+  int lsplit;               // pair-leaf passes: lanes per stem (log2, low 4 bits) | stems per group << 4
+};
+
+// Thread 0's shared-memory copy of the segments of one pair-leaf pass.
+constexpr int kSegCache = 192;  // the host plans at most (p-1)/2 (k-2) <= 186 segments per pass
+struct SegCache {
+  PairSeg seg[kSegCache];
+  int slot, pass;               // whose (-1: none)
+  unsigned long long gen;
 };
 
 // Thread 0's cache of the descriptors it read last (one slot and pass), so
@@ -589,7 +910,8 @@ __device__ __forceinline__ void slot_leave(const CtlStatic &cs, int s) {
 // task of the pass is then droppable too, so the rest of the pass is taken
 // in the same claim by compare-and-swap on the code's own generation.
 __device__ __forceinline__ void take(SlotState *st, const KParams &kp, bool serve, int s, unsigned long long w,
-                                    uint64_t key, Claim *o, ClaimCache &cc) {
+                                    uint64_t key, Claim *o, ClaimCache &cc, SegCache &sc,
+                                    const fpenum::BinomCols &B) {
   const unsigned long long t = w & kTaskMask;
   // the bound: the best recorded weight, else n - k + 2 (the skip rule uses
   // this one: it needs a recorded key); the g = 1 passes' least weight
@@ -602,7 +924,21 @@ __device__ __forceinline__ void take(SlotState *st, const KParams &kp, bool serv
   o->sd = cc.sd;
   o->pd = cc.pd;
   o->task = t - cc.pd.task_base;
-  if (cc.pd.g > 1) {
+  o->lsplit = 0;
+  if (cc.pd.g > 1 && cc.pd.nseg > 0) {
+    // pair-leaf pass: its segments, copied once per pass into shared memory
+    if (sc.slot != s || sc.gen != cc.gen || sc.pass != cc.P) {
+      const uint2 *src = reinterpret_cast<const uint2 *>(cc.sd.passes + cc.sd.npasses) + cc.pd.seg_off;
+      const int n = min((int)cc.pd.nseg, kSegCache);
+      for (int i = 0; i < n; ++i) reinterpret_cast<uint2 *>(sc.seg)[i] = __ldcg(src + i);
+      sc.slot = s;
+      sc.gen = cc.gen;
+      sc.pass = cc.P;
+    }
+    int ls = 0, spg = 1;
+    pair_task(cc.pd, sc.seg, cc.sd.k, B, o->task, &o->ulo, &o->uhi, &ls, &spg);
+    o->lsplit = ls | (spg << 4);
+  } else if (cc.pd.g > 1) {
     task_range(cc.pd, o->task, &o->ulo, &o->uhi);
   } else {
     o->ulo = o->task;
@@ -643,7 +979,8 @@ __device__ __forceinline__ void take(SlotState *st, const KParams &kp, bool serv
 // Thread 0: claim the next task of any live code.
 __device__ __forceinline__ int claim(const SlotDesc *slots, SlotState *states, const CtlStatic &cs,
                                      const KParams &kp, CtlDyn *cd, int &rr, unsigned long long &wait_t0,
-                                     unsigned long long t_start, Claim *o, ClaimCache &cc) {
+                                     unsigned long long t_start, Claim *o, ClaimCache &cc, SegCache &sc,
+                                     const fpenum::BinomCols &B) {
   const int nslots = cs.nslots;
   unsigned long long now = globaltimer();
   if (kp.timeout_ns && now - t_start > kp.timeout_ns) {
@@ -671,7 +1008,7 @@ __device__ __forceinline__ int claim(const SlotDesc *slots, SlotState *states, c
     }
     if ((w >> kGenShift) == cc.gen && cc.sd.npasses > 0 && fin != fin_tag(cc.gen)) {
       if (locate(cc, w & kTaskMask)) {
-        take(st, kp, cs.serve != 0, s, w, key, o, cc);
+        take(st, kp, cs.serve != 0, s, w, key, o, cc, sc, B);
         rr = s;
         wait_t0 = 0;
         cc.sleep_ns = 128;
@@ -736,7 +1073,7 @@ __device__ __forceinline__ int claim(const SlotDesc *slots, SlotState *states, c
         slot_leave(cs, s);
         continue;
       }
-      take(st, kp, cs.serve != 0, s, w, best_key(st), o, cc);
+      take(st, kp, cs.serve != 0, s, w, best_key(st), o, cc, sc, B);
       rr = s;
       wait_t0 = 0;
       cc.sleep_ns = 128;
@@ -811,18 +1148,27 @@ __device__ __forceinline__ void conclude(const CtlStatic &cs, const KParams &kp,
   }
 }
 
-// Thread 0: count a finished task of pass P.  Passes complete in any order;
-// whoever sees the frontier pass complete applies its termination test
-// (Alg. 6) with the least weight recorded in it and the passes before
+// Thread 0 counts a finished task of pass P off.  Passes complete in any
+// order; whoever sees the frontier pass complete applies its termination
+// test (Alg. 6) with the least weight recorded in it and the passes before
 // it, and moves the frontier on.  Two CTAs may test the same pass: they
 // read the same final values and write the same results, and the
 // compare-and-swap on the frontier lets exactly one move it.
-__device__ __forceinline__ void finish_task(const CtlStatic &cs, const KParams &kp, CtlDyn *cd, const SlotDesc &sd,
-                                            SlotState *st, SlotAux *ax, int slot, int P, const PassDesc &pd,
-                                            unsigned int ndone) {
-  __threadfence();
-  const unsigned int done = atomicAdd(&ax->pass_done[P], ndone) + ndone;
-  if (done != pd.ntasks) return;
+//
+// The count-off itself: a release add, so that the task's records and
+// counts (made before it, by this thread or, through the CTA barrier, by
+// the others) are seen by whoever finds the pass complete.  Returns the
+// tasks of pass P done with this one.
+__device__ __forceinline__ unsigned int count_off(SlotAux *ax, int P, unsigned int ndone) {
+  unsigned int old;
+  asm volatile("atom.release.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(&ax->pass_done[P]), "r"(ndone) : "memory");
+  return old + ndone;
+}
+
+// Termination tests from the frontier on, after a count-off that completed
+// pass P (see finish_task).
+__device__ __forceinline__ void test_frontier(const CtlStatic &cs, const KParams &kp, CtlDyn *cd, const SlotDesc &sd,
+                                              SlotState *st, SlotAux *ax, int slot, int P, const PassDesc &pd) {
   __threadfence();
   for (;;) {
     const int f = ld_vol(&st->frontier);
@@ -849,6 +1195,13 @@ __device__ __forceinline__ void finish_task(const CtlStatic &cs, const KParams &
   }
 }
 
+__device__ __forceinline__ void finish_task(const CtlStatic &cs, const KParams &kp, CtlDyn *cd, const SlotDesc &sd,
+                                            SlotState *st, SlotAux *ax, int slot, int P, const PassDesc &pd,
+                                            unsigned int ndone) {
+  if (count_off(ax, P, ndone) == pd.ntasks) test_frontier(cs, kp, cd, sd, st, ax, slot, P, pd);
+}
+
+
 #ifndef FPK_MIN_BLOCKS
 #define FPK_MIN_BLOCKS 4  // CTAs per SM the register allocation is capped for
 #endif
@@ -863,6 +1216,7 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
   uint32_t *tab = reinterpret_cast<uint32_t *>(tab4);
   __shared__ Claim s_cl;
   __shared__ ClaimCache s_cc;
+  __shared__ SegCache s_sc;
   __shared__ int s_cmd, s_stage;
   __shared__ unsigned long long s_count, s_staged_seq;
   __shared__ int s_staged_slot, s_staged_j;
@@ -881,6 +1235,9 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
     s_cc.gen = 0;
     s_cc.sleep_ns = 128;
     s_cc.busy_note = 0;
+    s_sc.slot = -1;
+    s_sc.pass = -1;
+    s_sc.gen = 0;
   }
   {
     static_assert(kBinomBytes == sizeof(cs.binom->cols), "staged binomial columns");
@@ -895,7 +1252,7 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
   __syncthreads();
   for (;;) {
     if (tid == 0) {
-      const int cmd = claim(slots, states, cs, kp, cdyn, rr, wait_t0, t_start, &s_cl, s_cc);
+      const int cmd = claim(slots, states, cs, kp, cdyn, rr, wait_t0, t_start, &s_cl, s_cc, s_sc, binom);
       s_cmd = cmd;
       if (cmd == kCmdRun && cs.serve) {  // keep the serving kernel whole (at most one note per 0.5 ms)
         const unsigned long long now = globaltimer();
@@ -931,7 +1288,8 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
     }
     unsigned long long count = 0;
     SlotAux *ax = cs.aux + slot;
-    if (!s_cl.skip) V::run(s_cl.sd, s_cl.pd, s_cl.pass, tab, binom, s_cl.ulo, s_cl.uhi, s_cl.U, &states[slot], ax, count);
+    if (!s_cl.skip)
+      V::run(s_cl.sd, s_cl.pd, s_cl.pass, tab, binom, s_cl.ulo, s_cl.uhi, s_cl.lsplit, s_cl.U, &states[slot], ax, count);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) count += __shfl_xor_sync(0xffffffffu, count, o);
     if ((tid & 31) == 0 && count) atomicAdd(&s_count, count);

@@ -83,11 +83,18 @@ extern "C" int fpcode_min_distance_noalloc(int p, int n, int k, const uint8_t *G
   int s = fph::prepare(p, n, k, G, o, &P);
   if (s) return s;
 
-  // layout inside the array: [binom][CtlStatic][SlotDesc][passes][table][state][dyn][aux][flags]
+  // layout inside the array: [binom][CtlStatic][SlotDesc][passes, segments][table][state][dyn][aux][flags].
+  // The pair-leaf plan (made below, for the grid) has at most one segment
+  // per block (h, q) of each pass.
+  size_t max_segs = 0;
+  if (P.pair)
+    for (const auto &pd : P.passes)
+      if (pd.g >= 2) max_segs += pd.g == 2 ? 1 : (size_t)((P.p - 1) / 2) * (size_t)(P.k - 2 - (pd.g - 3));
   const size_t off_ctl = a256(sizeof(fpenum::Binom));
   const size_t off_slot = a256(off_ctl + sizeof(fpk::CtlStatic));
   const size_t off_pass = a256(off_slot + sizeof(fpk::SlotDesc));
-  const size_t off_table = a256(off_pass + P.passes.size() * sizeof(fpk::PassDesc));
+  const size_t off_table =
+      a256(off_pass + P.passes.size() * sizeof(fpk::PassDesc) + max_segs * sizeof(fpk::PairSeg));
   const size_t off_state = a256(off_table + P.table.size() * sizeof(uint32_t));
   const size_t dyn_bytes = a256(sizeof(fpk::SlotState) + sizeof(fpk::CtlDyn));
   const size_t off_aux = off_state + dyn_bytes;
@@ -122,6 +129,10 @@ extern "C" int fpcode_min_distance_noalloc(int p, int n, int k, const uint8_t *G
   NA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int ctas = sms * per_sm;
   fph::plan_tasks(&P, ctas, 0, fph::kMinStepsSingle, true);
+  if (P.segs.size() > max_segs) {
+    fph::set_error("internal: pair-leaf plan larger than its bound");
+    return FPCODE_EINVAL;
+  }
 
   // host image of the static part (starting at off_ctl)
   std::vector<unsigned char> img(off_state - off_ctl, 0);
@@ -146,10 +157,15 @@ extern "C" int fpcode_min_distance_noalloc(int p, int n, int k, const uint8_t *G
   sd.mid_pass_exit = P.opts.mid_pass_exit;
   sd.complete = P.complete;
   sd.seed_u = P.seed_u;
+  sd.pair_sigp = P.pair ? P.pair_sigp : 0;
+  sd.pair_quick_max = P.pair_quick_max;
   sd.table = reinterpret_cast<const uint32_t *>(base + off_table);
   sd.passes = reinterpret_cast<const fpk::PassDesc *>(base + off_pass);
   std::memcpy(&img[off_slot - off_ctl], &sd, sizeof(sd));
   std::memcpy(&img[off_pass - off_ctl], P.passes.data(), P.passes.size() * sizeof(fpk::PassDesc));
+  if (!P.segs.empty())  // pair-leaf segments right after the passes
+    std::memcpy(&img[off_pass - off_ctl + P.passes.size() * sizeof(fpk::PassDesc)], P.segs.data(),
+                P.segs.size() * sizeof(fpk::PairSeg));
   std::memcpy(&img[off_table - off_ctl], P.table.data(), P.table.size() * sizeof(uint32_t));
 
   NA_CUDA(cudaMemcpyAsync(base + off_ctl, img.data(), img.size(), cudaMemcpyHostToDevice, st));

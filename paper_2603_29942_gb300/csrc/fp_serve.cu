@@ -266,6 +266,7 @@ int fpcode_serve_create(const fpcode_serve_opts *opts, void *stream, fpcode_serv
 int fpcode_serve_submit(fpcode_server *s, const fpcode_desc *code, uint64_t *ticket) {
   if (!s || !code || !ticket) return FPCODE_EINVAL;
   fpcode_opts o = s->o.search;
+  o.pair_leaves = 0;  // the serving kernels take one-row leaves
   if (code->budget) o.budget = code->budget;
   std::unique_ptr<fph::Prepared> P(new fph::Prepared());
   int st = fph::prepare(code->p, code->n, code->k, code->G, o, P.get());
@@ -326,6 +327,7 @@ int fpcode_serve_submit(fpcode_server *s, const fpcode_desc *code, uint64_t *tic
   sd.mid_pass_exit = P->opts.mid_pass_exit;
   sd.complete = P->complete;
   sd.seed_u = P->seed_u;
+  sd.pair_sigp = 0;
   sd.table = reinterpret_cast<const uint32_t *>(d_tab);
   sd.passes = reinterpret_cast<const fpk::PassDesc *>(d_pass);
   sd.seq = tk;

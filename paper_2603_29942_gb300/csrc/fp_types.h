@@ -52,7 +52,9 @@ struct PassDesc {
   // Tasks of all passes form one sequence: CTAs take them in order, so a
   // pass's tasks are handed out as soon as the previous pass has none left.
   uint32_t task_base;      // tasks of all earlier passes
-  uint32_t pad0, pad1, pad2;
+  uint32_t seg_off;        // pair-leaf passes: first segment of the pass in the code's segment list
+  uint32_t nseg;           // pair-leaf passes: its segments (0: a one-row-leaf pass)
+  uint32_t pad2;
 };
 
 // Words per row of the pair-signature table (Mersenne p = 3, 7): for each
@@ -120,6 +122,97 @@ FPK_HD void task_range(const PassDesc &d, uint64_t t, uint64_t *lo, uint64_t *hi
 }
 static_assert(sizeof(PassDesc) == 80, "PassDesc layout");
 
+// ---------------------------------------------------------------------------
+// Pair leaves (p = 3, 7).  A codeword of pass g >= 3 with rows T splits into
+// its two largest rows y < x and the stem Q (the other g - 2 rows, largest
+// q).  The table holds, for every pair y < x and c in [1, p), the pair
+// signature of B = A[y] + c A[x]; the lane holds the exact stem sum S, and
+// one popcount bounds both S + B and S - B (the pair filter).  S - B is -1
+// times the codeword with stem coefficients -c_Q, so stems take only half
+// the coefficients of q (h in [1, (p-1)/2]) and every class is met once.
+// Stem J of a pass: h = J / N1 + 1, and J % N1 is a prefix index of the
+// one-row-leaf enumeration over rows 0..k-2 at level g - 1 (largest row q,
+// the rest R with its coefficient counter).  Pass g = 2 has one empty stem
+// (S = 0) whose entries are the codewords themselves.
+//
+// Entry order: pairs by y descending, then x ascending, then c; the
+// entries with y > q are the first (p-1) C(k-1-q, 2).  After the signatures
+// the table holds slice 0 of every B (W words an entry): with the
+// signatures it gives B exactly (slice i+1 = slice i xor signature word i,
+// for the natural encoding of p = 2^r - 1), for the exact path.
+// ---------------------------------------------------------------------------
+
+// One segment of a pair-leaf pass: stems from the block (h, q) on, cut into
+// tasks of 256 >> lsplit groups of lanes, each group taking spg stems and
+// its 1 << lsplit lanes splitting each stem's entries.
+struct PairSeg {
+  uint32_t task_end;  // tasks of the pass up to the end of this segment
+  uint16_t spg;       // stems per group per task
+  uint8_t q;          // largest stem row of the first block (255: the empty stem of g = 2)
+  uint8_t hsplit;     // (h - 1) << 4 | lsplit
+};
+static_assert(sizeof(PairSeg) == 8, "PairSeg layout");
+
+// Packed key of a pair-leaf codeword: (weight, pass, stem J (33 bits),
+// entry e (14 bits), sign (S + B: 0, S - B: 1)).
+constexpr int kPairKeyJ = 15, kPairKeyE = 1;
+FPK_HD uint64_t make_pair_key(uint32_t weight, uint32_t pass, uint64_t J, uint32_t e, uint32_t sign) {
+  return ((uint64_t)weight << kKeyW) | ((uint64_t)pass << kKeyP) | (J << kPairKeyJ) | ((uint64_t)e << kPairKeyE) |
+         (uint64_t)sign;
+}
+FPK_HD uint64_t pair_key_stem(uint64_t key) { return (key >> kPairKeyJ) & ((1ull << 33) - 1); }
+FPK_HD uint32_t pair_key_entry(uint64_t key) { return (uint32_t)(key >> kPairKeyE) & 0x3FFFu; }
+FPK_HD uint32_t pair_key_sign(uint64_t key) { return (uint32_t)key & 1u; }
+
+// Entries of the pairs with y > q: (p - 1) C(k - 1 - q, 2) (q = -1: all).
+FPK_HD uint32_t pair_entries_above(int k, int q, int b) {
+  const uint32_t t = (uint32_t)(k - 1 - q);
+  return (uint32_t)b * (t * (t - 1) / 2);
+}
+// Entry e -> (y, x, c).  Pair index P = e / b; with t = k - 1 - y the pairs
+// above y number C(t, 2), so t is the largest with C(t, 2) <= P.
+FPK_HD void pair_entry_rows(int k, int b, uint32_t e, int *y, int *x, int *c) {
+  const uint32_t P = e / (uint32_t)b;
+  *c = (int)(e - P * (uint32_t)b) + 1;
+  uint32_t t = 1;
+  while ((t + 1) * t / 2 <= P) ++t;
+  *y = k - 1 - (int)t;
+  *x = *y + 1 + (int)(P - t * (t - 1) / 2);
+}
+
+// First stem of segment s of pair-leaf pass d (B(n, t) = C(n, t)).  Stems
+// of the blocks before (h, q): (h - 1) N1 + C(q, g - 2) (p-1)^(g-3), with
+// N1 = C(k - 2, g - 2) (p-1)^(g-3) the stems per h.
+template <class BT>
+FPK_HD uint64_t pair_seg_first(const PassDesc &d, const PairSeg &s, int k, const BT &B) {
+  if (s.q == 255) return 0;
+  const uint64_t N1 = B(k - 2, d.g - 2) * d.NC;
+  return (uint64_t)(s.hsplit >> 4) * N1 + B(s.q, d.g - 2) * d.NC;
+}
+
+// Stem range [Ja, Jb) and entry split of task t of pair-leaf pass d, whose
+// segments are seg[0 .. d.nseg) (device: a shared-memory copy; host: the
+// plan itself).  The segment is the first whose task_end exceeds t.  Group
+// g of the task takes stems [Ja + g spg, Ja + (g + 1) spg) within [Ja, Jb).
+template <class BT>
+FPK_HD void pair_task(const PassDesc &d, const PairSeg *seg, int k, const BT &B, uint64_t t, uint64_t *Ja,
+                      uint64_t *Jb, int *lsplit, int *spg = nullptr) {
+  int lo = 0, hi = (int)d.nseg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (seg[mid].task_end > t) hi = mid;
+    else lo = mid + 1;
+  }
+  const uint64_t t0 = lo > 0 ? seg[lo - 1].task_end : 0;
+  const uint64_t J0 = pair_seg_first(d, seg[lo], k, B);
+  const uint64_t J1 = lo + 1 < (int)d.nseg ? pair_seg_first(d, seg[lo + 1], k, B) : d.nprefix;
+  *lsplit = seg[lo].hsplit & 15;
+  if (spg) *spg = seg[lo].spg;
+  const uint64_t per = (uint64_t)(kThreads >> *lsplit) * seg[lo].spg;
+  *Ja = J0 + (t - t0) * per;
+  *Jb = *Ja + per < J1 ? *Ja + per : J1;
+}
+
 // Static description of one code as the kernel sees it.
 struct SlotDesc {
   int32_t p, n, k, r, W, rwpad;  // rwpad: words per stored multiple (r*W rounded up to 4)
@@ -129,7 +222,9 @@ struct SlotDesc {
   int32_t mid_pass_exit;
   int32_t complete;              // 1: the schedule runs to the last level
   int32_t seed_u;                // > 0: least weight of the g = 1 passes, the search's first bound
-  int32_t pad_s[3];
+  int32_t pair_sigp;             // > 0: pair-leaf passes (g >= 2), words per pair-table entry; 0: one-row leaves
+  int32_t pair_quick_max;        // pair leaves: thresholds up to this take the one-popcount bound
+  int32_t pad_s[1];
   const uint32_t *table;         // m * k * (p-1) * rwpad words, device
   const PassDesc *passes;        // npasses entries, device
   uint64_t seq;                  // serving: ticket of the code in this slot

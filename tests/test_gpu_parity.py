@@ -88,15 +88,19 @@ def test_bitslice_ops_on_device(p):
 
 # ------------------------------------------------- single workloads ----
 
+@pytest.mark.parametrize("pair", [1, 0])
 @pytest.mark.parametrize("name", ["f3_n30_k15", "f7_n40_k20", "f3_n80_k40"])
-def test_single_code_parity(name):
+def test_single_code_parity(name, pair):
+    """Both leaf forms (pair leaves: the last two rows from the pair table;
+    one-row leaves) against the oracle's stored values."""
     code = inputs.single(name)
     g = golden()[name]
     assert code.digest() == g["sha256"]
     for mode, kw in (("default", {}), ("paper_literal", {"per_round_check": 1, "defer": 0})):
         exp = g[mode]
         for mid in (1, 0):
-            res, _ = run(code, mid_pass_exit=mid, **kw)
+            res, pr = run(code, mid_pass_exit=mid, pair_leaves=pair, **kw)
+            assert (B.fpcode_test_pair_mode(pr) > 0) == bool(pair)
             assert res.status == B.OK
             assert (res.d, res.L, res.U, res.m, res.kj) == (exp["d"], exp["L"], exp["U"], exp["m"], exp["kj"])
             assert res.counts == exp["counts"]
@@ -108,11 +112,12 @@ def test_single_code_parity(name):
             check_witness(code, res.d, res.witness)
 
 
-def test_parity_mode_witness_is_deterministic():
+@pytest.mark.parametrize("pair", [1, 0])
+def test_parity_mode_witness_is_deterministic(pair):
     code = inputs.single("f7_n40_k20")
     ws = []
     for _ in range(3):
-        res, _ = run(code, mid_pass_exit=0)
+        res, _ = run(code, mid_pass_exit=0, pair_leaves=pair)
         ws.append(res.witness.tobytes())
     assert len(set(ws)) == 1
 
@@ -163,10 +168,11 @@ def test_mersenne_prime_kernels_parity(p, n, k, budget):
 def test_random_codes_parity(seed):
     """Random codes over several primes, word counts W = 1..4, rank-deficient
     last information sets, zero columns, k = 1 and k = n: same d, counts, L,
-    schedule as the oracle; a valid witness."""
+    schedule as the oracle; a valid witness.  Pair leaves for p = 3, 7 on
+    even seeds, one-row leaves on odd ones."""
     for code in _random_codes(1000 + seed, 17):
         r = oracle.bz(code, threads=4, budget=5 * 10 ** 7)
-        res, _ = run(code, mid_pass_exit=seed % 2, budget=5 * 10 ** 7)
+        res, _ = run(code, mid_pass_exit=seed % 2, budget=5 * 10 ** 7, pair_leaves=1 - seed % 2)
         assert res.status == status_of_oracle(r.status), (code.p, code.n, code.k)
         assert res.counts == r.counts
         assert (res.L, res.U) == (r.L, r.U)

@@ -305,7 +305,7 @@ def test_stored_rows_are_the_sliced_multiples(p, n, k, lib):
     slice i holds bit i of symbols 32w .. 32w + 31; for p = 3, 7 the pair
     signature of representative c holds bits y_i xor y_{i+1} of y = c A_j[t]."""
     code = inputs.single_code(77 + n, p, n, k)
-    pr = _prep(code)
+    pr = _prep(code, pair_leaves=0)  # the one-row-leaf tables (pair tables: test_stored_pair_table)
     m, _kj, _np, _c = B.fpcode_prepared_shape(pr)
     r = p.bit_length()
     W = -(-(n - k) // 32)
@@ -399,7 +399,7 @@ def test_task_ranges_tile_each_pass(ctas, fixed_pl, min_steps, lib):
     min_steps prefixes gets fewer tasks than CTAs, each (but the last)
     giving every lane at least min_steps prefixes."""
     code = inputs.single("f3_n80_k40")
-    pr = _prep(code)
+    pr = _prep(code, pair_leaves=0)  # one-row leaves (pair-leaf plans: test_pair_tasks_tile_each_pass)
     passes = B.fpcode_prepared_passes(pr)
     for i, (g, _j, _Lb, _La, _re, _size, nprefix) in enumerate(passes[:14]):
         if fixed_pl and nprefix > 256 * fixed_pl * 60000:
@@ -429,7 +429,7 @@ def test_guided_tasks_are_whole_rows_and_shrink(lib):
     units): every task but the pass's last holds whole rows, and task sizes
     never grow along the pass, ending on one-row tasks."""
     code = inputs.single("f3_n80_k40")
-    pr = _prep(code)
+    pr = _prep(code, pair_leaves=0)
     passes = B.fpcode_prepared_passes(pr)
     seen = 0
     for i, (g, _j, _Lb, _La, _re, _size, nprefix) in enumerate(passes[:14]):
@@ -497,7 +497,8 @@ def test_checkpoint_and_resume_validation(lib):
 
 def _code_hash(prep):
     """The code identity the library stores (FNV-1a of p, n, k, the two
-    schedule options and G), recomputed here from its definition."""
+    schedule options, whether pair leaves are taken, and G), recomputed here
+    from its definition."""
     h = 1469598103934665603
     def mix(v, nbytes=8):
         nonlocal h
@@ -505,8 +506,123 @@ def _code_hash(prep):
             h ^= (v >> (8 * b)) & 0xFF
             h = (h * 1099511628211) & 0xFFFFFFFFFFFFFFFF
     code = inputs.single("f7_n40_k20")
-    for v in (code.p, code.n, code.k, 0, 1):  # per_round_check 0, defer 1 (defaults)
+    for v in (code.p, code.n, code.k, 0, 1, 1):  # per_round_check 0, defer 1, pair leaves (defaults, F_7)
         mix(v)
     for byte in np.asarray(code.G, dtype=np.uint8).reshape(-1):
         mix(int(byte), 1)
     return h
+
+
+# ------------------------------------------------------------ pair leaves ----
+
+def _pair_key(pass_index, J, e, sign):
+    """The packed key of a pair-leaf codeword at weight 0 (its layout: pass
+    at bit 48, stem at bit 15, entry at bit 1, sign at bit 0)."""
+    return (pass_index << 48) | (J << 15) | (e << 1) | sign
+
+
+@pytest.mark.parametrize("p,n,k", [(3, 80, 40), (3, 30, 15), (7, 40, 20), (3, 50, 10), (7, 80, 20), (3, 140, 12)])
+def test_stored_pair_table(p, n, k, lib):
+    """Pair leaves: entry e of an information set's table holds the pair
+    signature (bits y_i xor y_{i+1} of every symbol) of B = A[y] + c A[x]
+    mod p, where the pairs run y = k-2 down to 0, x = y+1 up to k-1, and c
+    = 1 .. p-1 innermost; the words after the signature are zero; and
+    slice 0 (bit 0 of every symbol) of B."""
+    code = inputs.single_code(5 + n, p, n, k)
+    pr = _prep(code)
+    sigp = B.fpcode_test_pair_mode(pr)
+    assert sigp > 0
+    m, _kj, _np, _c = B.fpcode_prepared_shape(pr)
+    r = p.bit_length()
+    W = -(-(n - k) // 32)
+
+    def sliced(vals, nbits):
+        out = []
+        for w in range(W):
+            for i in range(nbits):
+                out.append(sum(((int(vals[32 * w + bb]) >> i) & 1) << bb
+                               for bb in range(32) if 32 * w + bb < len(vals)))
+        return out
+
+    rng = np.random.default_rng(k)
+    for j in range(m):
+        gam, piv = B.fpcode_prepared_gamma(pr, j)
+        red = [c for c in range(n) if c not in set(piv)]
+        A = [[int(gam[t, c]) for c in red] for t in range(k)]
+        order = [(y, x, c) for y in range(k - 2, -1, -1) for x in range(y + 1, k) for c in range(1, p)]
+        picks = range(len(order)) if len(order) <= 400 else rng.choice(len(order), 400, replace=False)
+        for e in picks:
+            y, x, c = order[e]
+            Bv = [(A[y][i] + c * A[x][i]) % p for i in range(n - k)]
+            want = sliced([(q ^ (q >> 1)) & ((1 << (r - 1)) - 1) for q in Bv], r - 1)
+            got = B.fpcode_test_pair_entry(pr, j, int(e))
+            assert len(got) == sigp + W
+            assert got[:len(want)] == want and not any(got[len(want):sigp]), (j, e)
+            assert got[sigp:] == sliced([q & 1 for q in Bv], 1), (j, e)
+
+
+def test_pair_mode_selection(lib):
+    """Pair leaves are taken for p = 3, 7 with k >= 3 when a set's pair
+    table fits 40 KiB, and never when switched off, for other primes, or for
+    k < 3."""
+    def mode(p, n, k, **kw):
+        return B.fpcode_test_pair_mode(_prep(inputs.single_code(9, p, n, k), **kw))
+    assert mode(3, 80, 40) == 2 and mode(7, 40, 20) == 2 and mode(3, 30, 15) == 1
+    assert mode(3, 80, 40, pair_leaves=0) == 0
+    assert mode(5, 40, 20) == 0 and mode(11, 30, 10) == 0 and mode(31, 40, 8) == 0
+    assert mode(3, 10, 2) == 0
+    assert mode(7, 100, 40) == 0  # 6 C(40,2) entries of 4 words: 75 KiB
+    assert mode(3, 160, 64) == 0  # 2 C(64,2) entries of 4 words: 64 KiB
+
+
+@pytest.mark.parametrize("p,k", [(3, 5), (3, 7), (7, 5), (7, 6)])
+def test_pair_pass_enumerates_each_class_once(p, k, lib):
+    """Every pass of a pair-leaf schedule visits each projective class of
+    codewords with exactly g nonzero coefficients once: over the stems J of
+    the pass, the entries the stem is evaluated against (hook: those with y
+    above the stem's largest row), and both signs (one for g = 2), the keys
+    decode to coefficient vectors that are pairwise inequivalent and number
+    C(k, g) (p-1)^(g-1)."""
+    rng = np.random.default_rng(k)
+    A = rng.integers(0, p, size=(k, k), dtype=np.uint8)
+    code = inputs.systematic(p, 2 * k, k, A)
+    pr = _prep(code, budget=0, defer=0)
+    assert B.fpcode_test_pair_mode(pr) > 0
+    inv = {a: pow(a, p - 2, p) for a in range(1, p)}
+    for i, (g, j, _Lb, _La, _re, size, nstems) in enumerate(B.fpcode_prepared_passes(pr)):
+        if g < 2:
+            continue
+        seen = set()
+        for J in range(nstems):
+            _w, E = B.fpcode_test_pair_mode(pr, i, J)
+            for e in range(E):
+                for sign in ((0, 1) if g >= 3 else (0,)):
+                    got = B.fpcode_test_key_coefficients(pr, _pair_key(i, J, e, sign))
+                    assert got is not None and got[0] == g and got[1] == j
+                    coef = got[2]
+                    assert sum(1 for c in coef if c) == g
+                    lead = next(c for c in coef if c)
+                    cls = tuple(c * inv[lead] % p for c in coef)  # first nonzero coefficient 1
+                    assert cls not in seen, (i, J, e, sign)
+                    seen.add(cls)
+        assert len(seen) == size == math.comb(k, g) * (p - 1) ** (g - 1)
+
+
+@pytest.mark.parametrize("name", ["f3_n80_k40", "f7_n40_k20", "f3_n30_k15"])
+@pytest.mark.parametrize("ctas", [608, 152, 7, 1])
+def test_pair_tasks_tile_each_pass(name, ctas, lib):
+    """The pair-leaf plan's tasks cover every stem of a pass exactly once and
+    in order, and the work per task shrinks toward the end of the pass
+    (guided by work): the last task is no larger than the first."""
+    pr = _prep(inputs.single(name))
+    passes = B.fpcode_prepared_passes(pr)
+    for i, (g, _j, _Lb, _La, _re, _size, nstems) in enumerate(passes[:14]):
+        if g < 2:
+            continue
+        ranges = B.fpcode_test_task_ranges(pr, i, ctas, 0, 8)
+        assert 0 < len(ranges) < 1 << 16
+        pos = 0
+        for lo, hi in ranges:
+            assert lo == pos and hi > lo, (i, lo, hi, pos)
+            pos = hi
+        assert pos == nstems
