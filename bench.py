@@ -1,35 +1,41 @@
-"""Benchmark: certified minimum distance on one GB300 (or N replicas).
+"""Benchmark: certified minimum distance on one GB300 (or N GPUs).
 
-One step certifies d of the workload code once, the whole hot path
-(every pass of the Brouwer-Zimmermann search, Sec. 3.1 Alg. 6, on the
-device).  Default workload: the F_3 [80,40] random systematic code
-(PCG64 seed 2), the largest single-code configuration.
+One step certifies d of the headline code once, the whole hot path (every
+pass of the Brouwer-Zimmermann search, Sec. 3.1 Alg. 6, on the device).
+Default workload: the F_3 [80,40] random systematic code (PCG64 seed 2),
+the largest single-code configuration.
 
 value     codewords/s of the device search with the code's tables already
-          resident in HBM (CUDA events around each step; L2 flushed between
-          steps with a 256 MiB memset outside the timed windows).
-e2e       the same metric through fpcode_min_distance() from a host matrix:
-          host preparation, H2D, search, D2H read-back of the result.
-roofline  the enumeration kernel against the POPC issue ceiling of the SMs
-          (16 POPC lane-ops per clock per SM at the maximum SM clock).
+          resident in HBM (CUDA events around each step, on the search's
+          stream; L2 flushed between steps with a 256 MiB memset outside the
+          timed windows).
+e2e       the same metric through fpcode_min_distance() from a pinned host
+          matrix: host preparation, H2D, search, D2H read-back of the result.
+roofline  the enumeration kernel against the POPC issue ceiling of the SMs:
+          the rate fpcode_int_peaks() measures (POPC lanes per clock per SM)
+          x SMs x the median SM clock sampled during the timed region.
 cpu_baseline  the CPU oracle (test infrastructure) on the same code, all
           host cores.
 
-Two further workloads have their own JSON line (not the default):
-  --workload batch512  512 random codes (p in {3,7}, n in 24..64, PCG64 seed 3)
-                       certified in one persistent launch
-                       (fpcode_min_distance_batch) vs one launch per code;
-                       codes/s end to end from host matrices, per-code
-                       budget --budget codewords (pass-granular).
-  --workload serve     the first --requests of 10,000 codes (p in {3,5,7},
-                       n in 20..72, PCG64 seed 4) arriving as a Poisson
-                       process at 200 requests/s, served continuously
-                       (fpcode_serve_*); codes/s and p50/p99 latency from
-                       arrival to result.
+The default line also carries the other configurations at their stated
+sizes, each measured in the same run:
+  f7_n40_k20  the F_7 [40,20] code (PCG64 seed 1): certified search time,
+              codewords/s, roofline fraction, and one long pass alone;
+  batch512    512 random codes (p in {3,7}, n in 24..64, PCG64 seed 3) in
+              persistent launches (fpcode_min_distance_batch) against one
+              launch per code, codes/s from host matrices, per-code budget
+              --budget codewords;
+  serve       10 000 codes (p in {3,5,7}, n in 20..72, PCG64 seed 4)
+              arriving as a Poisson process at 200 requests/s, served with
+              continuous batching (fpcode_serve_*): codes/s and latency from
+              arrival to result (p50, p90, p99, max).
+
+Further workloads have their own line (--workload): the single-pass probes,
+the additions benchmark of Sec. 5.1, and each extra above alone.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W]
                        [--impl ours|reference] [--workload NAME]
-                       [--budget B] [--requests R]
+                       [--budget B] [--requests R] [--no-extras]
 """
 from __future__ import annotations
 
@@ -56,9 +62,12 @@ WORKLOADS = {
     "probe_f7_n40_k20_g7": "one pass (g=7, Gamma_1) of the F_7 [40,20] code alone, termination off, U seeded at d: "
                            "C(20,7) 6^6 = 3 616 773 120 codewords",
     "batch512": "512 random codes, p in {3,7}, n in {24,...,64}, k = round(r n), r ~ U[1/3,2/3], PCG64 seed 3",
-    "serve": "Poisson arrivals (200/s) of random codes, p in {3,5,7}, n ~ U[20,72], k ~ U[n/3,2n/3], PCG64 seed 4",
+    "serve": "Poisson arrivals (200/s) of 10 000 random codes, p in {3,5,7}, n ~ U[20,72], k ~ U[n/3,2n/3], "
+             "PCG64 seed 4",
 }
-POPC_PER_CLK_SM = 16.0   # measured by fpcode_int_peaks on GB300 (and CUDA's documented rate)
+PROBES = {"probe_f3_n80_k40_g8": ("f3_n80_k40", 8), "probe_f7_n40_k20_g7": ("f7_n40_k20", 7)}
+ADDITIONS = {"additions_f3": 3, "additions_f7": 7}
+FLUSH_BYTES = 256 << 20
 
 # DRAM bytes of one bz_kernel launch per workload, from one ncu capture of
 # that workload (dram__bytes_read.sum + dram__bytes_write.sum, summarised
@@ -66,10 +75,7 @@ POPC_PER_CLK_SM = 16.0   # measured by fpcode_int_peaks on GB300 (and CUDA's doc
 # version that was profiled; any later change of their code reports null
 # (the hash skips comments and blank lines).
 KERNEL_SOURCES = ["fp_kernel.cuh", "fp_enum.cuh", "fp_bitslice.cuh", "fp_types.h"]
-PROFILED_TRAFFIC = {
-    "f3_n80_k40": {"sources_sha256": "407c689695f68215a8fbed688a9488cef947ab5ba5c26d6eefd060789e737205",
-                   "bytes": 89600},
-}
+PROFILED_TRAFFIC: dict = {}
 
 
 def code_of(text: str) -> str:
@@ -85,7 +91,7 @@ def kernel_sources_sha256() -> str:
     import hashlib
 
     h = hashlib.sha256()
-    root = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2603_29942_gb300", "csrc")
+    root = os.path.join(ROOT, "paper_2603_29942_gb300", "csrc")
     for f in KERNEL_SOURCES:
         with open(os.path.join(root, f), encoding="utf-8") as fh:
             h.update(code_of(fh.read()).encode())
@@ -97,8 +103,9 @@ def profiled_traffic(workload: str):
     if rec and rec["sources_sha256"] == kernel_sources_sha256():
         return rec["bytes"]
     return None
-SM_MAX_MHZ = 2070.0      # GB300 maximum SM clock
 
+
+# ----------------------------------------------------------- processes ----
 
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
@@ -130,8 +137,7 @@ def shard(n: int, rank: int, world: int) -> range:
     return range(lo, lo + base + (1 if rank < extra else 0))
 
 
-def sum_over_ranks(x: float, world: int) -> float:
-    """The total of a per-rank count over all ranks."""
+def _reduce(x: float, world: int, op: str) -> float:
     if world <= 1:
         return float(x)
     import torch
@@ -139,22 +145,19 @@ def sum_over_ranks(x: float, world: int) -> float:
 
     dev = torch.device("cuda") if dist.get_backend() == "nccl" else torch.device("cpu")
     t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM if op == "sum" else dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def sum_over_ranks(x: float, world: int) -> float:
+    """The total of a per-rank count over all ranks."""
+    return _reduce(x, world, "sum")
 
 
 def max_over_ranks(x: float, world: int) -> float:
     """The largest value over all ranks (a job takes as long as its slowest
     rank); barrier semantics come with the collective."""
-    if world <= 1:
-        return float(x)
-    import torch
-    import torch.distributed as dist
-
-    dev = torch.device("cuda") if dist.get_backend() == "nccl" else torch.device("cpu")
-    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    return _reduce(x, world, "max")
 
 
 class ClockSampler:
@@ -195,25 +198,32 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self) -> dict:
-        mhz, mx, reasons = [], 0.0, set()
+        """Median SM clock over the samples taken under load (power above the
+        idle floor or clock above a quarter of the maximum), the maximum clock,
+        and every throttle reason seen."""
+        rows, mx, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             parts = [x.strip() for x in ln.split(",")]
             if len(parts) < 9:
                 continue
             try:
-                mhz.append(float(parts[1]))
+                rows.append((float(parts[1]), float(parts[3])))
                 mx = max(mx, float(parts[2]))
             except ValueError:
                 continue
             for nm, v in zip(names, parts[5:9]):
                 if v.lower() == "active":
                     reasons.add(nm)
+        loaded = [c for c, _p in rows if c > 0.25 * mx] if mx else []
+        mhz = loaded or [c for c, _p in rows]
         return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx or None,
-                "reasons": sorted(reasons), "samples": len(mhz)}
+                "reasons": sorted(reasons), "samples": len(rows), "samples_under_load": len(loaded)}
 
 
-def cpu_baseline(code, budget_s: float = 30.0) -> dict:
+# ------------------------------------------------------------- CPU arms ----
+
+def cpu_baseline(code) -> dict:
     """The oracle as it stands, on every host core, on the same code."""
     import oracle
 
@@ -226,8 +236,18 @@ def cpu_baseline(code, budget_s: float = 30.0) -> dict:
             "d": r.d, "seconds": dt}
 
 
-def run_reference(args, code, rank: int):
-    """Reference arm: the CPU oracle on the host cores, same metric."""
+def single_config(name: str, d=None) -> dict:
+    """The config dict of a single-code workload, the same in both arms."""
+    cfg = {"workload": name, "description": WORKLOADS[name], "l2": "flushed between timed steps (256 MiB memset)",
+           "parallelism": "single GPU"}
+    if d is not None:
+        cfg["d"] = d
+    return cfg
+
+
+def run_reference(args, code, rank: int, world: int):
+    """Reference arm: the CPU oracle on the host cores, same metric and config
+    (rank 0 only; the other ranks exit without work)."""
     if rank != 0:
         return
     import oracle
@@ -243,17 +263,21 @@ def run_reference(args, code, rank: int):
         ev = r.evaluated
     total = sum(times)
     value = ev * args.steps / total
+    cfg = single_config(args.workload, r.d)
+    cfg["parallelism"] = "replicas" if world > 1 else "single GPU"
     line = {
         "impl": "reference", "metric": "codewords_per_s", "value": value, "unit": "codewords/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "d": r.d},
+        "config": cfg,
         "cpu_baseline": {"value": value, "unit": "codewords/s", "cores": threads, "kind": "oracle",
                          "sample": f"full certified search of the same code per step ({ev} codewords)"},
         "e2e": {"value": value, "unit": "codewords/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
+
+# -------------------------------------------------------------- the GPU ----
 
 def _cuda(local):
     import torch
@@ -267,8 +291,387 @@ def _cuda(local):
     return torch, B
 
 
-PROBES = {"probe_f3_n80_k40_g8": ("f3_n80_k40", 8), "probe_f7_n40_k20_g7": ("f7_n40_k20", 7)}
-ADDITIONS = {"additions_f3": 3, "additions_f7": 7}
+def popc_peak(B, stream, sm_mhz, sms) -> dict:
+    """The POPC ceiling: lanes per clock per SM measured by fpcode_int_peaks
+    (independent chains on every SM) x SMs x the SM clock sampled under load
+    (the microbenchmark's own clock if none was sampled)."""
+    rates = B.fpcode_int_peaks(stream)
+    mhz = sm_mhz or rates["sm_mhz"]
+    per_clk = rates["popc_per_clk_sm"]
+    return {"tpopc_s": per_clk * sms * mhz * 1e6 / 1e12, "popc_per_clk_sm": per_clk,
+            "lop3_per_clk_sm": rates["lop3_per_clk_sm"], "sm_mhz": mhz, "sms": sms,
+            "basis": f"fpcode_int_peaks: {per_clk:.2f} POPC/clk/SM x {sms} SMs x {mhz:.0f} MHz (median under load)"}
+
+
+def time_search(torch, B, prep, stream, steps, warmup, flush, want_d=None):
+    """Device-timed certified searches on resident tables: CUDA events on the
+    search's stream around each enqueue, L2 flushed outside the windows.
+    Returns (event ms per step, kernel ms per step, last result)."""
+    for _ in range(warmup):
+        B.fpcode_search_enqueue(prep, stream)
+        res = B.fpcode_search_finish(prep, stream, want_witness=False)
+    assert res.status == B.OK and (want_d is None or res.d == want_d)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    kern = []
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for i in range(steps):
+            flush.fill_(i & 0xFF)  # L2 flush, outside the timed window
+            evs[i][0].record(stream)
+            B.fpcode_search_enqueue(prep, stream)
+            evs[i][1].record(stream)
+            r = B.fpcode_search_finish(prep, stream, want_witness=(i == steps - 1))
+            assert r.status == B.OK and r.d == res.d
+            kern.append(r.t_kernel_ms)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs], kern, r
+
+
+def time_pass(torch, B, pr, idx, d, stream, steps, warmup, flush):
+    """Time pass `idx` of prepared code `pr` alone (U seeded at d), L2
+    flushed between steps.  Returns (total event ms, mean kernel ms, least
+    weight found in the pass)."""
+    g, size = B.fpcode_prepared_passes(pr)[idx][0], B.fpcode_prepared_passes(pr)[idx][5]
+    probe = B.fpcode_prepared_single_pass(pr, idx, d)
+    B.fpcode_prepared_upload(probe, stream)
+    for _ in range(warmup):
+        B.fpcode_search_enqueue(probe, stream)
+        r = B.fpcode_search_finish(probe, stream, want_witness=False)
+    assert r.counts[g] == size
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    kern = []
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for i in range(steps):
+            flush.fill_(i & 0xFF)
+            evs[i][0].record(stream)
+            B.fpcode_search_enqueue(probe, stream)
+            evs[i][1].record(stream)
+            r = B.fpcode_search_finish(probe, stream, want_witness=False)
+            assert r.counts[g] == size
+            kern.append(r.t_kernel_ms)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs), statistics.mean(kern), r.U
+
+
+def probe_prepare(B, code):
+    """The code prepared for a single-pass probe: the full schedule, with the
+    leaf form the library's own rule gives a search of the timed pass's size
+    (pair leaves from 10^8 codewords on, where they fit)."""
+    return B.fpcode_prepare(code.p, code.n, code.k, code.G, B.fpcode_opts_default(budget=0, pair_leaves=1))
+
+
+def probe_line(torch, B, code, name, g, d, stream, flush, peak_t, steps=5, warmup=3) -> dict:
+    """The kernel's steady state: one long pass of fixed, closed-form size
+    alone, termination off, U seeded at d (the threshold a certified search
+    has at that level)."""
+    pr = probe_prepare(B, code)
+    passes = B.fpcode_prepared_passes(pr)
+    idx = next(i for i, x in enumerate(passes) if x[0] == g and x[1] == 0)
+    size = passes[idx][5]
+    t_ms, k_ms, least = time_pass(torch, B, pr, idx, d, stream, steps, warmup, flush)
+    W = max(1, -(-(code.n - code.k) // 32))
+    ach = size * W / (k_ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": ach, "peak": peak_t, "unit": "Tpopc/s", "frac": ach / peak_t,
+            "pass": [g, 0], "codewords": size, "kernel_ms": k_ms, "workload": name,
+            "leaf_form": "pair" if B.fpcode_test_pair_mode(pr) else "one-row", "least_weight_in_pass": least,
+            "note": "the same kernel on one pass of fixed size alone, termination off, U seeded at d"}
+
+
+def single_code(args, torch, B, name, stream, flush, world, clk_need=True):
+    """One certified single-code workload: device-timed steps and the kernel
+    time of each.  Returns a dict of the measurements."""
+    from paper_2603_29942_gb300 import inputs
+
+    code = inputs.single(name)
+    prep = B.fpcode_prepare(code.p, code.n, code.k, code.G)
+    B.fpcode_prepared_upload(prep, stream)
+    steps_ms, kern, r = time_search(torch, B, prep, stream, args.steps, args.warmup, flush)
+    W = max(1, -(-(code.n - code.k) // 32))
+    return {"code": code, "prep": prep, "res": r, "steps_ms": steps_ms, "kern_ms": kern, "W": W,
+            "codewords": r.enumerated, "counts_total": sum(r.counts),
+            "leaf_form": "pair" if B.fpcode_test_pair_mode(prep) else "one-row"}
+
+
+def e2e_line(torch, B, code, prep, stream, steps, world, counts_total):
+    """The same metric through the public call from a pinned host matrix:
+    preparation, H2D of the tables, search, D2H of the result each step."""
+    h2d, d2h = B.fpcode_prepared_bytes(prep)
+    G_host = torch.from_numpy(code.G.copy()).pin_memory().numpy()
+    for _ in range(3):
+        B.fpcode_min_distance(code.p, code.n, code.k, G_host, stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        d, _w = B.fpcode_min_distance(code.p, code.n, code.k, G_host, stream)
+    e2e_s = time.perf_counter() - t0
+    return {"value": world * counts_total * steps / e2e_s, "unit": "codewords/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s / steps, "d": d}
+
+
+def batch_measure(args, torch, B, rank, world) -> dict:
+    """512 codes: persistent batched launches vs one launch per code, end to
+    end from host matrices, the same per-code budget."""
+    from paper_2603_29942_gb300 import inputs
+
+    all_codes = inputs.batch_codes(512)
+    codes = [all_codes[i] for i in shard(len(all_codes), rank, world)]  # codes are independent: no exchange
+    budget = int(args.budget)
+    budgets = [budget] * len(codes)
+    stream = torch.cuda.Stream()
+    # launch settings chosen by measurement on this GPU (outside the timed region)
+    tuning = B.fpcode_autotune_batch(codes, stream, budgets=budgets, reps=2)
+    opts = tuning.pop("opts")
+    for _ in range(2):
+        res = B.fpcode_min_distance_batch(codes, stream, opts=opts, budgets=budgets, want_witness=False)
+    torch.cuda.synchronize()
+    max_over_ranks(0.0, world)  # barrier
+    reps = 3
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        res = B.fpcode_min_distance_batch(codes, stream, opts=opts, budgets=budgets, want_witness=True)
+    torch.cuda.synchronize()
+    t_batch = max_over_ranks((time.perf_counter() - t0) / reps, world)
+    launches = sorted({r.launch for r in res})
+    kernel_ms = sum(next(r.t_kernel_ms for r in res if r.launch == L) for L in launches)
+    t0 = time.perf_counter()
+    for c in codes:
+        B.fpcode_min_distance_batch([c], stream, opts=opts, budgets=[budget], want_witness=True)
+    torch.cuda.synchronize()
+    t_single = max_over_ranks(time.perf_counter() - t0, world)
+    certified = int(sum_over_ranks(sum(r.status == B.OK for r in res), world))
+    work = int(sum_over_ranks(sum(r.enumerated for r in res), world))
+    return {"codes_per_s": len(all_codes) / t_batch, "ms_per_batch": 1e3 * t_batch, "budget_per_code": budget,
+            "certified": certified, "budget_limited": len(all_codes) - certified, "codewords": work,
+            "kernel_ms": kernel_ms, "launches_per_batch": len(launches),
+            "per_code": {"codes_per_s": len(all_codes) / t_single, "ms_total": 1e3 * t_single,
+                         "form": "fpcode_min_distance_batch on one code at a time (one launch per code)"},
+            "batched_over_per_code": t_single / t_batch,
+            "tuning": tuning,
+            "timing": "end to end from host matrices (host preparation on all cores, H2D, launches, D2H), "
+                      f"mean of {reps} batches",
+            "shard": "the 512 codes split into contiguous blocks, one per rank" if world > 1 else "one GPU"}
+
+
+def serve_measure(args, torch, B, n_req=None) -> dict:
+    """Continuous batching of Poisson arrivals; latency from arrival to result."""
+    from paper_2603_29942_gb300 import inputs
+
+    codes, arrivals = inputs.serve_codes()
+    n_req = min(n_req or args.requests, len(codes))
+    codes, arrivals = codes[:n_req], arrivals[:n_req]
+    budget = int(args.budget)
+    stream = torch.cuda.Stream()
+    srv = B.fpcode_serve_create(B.fpcode_serve_opts_default(slots=128), stream)
+    for c in codes[:8]:  # warm-up: a few codes through the server
+        B.fpcode_serve_submit(srv, c, budget=budget)
+    B.fpcode_serve_drain(srv)
+    B.fpcode_serve_poll(srv)
+    relaunch0 = B.fpcode_serve_launches(srv)
+    pending = list(range(n_req))
+    ticket_of, done_at, results = {}, {}, {}
+    t0 = time.perf_counter()
+    while len(done_at) < n_req:
+        now = time.perf_counter() - t0
+        while pending and arrivals[pending[0]] <= now:
+            i = pending[0]
+            t = B.fpcode_serve_submit(srv, codes[i], budget=budget)
+            if t is None:
+                break  # no slot or memory free: the request waits (its latency runs)
+            ticket_of[t] = i
+            pending.pop(0)
+        for t, r in B.fpcode_serve_poll(srv, want_witness=False):
+            i = ticket_of.pop(t)
+            done_at[i] = time.perf_counter() - t0
+            results[i] = r
+        if not pending and not ticket_of:
+            break
+        time.sleep(0.0002)
+    elapsed = time.perf_counter() - t0
+    launches = B.fpcode_serve_launches(srv) - relaunch0
+    B.fpcode_serve_destroy(srv)
+    lat = sorted((done_at[i] - arrivals[i]) * 1e3 for i in done_at)
+    pct = lambda q: lat[min(len(lat) - 1, int(q * len(lat)))]
+    return {"codes_per_s": n_req / elapsed, "requests": n_req, "seconds": elapsed, "budget_per_code": budget,
+            "certified": sum(r.status == B.OK for r in results.values()), "arrival_span_s": float(arrivals[-1]),
+            "latency_ms": {"p50": pct(0.50), "p90": pct(0.90), "p99": pct(0.99), "max": lat[-1]},
+            "gpu_launches": launches}
+
+
+# ------------------------------------------------------------ workloads ----
+
+def run_default(args, rank, world, local):
+    """The headline single code, with the other configurations as extra keys."""
+    from paper_2603_29942_gb300 import inputs
+
+    code = inputs.single(args.workload)
+    if args.impl == "reference":
+        return run_reference(args, code, rank, world)
+    torch, B = _cuda(local)
+    dist_init(world, local)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+
+    # --- value: device search on resident tables (the timed region) ---
+    if world > 1:
+        torch.distributed.barrier()
+    with ClockSampler(local) as clk:
+        head = single_code(args, torch, B, args.workload, stream, flush, world)
+        if world > 1:
+            torch.distributed.barrier()
+    clocks = clk.summary()
+    t_ms = max_over_ranks(sum(head["steps_ms"]), world)
+    value = world * head["codewords"] * args.steps / (t_ms * 1e-3)
+    e2e = e2e_line(torch, B, head["code"], head["prep"], stream, args.steps, world, head["counts_total"])
+
+    # --- roofline of the enumeration kernel (peak measured, at the sampled clock) ---
+    peak = popc_peak(B, stream, clocks["sm_mhz"], sms)
+    kern_ms = statistics.mean(head["kern_ms"])
+    W = head["W"]
+    ach = head["codewords"] * W / (kern_ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "achieved": ach, "peak": peak["tpopc_s"], "unit": "Tpopc/s", "frac": ach / peak["tpopc_s"],
+            "traffic": profiled_traffic(args.workload), "kernel": "bz_kernel", "ops_per_codeword": W,
+            "kernel_ms": kern_ms, "peak_basis": peak["basis"], "peak_of": "measured",
+            "leaf_form": head["leaf_form"]}
+    probe_of = {v[0]: (k, v[1]) for k, v in PROBES.items()}
+    roof_probe = None
+    if args.workload in probe_of:
+        pname, pg = probe_of[args.workload]
+        roof_probe = probe_line(torch, B, head["code"], pname, pg, head["res"].d, stream, flush, peak["tpopc_s"])
+
+    line = {
+        "metric": "codewords_per_s", "value": value, "unit": "codewords/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": single_config(args.workload, head["res"].d) | {
+            "parallelism": "replicas" if world > 1 else "single GPU"},
+        "time_to_certified_d_ms": t_ms / args.steps, "codewords_per_step": head["codewords"],
+        "schedule_codewords": head["counts_total"],
+        "roofline": roof, "roofline_pass_probe": roof_probe, "e2e": e2e,
+        "gpu_launches": args.steps, "clocks": clocks,
+    }
+
+    # --- the other configurations, each at its stated size ---
+    if not args.no_extras:
+        extras = {}
+        name7 = "f7_n40_k20"
+        if args.workload != name7:
+            f7 = single_code(args, torch, B, name7, stream, flush, world)
+            k7 = statistics.mean(f7["kern_ms"])
+            t7 = max_over_ranks(sum(f7["steps_ms"]), world) / args.steps
+            a7 = f7["codewords"] * f7["W"] / (k7 * 1e-3) / 1e12
+            extras[name7] = {
+                "d": f7["res"].d, "time_to_certified_d_ms": t7, "kernel_ms": k7,
+                "codewords_per_step": f7["codewords"], "codewords_per_s": world * f7["codewords"] / (t7 * 1e-3),
+                "roofline": {"bound": "alu", "achieved": a7, "peak": peak["tpopc_s"], "unit": "Tpopc/s",
+                             "frac": a7 / peak["tpopc_s"], "ops_per_codeword": f7["W"], "leaf_form": f7["leaf_form"]},
+                "roofline_pass_probe": probe_line(torch, B, f7["code"], "probe_f7_n40_k20_g7", 7, f7["res"].d, stream,
+                                                  flush, peak["tpopc_s"]),
+                "gpu_launches": args.steps}
+        extras["batch512"] = batch_measure(args, torch, B, rank, world)
+        if rank == 0:
+            extras["serve"] = serve_measure(args, torch, B)
+        line["extras"] = extras
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(head["code"])
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_probe(args, rank, world, local):
+    """Kernel efficiency on one pass of fixed, closed-form size (no early
+    termination): the pass runs alone, every task to the end, with the record
+    threshold a certified search has at that level (U = d)."""
+    from paper_2603_29942_gb300 import inputs
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle is timed on the certified "
+                              "single-code searches; a single pass has no reference arm"}))
+        return
+    from paper_2603_29942_gb300 import inputs
+
+    torch, B = _cuda(local)
+    name, g = PROBES[args.workload]
+    code = inputs.single(name)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    d = B.fpcode_min_distance_ex(B.fpcode_prepare(code.p, code.n, code.k, code.G), stream).d
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    with ClockSampler(local) as clk:
+        pr = probe_prepare(B, code)
+        passes = B.fpcode_prepared_passes(pr)
+        idx = next(i for i, x in enumerate(passes) if x[0] == g and x[1] == 0)
+        size = passes[idx][5]
+        t_ms, kern_ms, least = time_pass(torch, B, pr, idx, d, stream, args.steps, args.warmup, flush)
+    clocks = clk.summary()
+    peak = popc_peak(B, stream, clocks["sm_mhz"], sms)
+    W = max(1, -(-(code.n - code.k) // 32))
+    achieved = size * W / (kern_ms * 1e-3) / 1e12
+    line = {
+        "metric": "codewords_per_s", "value": world * size * args.steps / (t_ms * 1e-3), "unit": "codewords/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "pass": [g, 0],
+                   "codewords_per_step": size, "u_seed": d, "least_weight_in_pass": least,
+                   "l2": "flushed between timed steps (256 MiB memset)", "parallelism": "single GPU"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak["tpopc_s"], "unit": "Tpopc/s",
+                     "frac": achieved / peak["tpopc_s"], "traffic": profiled_traffic(args.workload),
+                     "kernel": "bz_kernel", "ops_per_codeword": W, "peak_basis": peak["basis"], "peak_of": "measured"},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_batch(args, rank, world, local):
+    """512 codes: persistent batched launches vs one launch per code."""
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle is timed on the single-code "
+                              "workloads only; batch512 has no reference arm"}))
+        return
+    torch, B = _cuda(local)
+    dist_init(world, local)
+    with ClockSampler(local) as clk:
+        b = batch_measure(args, torch, B, rank, world)
+    line = {
+        "metric": "codes_per_s", "value": b["codes_per_s"], "unit": "codes/s", "n_gpus": world, "steps": 3,
+        "warmup": 2, "ms_per_step": b["ms_per_batch"], "higher_is_better": True,
+        "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "batch512", "description": WORKLOADS["batch512"]},
+        "batch512": b, "batched_over_per_code": b["batched_over_per_code"],
+        "gpu_launches": 3 * b["launches_per_batch"], "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_serve(args, rank, world, local):
+    """Continuous batching of Poisson arrivals; latency from arrival to result."""
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle is timed on the single-code "
+                              "workloads only; serve has no reference arm"}))
+        return
+    if rank != 0:
+        return  # one request stream, served by one GPU (the other ranks hold none)
+    torch, B = _cuda(local)
+    with ClockSampler(local) as clk:
+        s = serve_measure(args, torch, B)
+    line = {
+        "metric": "codes_per_s", "value": s["codes_per_s"], "unit": "codes/s", "n_gpus": 1,
+        "steps": 1, "warmup": 1, "ms_per_step": 1e3 * s["seconds"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "serve", "description": WORKLOADS["serve"], "requests": s["requests"],
+                   "budget_per_code": s["budget_per_code"]},
+        "serve": s, "latency_ms": s["latency_ms"], "gpu_launches": s["gpu_launches"], "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
 
 
 def run_additions(args, rank, world, local):
@@ -292,11 +695,12 @@ def run_additions(args, rank, world, local):
     b = rng.integers(0, p, size=(nvec, nsym), dtype=np.uint8)
     want = ((a.astype(np.int64) + reps * b.astype(np.int64)) % p).astype(np.uint8)
     rates, times = {}, {}
+    steps = max(1, min(args.steps, 5))
     with ClockSampler(local) as clk:
         for form, sliced in (("sliced", True), ("bytes", False)):
             B.fpcode_bench_additions(p, a[:64], b[:64], 10, sliced)  # warm-up
             ms = []
-            for _ in range(max(1, min(args.steps, 5))):
+            for _ in range(steps):
                 out, t = B.fpcode_bench_additions(p, a, b, reps, sliced)
                 assert np.array_equal(out, want)
                 ms.append(t)
@@ -304,205 +708,16 @@ def run_additions(args, rank, world, local):
             rates[form] = nvec * nsym * reps / (times[form] * 1e-3)
     line = {
         "metric": "symbol_additions_per_s", "value": rates["sliced"], "unit": "symbol additions/s", "n_gpus": 1,
-        "steps": max(1, min(args.steps, 5)), "warmup": 1, "ms_per_step": times["sliced"], "higher_is_better": True,
+        "steps": steps, "warmup": 1, "ms_per_step": times["sliced"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": args.workload, "p": p, "vectors": nvec, "symbols": nsym, "repetitions": reps,
                    "form": "bit-sliced natural encoding, 32 symbols per word and slice; repetitions chained",
                    "bytes_form_ms": times["bytes"], "bytes_form_symbol_additions_per_s": rates["bytes"],
                    "sliced_over_bytes": times["bytes"] / times["sliced"], "checked": "a + reps*b mod p, every symbol"},
-        "gpu_launches": 2 * max(1, min(args.steps, 5)),
+        "gpu_launches": 2 * steps,
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
-
-
-def time_pass(torch, B, code, pr, idx, d, stream, steps, warmup):
-    """Time pass `idx` of prepared code `pr` alone (U seeded at d), L2
-    flushed between steps.  Returns (total event ms, mean kernel ms, least
-    weight found in the pass)."""
-    g, size = B.fpcode_prepared_passes(pr)[idx][0], B.fpcode_prepared_passes(pr)[idx][5]
-    probe = B.fpcode_prepared_single_pass(pr, idx, d)
-    B.fpcode_prepared_upload(probe, stream)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    for _ in range(warmup):
-        B.fpcode_search_enqueue(probe, stream)
-        r = B.fpcode_search_finish(probe, stream, want_witness=False)
-    assert r.counts[g] == size
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    kern = []
-    torch.cuda.synchronize()
-    with torch.cuda.stream(stream):
-        for i in range(steps):
-            flush.fill_(i & 0xFF)
-            evs[i][0].record(stream)
-            B.fpcode_search_enqueue(probe, stream)
-            evs[i][1].record(stream)
-            r = B.fpcode_search_finish(probe, stream, want_witness=False)
-            assert r.counts[g] == size
-            kern.append(r.t_kernel_ms)
-    torch.cuda.synchronize()
-    return sum(a.elapsed_time(b) for a, b in evs), statistics.mean(kern), r.U
-
-
-def run_probe(args, rank, world, local):
-    """Kernel efficiency on one pass of fixed, closed-form size (no early
-    termination): the pass runs alone, every task to the end, with the record
-    threshold a certified search has at that level (U = d)."""
-    from paper_2603_29942_gb300 import inputs
-
-    if args.impl == "reference":
-        if rank == 0:
-            print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle is timed on the certified "
-                              "single-code searches; a single pass has no reference arm"}))
-        return
-    torch, B = _cuda(local)
-    name, g = PROBES[args.workload]
-    code = inputs.single(name)
-    stream = torch.cuda.Stream()
-    full = B.fpcode_prepare(code.p, code.n, code.k, code.G)
-    d = B.fpcode_min_distance_ex(full, stream).d  # the bound a certified search ends with
-    pr = B.fpcode_prepare(code.p, code.n, code.k, code.G, B.fpcode_opts_default(budget=0))
-    passes = B.fpcode_prepared_passes(pr)
-    idx = next(i for i, x in enumerate(passes) if x[0] == g and x[1] == 0)
-    size = passes[idx][5]
-    with ClockSampler(local) as clk:
-        t_ms, kern_ms, least = time_pass(torch, B, code, pr, idx, d, stream, args.steps, args.warmup)
-    W = max(1, -(-(code.n - code.k) // 32))
-    sms = torch.cuda.get_device_properties(local).multi_processor_count
-    peak = POPC_PER_CLK_SM * sms * SM_MAX_MHZ * 1e6 / 1e12
-    achieved = size * W / (kern_ms * 1e-3) / 1e12
-    line = {
-        "metric": "codewords_per_s", "value": world * size * args.steps / (t_ms * 1e-3), "unit": "codewords/s",
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "pass": [g, 0],
-                   "codewords_per_step": size, "u_seed": d, "least_weight_in_pass": least,
-                   "l2": "flushed between timed steps (256 MiB memset)", "parallelism": "single GPU"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tpopc/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "bz_kernel", "ops_per_codeword": W,
-                     "peak_basis": f"{POPC_PER_CLK_SM:.0f} POPC/clk/SM x {sms} SMs x {SM_MAX_MHZ:.0f} MHz"},
-        "gpu_launches": args.steps,
-        "clocks": clk.summary(),
-    }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-
-
-def run_batch(args, rank, world, local):
-    """512 codes: one persistent batched launch vs one launch per code."""
-    from paper_2603_29942_gb300 import inputs
-
-    if args.impl == "reference":
-        if rank == 0:
-            print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle is timed on the single-code "
-                              "workloads only; batch512 has no reference arm"}))
-        return
-    torch, B = _cuda(local)
-    dist_init(world, local)
-    all_codes = inputs.batch_codes(512)
-    codes = [all_codes[i] for i in shard(len(all_codes), rank, world)]  # codes are independent: no exchange
-    budget = int(args.budget)
-    budgets = [budget] * len(codes)
-    stream = torch.cuda.Stream()
-    for _ in range(args.warmup):
-        res = B.fpcode_min_distance_batch(codes, stream, budgets=budgets, want_witness=False)
-    torch.cuda.synchronize()
-    max_over_ranks(0.0, world)  # barrier
-    with ClockSampler(local) as clk:
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            res = B.fpcode_min_distance_batch(codes, stream, budgets=budgets, want_witness=True)
-        torch.cuda.synchronize()
-        t_batch = max_over_ranks((time.perf_counter() - t0) / args.steps, world)
-        # the plain form: one launch per code, same budget
-        t0 = time.perf_counter()
-        for c in codes:
-            B.fpcode_min_distance_batch([c], stream, budgets=[budget], want_witness=True)
-        torch.cuda.synchronize()
-        t_single = max_over_ranks(time.perf_counter() - t0, world)
-    certified = int(sum_over_ranks(sum(r.status == B.OK for r in res), world))
-    work = int(sum_over_ranks(sum(r.enumerated for r in res), world))
-    line = {
-        "metric": "codes_per_s", "value": len(all_codes) / t_batch, "unit": "codes/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_batch, "higher_is_better": True,
-        "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": "batch512", "description": WORKLOADS["batch512"], "budget_per_code": budget,
-                   "certified": certified, "budget_limited": len(all_codes) - certified,
-                   "shard": "the 512 codes split into contiguous blocks, one per rank" if world > 1 else "one GPU",
-                   "codewords_per_step": work, "kernel_ms": res[0].t_kernel_ms,
-                   "timing": "end to end from host matrices (host preparation on all cores, H2D, one launch, D2H)"},
-        "per_code": {"codes_per_s": len(all_codes) / t_single, "ms_total": 1e3 * t_single,
-                     "form": "fpcode_min_distance_batch on one code at a time (one launch per code)"},
-        "batched_over_per_code": t_single / t_batch,
-        "gpu_launches": args.steps,
-        "clocks": clk.summary(),
-    }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-
-
-def run_serve(args, rank, world, local):
-    """Continuous batching of Poisson arrivals; latency from arrival to result."""
-    from paper_2603_29942_gb300 import inputs
-
-    if args.impl == "reference":
-        if rank == 0:
-            print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle is timed on the single-code "
-                              "workloads only; serve has no reference arm"}))
-        return
-    if rank != 0:
-        return  # one request stream, served by one GPU (the other ranks hold none)
-    torch, B = _cuda(local)
-    codes, arrivals = inputs.serve_codes()
-    n_req = min(args.requests, len(codes))
-    codes, arrivals = codes[:n_req], arrivals[:n_req]
-    budget = int(args.budget)
-    stream = torch.cuda.Stream()
-    srv = B.fpcode_serve_create(B.fpcode_serve_opts_default(slots=128), stream)
-    # warm-up: a few codes through the server
-    for c in codes[:8]:
-        B.fpcode_serve_submit(srv, c, budget=budget)
-    B.fpcode_serve_drain(srv)
-    B.fpcode_serve_poll(srv)
-    pending = list(range(n_req))
-    ticket_of = {}
-    done_at = {}
-    results = {}
-    with ClockSampler(local) as clk:
-        t0 = time.perf_counter()
-        while len(done_at) < n_req:
-            now = time.perf_counter() - t0
-            while pending and arrivals[pending[0]] <= now:
-                i = pending[0]
-                t = B.fpcode_serve_submit(srv, codes[i], budget=budget)
-                if t is None:
-                    break  # no slot or memory free: the request waits (its latency runs)
-                ticket_of[t] = i
-                pending.pop(0)
-            for t, r in B.fpcode_serve_poll(srv, want_witness=False):
-                i = ticket_of.pop(t)
-                done_at[i] = time.perf_counter() - t0
-                results[i] = r
-            if not pending and not ticket_of:
-                break
-            time.sleep(0.0002)
-        elapsed = time.perf_counter() - t0
-    lat = sorted((done_at[i] - arrivals[i]) * 1e3 for i in done_at)
-    certified = sum(r.status == B.OK for r in results.values())
-    pct = lambda q: lat[min(len(lat) - 1, int(q * len(lat)))]
-    line = {
-        "metric": "codes_per_s", "value": n_req / elapsed, "unit": "codes/s", "n_gpus": 1,
-        "steps": 1, "warmup": 1, "ms_per_step": 1e3 * elapsed, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": "serve", "description": WORKLOADS["serve"], "requests": n_req,
-                   "budget_per_code": budget, "certified": certified, "arrival_span_s": float(arrivals[-1])},
-        "latency_ms": {"p50": pct(0.50), "p90": pct(0.90), "p99": pct(0.99), "max": lat[-1]},
-        "gpu_launches": None,
-        "clocks": clk.summary(),
-    }
-    B.fpcode_serve_destroy(srv)
-    if rank == 0:
-        print(json.dumps(line), flush=True)
 
 
 def main():
@@ -513,12 +728,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="f3_n80_k40", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="leave the other configurations out of the default line")
     ap.add_argument("--budget", type=float, default=1e8, help="per-code budget (batch512, serve)")
-    ap.add_argument("--requests", type=int, default=2000, help="requests served (serve)")
+    ap.add_argument("--requests", type=int, default=10000, help="requests served (serve)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-
-    from paper_2603_29942_gb300 import inputs
 
     rank, world, local = dist_env()
     if args.workload == "batch512":
@@ -529,114 +743,7 @@ def main():
         return run_additions(args, rank, world, local)
     if args.workload == "serve":
         return run_serve(args, rank, world, local)
-    code = inputs.single(args.workload)
-    if args.impl == "reference":
-        run_reference(args, code, rank)
-        return
-
-    import torch
-
-    torch.cuda.set_device(local)
-    dist_init(world, local)
-
-    from paper_2603_29942_gb300 import _binding as B
-    from paper_2603_29942_gb300 import build as _b
-
-    _b.build()
-    stream = torch.cuda.Stream()
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-
-    # --- value: device search on resident tables ---
-    prep = B.fpcode_prepare(code.p, code.n, code.k, code.G)
-    B.fpcode_prepared_upload(prep, stream)
-    for _ in range(args.warmup):
-        B.fpcode_search_enqueue(prep, stream)
-        res = B.fpcode_search_finish(prep, stream)
-    assert res.status == B.OK
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    kern = []
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        with torch.cuda.stream(stream):
-            for i in range(args.steps):
-                flush.fill_(i & 0xFF)  # L2 flush, outside the timed window
-                evs[i][0].record(stream)
-                B.fpcode_search_enqueue(prep, stream)
-                evs[i][1].record(stream)
-                r = B.fpcode_search_finish(prep, stream, want_witness=(i == args.steps - 1))
-                assert r.status == B.OK and r.d == res.d
-                kern.append(r.t_kernel_ms)
-        torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
-    step_ms = [a.elapsed_time(b) for a, b in evs]
-    t_ms = sum(step_ms)
-    codewords = r.enumerated  # evaluated per step (the last step; all steps enumerate the same passes)
-    counts_total = sum(r.counts)
-    t_ms = max_over_ranks(t_ms, world)
-    value = world * codewords * args.steps / (t_ms * 1e-3)
-
-    # --- e2e: public API from host matrices, with copies ---
-    h2d, d2h = B.fpcode_prepared_bytes(prep)
-    G_host = torch.from_numpy(code.G.copy()).pin_memory().numpy()
-    for _ in range(3):
-        B.fpcode_min_distance(code.p, code.n, code.k, G_host, stream)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        d, _w = B.fpcode_min_distance(code.p, code.n, code.k, G_host, stream)
-        assert d == res.d
-    e2e_s = time.perf_counter() - t0
-    e2e_value = world * counts_total * args.steps / e2e_s
-
-    # --- roofline of the enumeration kernel ---
-    kern_ms = statistics.mean(kern)
-    W = max(1, -(-(code.n - code.k) // 32))
-    popc_per_cw = W  # one popcount per 32-bit word of the redundant part
-    achieved = codewords * popc_per_cw / (kern_ms * 1e-3) / 1e12
-    sms = torch.cuda.get_device_properties(local).multi_processor_count
-    peak = POPC_PER_CLK_SM * sms * SM_MAX_MHZ * 1e6 / 1e12
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tpopc/s", "frac": achieved / peak,
-            "traffic": profiled_traffic(args.workload), "kernel": "bz_kernel", "ops_per_codeword": popc_per_cw,
-            "peak_basis": f"{POPC_PER_CLK_SM:.0f} POPC/clk/SM x {sms} SMs x {SM_MAX_MHZ:.0f} MHz"}
-
-    # --- the same kernel in steady state: one long pass alone (fixed size) ---
-    probe_of = {v[0]: (k, v[1]) for k, v in PROBES.items()}
-    roof_probe = None
-    if args.workload in probe_of:
-        pname, pg = probe_of[args.workload]
-        pr_all = B.fpcode_prepare(code.p, code.n, code.k, code.G, B.fpcode_opts_default(budget=0))
-        pidx = next(i for i, x in enumerate(B.fpcode_prepared_passes(pr_all)) if x[0] == pg and x[1] == 0)
-        psize = B.fpcode_prepared_passes(pr_all)[pidx][5]
-        _t, pk_ms, _least = time_pass(torch, B, code, pr_all, pidx, res.d, stream, 5, 3)
-        pach = psize * popc_per_cw / (pk_ms * 1e-3) / 1e12
-        roof_probe = {"bound": "alu", "achieved": pach, "peak": peak, "unit": "Tpopc/s", "frac": pach / peak,
-                      "pass": [pg, 0], "codewords": psize, "kernel_ms": pk_ms, "workload": pname,
-                      "note": "the same kernel on one pass of fixed size alone, termination off, U seeded at d"}
-
-    line = {
-        "metric": "codewords_per_s", "value": value, "unit": "codewords/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "d": res.d,
-                   "codewords_per_step": codewords, "schedule_codewords": counts_total,
-                   "time_to_certified_d_ms": t_ms / args.steps, "l2": "flushed between timed steps (256 MiB memset)",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": roof,
-        "roofline_pass_probe": roof_probe,
-        "e2e": {"value": e2e_value, "unit": "codewords/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": 1e3 * e2e_s / args.steps},
-        "gpu_launches": args.steps,
-        "clocks": clk.summary(),
-    }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(code)
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    return run_default(args, rank, world, local)
 
 
 if __name__ == "__main__":

@@ -70,7 +70,9 @@ typedef struct fpcode_opts {
                           per-level counts are unchanged, `enumerated` and
                           the choice among equal-weight witnesses may vary */
   int ctas_per_sm;     /* 0: from the occupancy calculator */
-  int prefixes_per_lane; /* 0: autotuned per pass; else fixed (1..64) */
+  int prefixes_per_lane; /* one-row leaves: 0: the task plan (guided
+                          tasks, min_steps for small passes); else fixed
+                          tasks of this many prefixes per lane (1..64) */
   int lookahead;       /* 1 (default): CTAs take tasks of the next passes as
                           soon as the current pass has none left, instead of
                           waiting for its last tasks; the termination test
@@ -82,17 +84,34 @@ typedef struct fpcode_opts {
   double wait_limit_s; /* bound on one device wait at a pass hand-off
                           (default 10 s); past it the kernel exits with
                           FPCODE_ETIMEOUT instead of spinning */
-  int pair_leaves;     /* 1 (default): a single code with p = 3 or 7 whose
-                          pair table fits (40 KiB per information set)
+  int pair_leaves;     /* 1: a single code with p = 3 or 7 whose pair
+                          table fits (40 KiB per information set)
                           enumerates each codeword of a pass g >= 2 as a
                           stem of g - 2 rows held exactly plus a pair of
                           rows (y, x) from a table of A[y] + c A[x], and
                           bounds S + B and S - B with one popcount (the
                           isometric last addition of Sec. 4.3 carried to
-                          the last two rows); 0: one-row leaves.  Batches
-                          and servers use one-row leaves.  d, L, U and the
+                          the last two rows); 0: one-row leaves; 2
+                          (default): pair leaves when the search is
+                          expected to take 10^8 codewords or more (d from
+                          the Gilbert-Varshamov bound), since the pair
+                          table pays off on large passes and small
+                          searches are bound by latency.  Batches and
+                          servers use one-row leaves.  d, L, U and the
                           per-level counts do not depend on it. */
-  int reserved[3];
+  int min_steps;       /* one-row leaves: prefixes per lane given to a pass
+                          too small to fill the grid (0: 8 for one code,
+                          32 for a batch, 1 when serving) */
+  int task_work;       /* pair leaves: least work of a task per lane, in
+                          pair entries (0: 192) */
+  int task_share;      /* pair leaves: a task takes 1 / (task_share * C) of
+                          its pass's remaining work, C the CTAs of the
+                          grid, until task_work (0: 2) */
+  int batch_words;     /* batches: words per slice up to which a code with
+                          p in {3, 5, 7} goes to the narrow batched kernel
+                          (0 or 2: n - k <= 64, the others in a second,
+                          wide launch; 4: every such code in one wide
+                          launch) */
 } fpcode_opts;
 
 typedef struct fpcode_result {
@@ -102,7 +121,10 @@ typedef struct fpcode_result {
   int U;               /* best weight found (upper bound) */
   int m;               /* number of information sets */
   int npasses;         /* passes entered (last pass index + 1) */
-  int reserved0, reserved1;
+  int launch;          /* fpcode_min_distance_batch: index of the kernel
+                          launch that searched this code (codes are grouped
+                          by kernel); t_kernel_ms is that launch's time */
+  int reserved1;
   uint64_t enumerated; /* codewords the GPU evaluated in the passes entered
                           (work taken ahead past the certifying pass is not
                           counted) */
@@ -232,6 +254,41 @@ typedef struct fpcode_desc {
 int fpcode_min_distance_batch(int num, const fpcode_desc *codes, void *stream, const fpcode_opts *opts,
                               fpcode_result *results, uint8_t *witnesses);
 
+/* Launch settings of fpcode_min_distance_batch chosen by measurement on
+ * this GPU (the batching of north_star's "words-per-row, warps-per-code and
+ * chunk size chosen by an autotuner"; the paper tunes its word width and
+ * isometry per configuration by hand, Sec. 4.1, Table 3).  The settings
+ * searched: CTAs per SM (0: the occupancy limit, 3, 2: fewer, longer-lived
+ * warps per code), min_steps (8, 16, 32, 64, 128 prefixes per lane in the
+ * small passes: the chunk size) and batch_words (2: narrow and wide
+ * launches by words per slice; 4: one wide launch).  A coordinate search
+ * starts at the defaults, measures every value of one setting with the
+ * others held (each point once, `reps` timed batches after a warm-up, end
+ * to end from the host matrices), moves to the best, and stops when a round
+ * over all settings finds nothing better.  The choice is cached per GPU
+ * (name and SM count) and workload class (the primes present, the largest
+ * words per slice and k, the number of codes and the budget, in powers of
+ * two and ten): a later call for the same class returns it with
+ * evaluated = 0. */
+typedef struct fpcode_tuning {
+  int ctas_per_sm;        /* chosen CTAs per SM (0: the occupancy limit) */
+  int min_steps;          /* chosen prefixes per lane of small passes */
+  int batch_words;        /* chosen grouping: 2 or 4 */
+  int evaluated;          /* settings measured by this call (0: from the cache) */
+  double ms;              /* one batch with the chosen settings */
+  double ms_default;      /* one batch with the default settings */
+  char workload_class[96];
+} fpcode_tuning;
+
+/* Choose the batch launch settings for `codes` by measurement (above);
+ * base: options the settings are added to (NULL: defaults; its budget
+ * applies to codes whose own budget is 0).  *out receives the choice;
+ * apply it with fpcode_tuning_apply.  Errors: as fpcode_min_distance_batch. */
+int fpcode_autotune_batch(int num, const fpcode_desc *codes, void *stream, const fpcode_opts *base, int reps,
+                          fpcode_tuning *out);
+/* Copy a tuning's settings into *opts. */
+void fpcode_tuning_apply(const fpcode_tuning *t, fpcode_opts *opts);
+
 /* Serving: a request loop over the same persistent kernel.  Requests are
  * admitted into free slots as device memory allows, kept resident with
  * their bounds, and interleaved on the GPU with the codes already running;
@@ -263,6 +320,9 @@ int fpcode_serve_poll(fpcode_server *s, fpcode_result *out, uint64_t *tickets, u
                       int *n_out);
 /* Wait until every admitted code has finished (bounded by timeout_ms). */
 int fpcode_serve_drain(fpcode_server *s, int timeout_ms);
+/* Kernel launches the server has made so far (the persistent kernel exits
+ * after its idle period and is launched again on demand). */
+int fpcode_serve_launches(const fpcode_server *s, uint64_t *n);
 void fpcode_serve_destroy(fpcode_server *s);
 
 /* Measured integer issue rates of this GPU (LOP3, POPC, IADD lanes per

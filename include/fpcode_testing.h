@@ -83,6 +83,12 @@ int fpcode_test_pair_mode(const fpcode_prepared *prep, int pass, uint64_t J, uin
  * holds up to 12 words.  Returns the number of words, or a negative
  * status. */
 int fpcode_test_pair_entry(const fpcode_prepared *prep, int j, uint32_t e, uint32_t *sig);
+/* The coordinate search of fpcode_autotune_batch over a synthetic cost
+ * table: ndim settings with sizes[i] values each, cost[] in row-major order
+ * (the last setting fastest), starting at index vector `start`.  best
+ * receives the chosen index vector, *evals the points evaluated.  Returns
+ * 0, or a negative status. */
+int fpcode_test_tune_search(int ndim, const int *sizes, const int *start, const double *cost, int *best, int *evals);
 /* Coefficients (k ints, 0 for rows outside the codeword) of the codeword of
  * Gamma_j that packed key `key` stands for, as the witness is rebuilt; *g
  * and *j receive its level and information set.  Returns 0, or -1 if the

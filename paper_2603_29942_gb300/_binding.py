@@ -39,7 +39,22 @@ class fpcode_opts(ctypes.Structure):
         ("timeout_s", ctypes.c_double),
         ("wait_limit_s", ctypes.c_double),
         ("pair_leaves", ctypes.c_int),
-        ("reserved", ctypes.c_int * 3),
+        ("min_steps", ctypes.c_int),
+        ("task_work", ctypes.c_int),
+        ("task_share", ctypes.c_int),
+        ("batch_words", ctypes.c_int),
+    ]
+
+
+class fpcode_tuning(ctypes.Structure):
+    _fields_ = [
+        ("ctas_per_sm", ctypes.c_int),
+        ("min_steps", ctypes.c_int),
+        ("batch_words", ctypes.c_int),
+        ("evaluated", ctypes.c_int),
+        ("ms", ctypes.c_double),
+        ("ms_default", ctypes.c_double),
+        ("workload_class", ctypes.c_char * 96),
     ]
 
 
@@ -51,7 +66,7 @@ class fpcode_result(ctypes.Structure):
         ("U", ctypes.c_int),
         ("m", ctypes.c_int),
         ("npasses", ctypes.c_int),
-        ("reserved0", ctypes.c_int),
+        ("launch", ctypes.c_int),
         ("reserved1", ctypes.c_int),
         ("enumerated", ctypes.c_uint64),
         ("counts", ctypes.c_uint64 * (MAX_K + 1)),
@@ -143,6 +158,7 @@ def _declare(lib):
         "fpcode_serve_poll": (ctypes.c_int, [_VP, ctypes.POINTER(fpcode_result), ctypes.POINTER(ctypes.c_uint64),
                                              _U8P, ctypes.c_int, _IP]),
         "fpcode_serve_drain": (ctypes.c_int, [_VP, ctypes.c_int]),
+        "fpcode_serve_launches": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint64)]),
         "fpcode_serve_destroy": (None, [_VP]),
         "fpcode_int_peaks": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),
         "fpcode_test_bitslice_host": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _U32P, _U32P, _U32P]),
@@ -176,6 +192,11 @@ def _declare(lib):
         "fpcode_test_pair_mode": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint32)]),
         "fpcode_test_key_coefficients": (ctypes.c_int, [_VP, ctypes.c_uint64, _IP, _IP, _IP]),
         "fpcode_test_pair_entry": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]),
+        "fpcode_autotune_batch": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(fpcode_desc), _VP,
+                                                 ctypes.POINTER(fpcode_opts), ctypes.c_int,
+                                                 ctypes.POINTER(fpcode_tuning)]),
+        "fpcode_tuning_apply": (None, [ctypes.POINTER(fpcode_tuning), ctypes.POINTER(fpcode_opts)]),
+        "fpcode_test_tune_search": (ctypes.c_int, [ctypes.c_int, _IP, _IP, ctypes.POINTER(ctypes.c_double), _IP, _IP]),
     }
     found = []
     for name, (res, args) in sig.items():
@@ -257,11 +278,12 @@ class Result:
     t_kernel_ms: float
     t_total_ms: float
     witness: np.ndarray | None = field(default=None, repr=False)
+    launch: int = 0
 
     @classmethod
     def of(cls, r: fpcode_result, k: int, witness=None) -> "Result":
         return cls(r.status, r.d, r.L, r.U, r.m, r.npasses, int(r.enumerated), [int(x) for x in r.counts[:k + 1]],
-                   [int(x) for x in r.kj[:r.m]], r.t_prepare_ms, r.t_kernel_ms, r.t_total_ms, witness)
+                   [int(x) for x in r.kj[:r.m]], r.t_prepare_ms, r.t_kernel_ms, r.t_total_ms, witness, r.launch)
 
 
 class Prepared:
@@ -370,7 +392,7 @@ def _results_of(res: np.ndarray, ks, ns, wit) -> list[Result]:
     """Result objects from a structured array of fpcode_result (field by
     field, vectorised, so that a large batch costs little Python)."""
     cols = {f: res[f].tolist() for f in ("status", "d", "L", "U", "m", "npasses", "enumerated", "t_prepare_ms",
-                                         "t_kernel_ms", "t_total_ms")}
+                                         "t_kernel_ms", "t_total_ms", "launch")}
     counts, kj = res["counts"], res["kj"]
     out = []
     off = 0
@@ -380,7 +402,8 @@ def _results_of(res: np.ndarray, ks, ns, wit) -> list[Result]:
         m = cols["m"][i]
         out.append(Result(cols["status"][i], cols["d"][i], cols["L"][i], cols["U"][i], m, cols["npasses"][i],
                           cols["enumerated"][i], counts[i, :k + 1].tolist(), kj[i, :max(m, 0)].tolist(),
-                          cols["t_prepare_ms"][i], cols["t_kernel_ms"][i], cols["t_total_ms"][i], w))
+                          cols["t_prepare_ms"][i], cols["t_kernel_ms"][i], cols["t_total_ms"][i], w,
+                          cols["launch"][i]))
     return out
 
 
@@ -414,6 +437,59 @@ def fpcode_min_distance_batch(codes, stream=None, opts: fpcode_opts | None = Non
                                            wit.ctypes.data_as(_U8P) if want_witness else None),
            "fpcode_min_distance_batch")
     return _results_of(res[:num], ks, ns, wit)
+
+
+def _descs(codes, budgets=None):
+    """Packed matrices and a descriptor array (the buffer must outlive the call)."""
+    num = len(codes)
+    mats = [np.asarray(c.G, dtype=np.uint8).reshape(-1) for c in codes]
+    buf = np.concatenate(mats) if num else np.zeros(1, dtype=np.uint8)
+    offs = np.zeros(num + 1, dtype=np.uint64)
+    np.cumsum(np.asarray([int(c.n) * int(c.k) for c in codes], dtype=np.uint64), out=offs[1:])
+    descs = np.zeros(max(num, 1), dtype=_DESC_DT)
+    descs["p"][:num] = [int(c.p) for c in codes]
+    descs["n"][:num] = [int(c.n) for c in codes]
+    descs["k"][:num] = [int(c.k) for c in codes]
+    descs["G"][:num] = np.uint64(buf.ctypes.data) + offs[:-1]
+    if budgets is not None:
+        descs["budget"][:num] = np.asarray(budgets, dtype=np.uint64)
+    return buf, descs
+
+
+def fpcode_autotune_batch(codes, stream=None, opts: fpcode_opts | None = None, budgets=None, reps: int = 2) -> dict:
+    """Measured choice of the batch launch settings for these codes (cached
+    per GPU and workload class); returns the tuning as a dict, and the
+    options with it applied under key "opts"."""
+    buf, descs = _descs(codes, budgets)
+    t = fpcode_tuning()
+    _check(lib().fpcode_autotune_batch(len(codes), ctypes.cast(descs.ctypes.data, ctypes.POINTER(fpcode_desc)),
+                                       _stream(stream), ctypes.byref(opts) if opts else None, int(reps),
+                                       ctypes.byref(t)), "fpcode_autotune_batch")
+    del buf
+    o = fpcode_opts()
+    if opts is not None:
+        ctypes.memmove(ctypes.byref(o), ctypes.byref(opts), ctypes.sizeof(o))
+    else:
+        lib().fpcode_opts_default(ctypes.byref(o))
+    lib().fpcode_tuning_apply(ctypes.byref(t), ctypes.byref(o))
+    return {"ctas_per_sm": t.ctas_per_sm, "min_steps": t.min_steps, "batch_words": t.batch_words,
+            "evaluated": t.evaluated, "ms": t.ms, "ms_default": t.ms_default,
+            "workload_class": t.workload_class.decode(), "opts": o}
+
+
+def fpcode_test_tune_search(sizes, start, cost):
+    """The tuner's coordinate search over a synthetic cost table (row-major)."""
+    nd = len(sizes)
+    sz = (ctypes.c_int * nd)(*sizes)
+    st = (ctypes.c_int * nd)(*start)
+    c = np.ascontiguousarray(np.asarray(cost, dtype=np.float64).reshape(-1))
+    best = (ctypes.c_int * nd)()
+    ev = ctypes.c_int(0)
+    rc = lib().fpcode_test_tune_search(nd, sz, st, c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), best,
+                                       ctypes.byref(ev))
+    if rc < 0:
+        raise FpcodeError(-rc, "fpcode_test_tune_search")
+    return [int(x) for x in best], int(ev.value)
 
 
 def fpcode_int_peaks(stream=None) -> dict:
@@ -590,6 +666,13 @@ def fpcode_serve_poll(server: Server, max_results: int = 256, want_witness: bool
 
 def fpcode_serve_drain(server: Server, timeout_ms: int = 60000) -> None:
     _check(lib().fpcode_serve_drain(server.handle, timeout_ms), "fpcode_serve_drain")
+
+
+def fpcode_serve_launches(server: Server) -> int:
+    """Kernel launches the server has made so far."""
+    n = ctypes.c_uint64(0)
+    _check(lib().fpcode_serve_launches(server.handle, ctypes.byref(n)), "fpcode_serve_launches")
+    return int(n.value)
 
 
 def fpcode_serve_destroy(server: Server) -> None:

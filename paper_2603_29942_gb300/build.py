@@ -15,7 +15,7 @@ LIB = os.path.join(BUILD, "libfpcode.so")
 
 CU_SOURCES = ["fp_api.cu", "fp_k_p3.cu", "fp_k_p5.cu", "fp_k_p7.cu", "fp_k_generic.cu", "fp_k_multi.cu",
               "fp_k_multi_wide.cu", "fp_k_mersenne.cu", "fp_noalloc.cu", "fp_serve.cu", "fp_addbench.cu"]
-CPP_SOURCES = ["fp_host.cpp"]
+CPP_SOURCES = ["fp_host.cpp", "fp_tune.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

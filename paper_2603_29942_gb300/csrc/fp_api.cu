@@ -40,6 +40,20 @@ using fpd::DevCtx;
     }                                                                                            \
   } while (0)
 
+namespace fph {
+
+int device_identity(int *sms, char *name, size_t name_len) {
+  int dev = 0;
+  FP_CUDA(cudaGetDevice(&dev));
+  cudaDeviceProp prop;
+  FP_CUDA(cudaGetDeviceProperties(&prop, dev));
+  *sms = prop.multiProcessorCount;
+  std::snprintf(name, name_len, "%s", prop.name);
+  return FPCODE_OK;
+}
+
+}  // namespace fph
+
 namespace fpd {
 
 std::mutex g_ctx_mu;
@@ -205,6 +219,7 @@ void fill_static(const Layout &L, const std::vector<const fph::Prepared *> &code
     sd.seed_u = P.seed_u;
     sd.pair_sigp = P.pair ? P.pair_sigp : 0;
     sd.pair_quick_max = P.pair_quick_max;
+    sd.nsegs = (int)P.segs.size();
     sd.table = reinterpret_cast<const uint32_t *>(d + L.table_off[i]);
     sd.passes = reinterpret_cast<const PassDesc *>(d + L.pass_off[i]);
     std::memcpy(h + L.off_slots + i * sizeof(SlotDesc), &sd, sizeof(sd));
@@ -267,7 +282,8 @@ int plan_one(fpcode_prepared *prep, const DevCtx &c) {
   int s = occupancy(fn, prep->smem, P.opts.ctas_per_sm, &per_sm);
   if (s) return s;
   prep->ctas = c.sms * per_sm;
-  fph::plan_tasks(&P, prep->ctas, P.opts.prefixes_per_lane, fph::kMinStepsSingle, true);
+  fph::plan_tasks(&P, prep->ctas, P.opts.prefixes_per_lane, P.opts.min_steps > 0 ? P.opts.min_steps : fph::kMinStepsSingle,
+                  true);
   return FPCODE_OK;
 }
 
@@ -393,7 +409,7 @@ void fpcode_opts_default(fpcode_opts *o) {
   o->mid_pass_exit = 1;
   o->lookahead = 1;
   o->wait_limit_s = 10.0;
-  o->pair_leaves = 1;
+  o->pair_leaves = 2;
 }
 
 const char *fpcode_last_error(void) { return fph::last_error(); }
@@ -628,9 +644,10 @@ int fpcode_min_distance_batch(int num, const fpcode_desc *codes, void *stream, c
   {
     std::vector<int> narrow, wide;
     std::vector<std::vector<int>> other(64);
+    const int narrow_w = o.batch_words == 4 ? 0 : 2;
     for (int i = 0; i < num; ++i) {
       if (status[i] != FPCODE_OK) continue;
-      if (preps[i]->variant < 12) (preps[i]->W <= 2 ? narrow : wide).push_back(i);
+      if (preps[i]->variant < 12) (preps[i]->W <= narrow_w ? narrow : wide).push_back(i);
       else other[preps[i]->variant].push_back(i);
     }
     if (!narrow.empty()) groups.push_back(narrow);
@@ -644,6 +661,7 @@ int fpcode_min_distance_batch(int num, const fpcode_desc *codes, void *stream, c
   cudaEvent_t e0, e1;
   FP_CUDA(cudaEventCreate(&e0));
   FP_CUDA(cudaEventCreate(&e1));
+  int nlaunch = -1;
   for (auto &grp : groups) {
     std::vector<const fph::Prepared *> codesv;
     std::vector<int> idx;
@@ -664,7 +682,8 @@ int fpcode_min_distance_batch(int num, const fpcode_desc *codes, void *stream, c
     const int ctas = c->sms * per_sm;
     const bool many = idx.size() > 1;
     for (int i : idx)
-      fph::plan_tasks(preps[i].get(), ctas, o.prefixes_per_lane, many ? fph::kMinStepsBatch : fph::kMinStepsSingle, !many);
+      fph::plan_tasks(preps[i].get(), ctas, o.prefixes_per_lane,
+                      o.min_steps > 0 ? o.min_steps : many ? fph::kMinStepsBatch : fph::kMinStepsSingle, !many);
     Layout L = make_layout(codesv);
     s = ws_reserve(*c, L.total, std::max(L.static_bytes, L.dyn_bytes));
     if (s) break;
@@ -674,6 +693,7 @@ int fpcode_min_distance_batch(int num, const fpcode_desc *codes, void *stream, c
     FP_CUDA(cudaEventRecord(e0, st));
     s = launch(fn, ctas, smem, st, c->ws, L, kparams(o, 0));
     if (s) break;
+    ++nlaunch;
     FP_CUDA(cudaEventRecord(e1, st));
     FP_CUDA(cudaStreamSynchronize(st));  // the staging buffer is reused for the read-back
     FP_CUDA(cudaMemcpyAsync(c->ws_pinned, c->ws + L.off_states, L.dyn_bytes, cudaMemcpyDeviceToHost, st));
@@ -688,6 +708,7 @@ int fpcode_min_distance_batch(int num, const fpcode_desc *codes, void *stream, c
       uint8_t *w = witnesses ? witnesses + woff[i] : nullptr;
       fph::decode_result(*preps[i], outcome_of(states[q], dyn), &results[i], w);
       results[i].t_kernel_ms = ms;
+      results[i].launch = nlaunch;
       results[i].t_prepare_ms = t_prep;
     }
   }

@@ -178,6 +178,34 @@ int lower_bound(const std::vector<int> &e, const std::vector<int> &kj, int k) {
 
 int digit_bits(int p) { return digit_bits_of(p); }
 
+// Codewords a search of a random [n, k] code over F_p is expected to take:
+// d estimated by the Gilbert-Varshamov bound (the least d with
+// sum_{i<d} C(n,i)(p-1)^i >= p^(n-k), in logarithms), the information sets
+// taken as m = floor(n/k) full ones, and the passes of each round g summed
+// until the bound after the round, m (g + 1), reaches d.  Only a guide for
+// choosing the leaf form: the search itself certifies the true d.
+double expected_work(int p, int n, int k) {
+  const double lq = std::log((double)p);
+  double lsum = -1e300;
+  int d = 1;
+  for (int i = 0; i <= n; ++i) {
+    const double lt = std::lgamma(n + 1.0) - std::lgamma(i + 1.0) - std::lgamma(n - i + 1.0) + i * std::log(p - 1.0);
+    lsum = lsum > lt ? lsum + std::log1p(std::exp(lt - lsum)) : lt + std::log1p(std::exp(lsum - lt));
+    if (lsum >= (n - k) * lq) {
+      d = i + 1;
+      break;
+    }
+  }
+  const int m = std::max(1, n / k);
+  double work = 0;
+  for (int g = 1; g <= k; ++g) {
+    work += m * std::exp(std::lgamma(k + 1.0) - std::lgamma(g + 1.0) - std::lgamma(k - g + 1.0) + (g - 1) * std::log(p - 1.0));
+    if (m * (g + 1) >= d) break;
+  }
+  return work;
+}
+constexpr double kPairWork = 1e8;  // pair_leaves 2: pair leaves from this much expected work on
+
 }  // namespace
 
 int prepare(int p, int n, int k, const uint8_t *G, const fpcode_opts &opts, Prepared *P) {
@@ -207,7 +235,7 @@ int prepare(int p, int n, int k, const uint8_t *G, const fpcode_opts &opts, Prep
   // stem below the pair (k >= 3), and a pair table that fits
   P->pair = false;
   P->pair_sigp = 0;
-  if (opts.pair_leaves && (p == 3 || p == 7) && k >= 3) {
+  if (opts.pair_leaves && (p == 3 || p == 7) && k >= 3 && (opts.pair_leaves == 1 || expected_work(p, n, k) >= kPairWork)) {
     const int sigw = P->W * (P->r - 1);
     P->pair = true;
     P->pair_sigp = sigw <= 1 ? 1 : sigw <= 2 ? 2 : sigw <= 4 ? 4 : 8;
@@ -460,15 +488,16 @@ namespace {
 // row ascending -- whose stems all have E(q) = (p-1) C(k-1-q, 2) entries.
 // A lane's work for one stem is its share of the entries plus the stem
 // step.  Tasks are guided by work: a block's tasks aim at a per-lane load
-// of half the pass's remaining work spread over every lane of the grid
-// (at least kMinTaskLane).  A stem whose entries alone exceed that target,
+// of 1 / task_share of the pass's remaining work spread over every lane of
+// the grid (at least task_work).  A stem whose entries alone exceed that target,
 // or a block with too few stems to give every group one, splits its
 // entries over 2^lsplit lanes (interleaved entry chunks, so a warp's loads
 // stay broadcasts or consecutive words).  Each block is a segment of its
 // own, so the groups of a task have equal work.
 constexpr uint64_t kStemCost = 8;      // a stem step, in entry evaluations
-constexpr uint64_t kMinTaskLane = 96;  // least per-lane work of a task, in entry evaluations
-constexpr uint64_t kSpreadLane = 64;   // a pass of at most this much work per lane of the grid is spread wide
+constexpr uint64_t kMinTaskLane = 192;  // least per-lane work of a task, in entry evaluations (task_work 0)
+constexpr uint64_t kTaskShare = 2;      // guided share: 1 / (kTaskShare C) of the remaining work (task_share 0)
+constexpr uint64_t kSpreadLane = 4;    // a pass of at most this much work per lane of the grid is spread wide
 
 void plan_pair_pass(Prepared *P, fpk::PassDesc &d, uint64_t C) {
   const int k = P->k, b = P->p - 1, g = d.g;
@@ -494,6 +523,8 @@ void plan_pair_pass(Prepared *P, fpk::PassDesc &d, uint64_t C) {
   // the grid allows: one stem per group, a stem's entries over as many
   // lanes as keeps two loads per lane.
   const bool spread = rem <= (long double)(C * lanes * kSpreadLane);
+  const uint64_t Tmin = P->opts.task_work > 0 ? (uint64_t)P->opts.task_work : kMinTaskLane;
+  const uint64_t share = P->opts.task_share > 0 ? (uint64_t)P->opts.task_share : kTaskShare;
   const uint64_t T_spread = std::max<uint64_t>(2, (uint64_t)(rem / (long double)(C * lanes)) + 1);
   // Stems of one group start on the same phase of the coefficient counter
   // (units of (p-1)^t stems, t <= g - 3), so the lanes of a warp take the
@@ -511,7 +542,7 @@ void plan_pair_pass(Prepared *P, fpk::PassDesc &d, uint64_t C) {
   };
   for (auto &x : blks) {
     const uint64_t T =
-        spread ? T_spread : std::max<uint64_t>(kMinTaskLane, (uint64_t)(rem / (long double)(2 * C * lanes)));
+        spread ? T_spread : std::max<uint64_t>(Tmin, (uint64_t)(rem / (long double)(share * C * lanes)));
     int l = 0;
     // split a stem's entries while one lane's share exceeds the target, or
     // while the block cannot give every group a stem (at least two entry
@@ -521,6 +552,8 @@ void plan_pair_pass(Prepared *P, fpk::PassDesc &d, uint64_t C) {
       ++l;
     const uint64_t per_stem = ((x.E + (1ull << l) - 1) >> l) + kStemCost;
     uint64_t want = spread ? 1 : std::max<uint64_t>(1, (T + per_stem / 2) / per_stem);
+    // no more stems per group than spreads the block over every group
+    want = std::min<uint64_t>(want, (x.n + (lanes >> l) - 1) / (lanes >> l));
     uint64_t unit = 1;
     for (int t = 0; t < L && unit * (uint64_t)b <= want; ++t) unit *= (uint64_t)b;
     want = std::min<uint64_t>(65535 / unit * unit, want / unit * unit);

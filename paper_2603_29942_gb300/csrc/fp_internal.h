@@ -88,6 +88,9 @@ constexpr int kMinStepsSingle = 8;   // one code per launch
 constexpr int kMinStepsBatch = 32;   // many codes share the grid
 constexpr int kMinStepsServe = 1;    // streamed codes: latency first
 
+// Name and SM count of the current device (fp_api.cu).  Returns an fpcode status.
+int device_identity(int *sms, char *name, size_t name_len);
+
 // Fill a result from the final device state of one code.
 struct DeviceOutcome {
   uint64_t best_key;     // kNoKey if none

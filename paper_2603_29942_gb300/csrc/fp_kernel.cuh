@@ -771,6 +771,7 @@ __device__ void task_pairs(const SlotDesc &sd, const PassDesc &pd, int pass, con
 template <int P, int R, int W, int UNR = LeafFilter<P, R, W>::kUnroll, bool PAIRS = false>
 struct Fixed {
   static constexpr int DB = P == 3 ? 1 : (P == 5 || P == 7) ? 4 : 8;  // as the host's digit width
+  static constexpr int kSegCache = PAIRS ? 768 : 1;  // pair-leaf segments held in shared memory
   static __device__ __forceinline__ void run(const SlotDesc &sd, const PassDesc &pd, int pass, const uint32_t *tab,
                                              const fpenum::BinomCols &B, uint64_t ulo, uint64_t uhi, int lsplit,
                                              int U, SlotState *st, SlotAux *ax, unsigned long long &count) {
@@ -796,6 +797,7 @@ struct Fixed {
 // rest.
 template <int WMAX>
 struct Multi357 {
+  static constexpr int kSegCache = 1;  // batches take one-row leaves
   static __device__ __forceinline__ void run(const SlotDesc &sd, const PassDesc &pd, int pass, const uint32_t *tab,
                                              const fpenum::BinomCols &B, uint64_t ulo, uint64_t uhi, int lsplit,
                                              int U, SlotState *st, SlotAux *ax, unsigned long long &count) {
@@ -833,11 +835,14 @@ struct Claim {
   int lsplit;               // pair-leaf passes: lanes per stem (log2, low 4 bits) | stems per group << 4
 };
 
-// Thread 0's shared-memory copy of the segments of one pair-leaf pass.
-constexpr int kSegCache = 192;  // the host plans at most (p-1)/2 (k-2) <= 186 segments per pass
+// Shared-memory copy of pair-leaf segments: for a one-code launch, the
+// whole list of the code (staged by the CTA at its start, pass = -2), else
+// those of the pass thread 0 claims from (at most (p-1)/2 (k-2) <= 186).
+constexpr int kSegPass = 192;
+template <int N>
 struct SegCache {
-  PairSeg seg[kSegCache];
-  int slot, pass;               // whose (-1: none)
+  PairSeg seg[N];
+  int slot, pass;               // whose (-1: none; pass -2: the whole list)
   unsigned long long gen;
 };
 
@@ -909,9 +914,9 @@ __device__ __forceinline__ void slot_leave(const CtlStatic &cs, int s) {
 // cc.P) of slot s.  A task the skip rule drops needs no work; every later
 // task of the pass is then droppable too, so the rest of the pass is taken
 // in the same claim by compare-and-swap on the code's own generation.
+template <class SC>
 __device__ __forceinline__ void take(SlotState *st, const KParams &kp, bool serve, int s, unsigned long long w,
-                                    uint64_t key, Claim *o, ClaimCache &cc, SegCache &sc,
-                                    const fpenum::BinomCols &B) {
+                                    uint64_t key, Claim *o, ClaimCache &cc, SC &sc, const fpenum::BinomCols &B) {
   const unsigned long long t = w & kTaskMask;
   // the bound: the best recorded weight, else n - k + 2 (the skip rule uses
   // this one: it needs a recorded key); the g = 1 passes' least weight
@@ -926,17 +931,29 @@ __device__ __forceinline__ void take(SlotState *st, const KParams &kp, bool serv
   o->task = t - cc.pd.task_base;
   o->lsplit = 0;
   if (cc.pd.g > 1 && cc.pd.nseg > 0) {
-    // pair-leaf pass: its segments, copied once per pass into shared memory
-    if (sc.slot != s || sc.gen != cc.gen || sc.pass != cc.P) {
+    // pair-leaf pass: its segments from the CTA's copy of the whole list,
+    // else copied for this pass (eight loads in flight at a time)
+    const PairSeg *segs = sc.seg;
+    if (sc.slot == s && sc.gen == cc.gen && sc.pass == -2) {
+      segs += cc.pd.seg_off;
+    } else if (sc.slot != s || sc.gen != cc.gen || sc.pass != cc.P) {
       const uint2 *src = reinterpret_cast<const uint2 *>(cc.sd.passes + cc.sd.npasses) + cc.pd.seg_off;
-      const int n = min((int)cc.pd.nseg, kSegCache);
-      for (int i = 0; i < n; ++i) reinterpret_cast<uint2 *>(sc.seg)[i] = __ldcg(src + i);
+      const int n = min((int)cc.pd.nseg, kSegPass);
+      for (int i0 = 0; i0 < n; i0 += 8) {
+        uint2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (i0 + u < n) v[u] = __ldcg(src + i0 + u);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (i0 + u < n) reinterpret_cast<uint2 *>(sc.seg)[i0 + u] = v[u];
+      }
       sc.slot = s;
       sc.gen = cc.gen;
       sc.pass = cc.P;
     }
     int ls = 0, spg = 1;
-    pair_task(cc.pd, sc.seg, cc.sd.k, B, o->task, &o->ulo, &o->uhi, &ls, &spg);
+    pair_task(cc.pd, segs, cc.sd.k, B, o->task, &o->ulo, &o->uhi, &ls, &spg);
     o->lsplit = ls | (spg << 4);
   } else if (cc.pd.g > 1) {
     task_range(cc.pd, o->task, &o->ulo, &o->uhi);
@@ -977,9 +994,10 @@ __device__ __forceinline__ void take(SlotState *st, const KParams &kp, bool serv
 }
 
 // Thread 0: claim the next task of any live code.
+template <class SC>
 __device__ __forceinline__ int claim(const SlotDesc *slots, SlotState *states, const CtlStatic &cs,
                                      const KParams &kp, CtlDyn *cd, int &rr, unsigned long long &wait_t0,
-                                     unsigned long long t_start, Claim *o, ClaimCache &cc, SegCache &sc,
+                                     unsigned long long t_start, Claim *o, ClaimCache &cc, SC &sc,
                                      const fpenum::BinomCols &B) {
   const int nslots = cs.nslots;
   unsigned long long now = globaltimer();
@@ -1216,7 +1234,7 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
   uint32_t *tab = reinterpret_cast<uint32_t *>(tab4);
   __shared__ Claim s_cl;
   __shared__ ClaimCache s_cc;
-  __shared__ SegCache s_sc;
+  __shared__ SegCache<V::kSegCache> s_sc;
   __shared__ int s_cmd, s_stage;
   __shared__ unsigned long long s_count, s_staged_seq;
   __shared__ int s_staged_slot, s_staged_j;
@@ -1248,6 +1266,21 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
   if (blockIdx.x == 0 && tid == 0 && cs.nslots == 1) {
     const SlotDesc sd0 = load_cg(&slots[0]);
     if (sd0.pass_times) sd0.pass_times[kMaxPasses] = t_start;  // launch start
+  }
+  if constexpr (V::kSegCache > kSegPass) {
+    // one code: the whole segment list, staged once by every thread
+    if (cs.nslots == 1 && !cs.serve) {
+      const SlotDesc sd0 = load_cg(&slots[0]);
+      if (sd0.nsegs > 0 && sd0.nsegs <= V::kSegCache) {
+        const uint2 *src = reinterpret_cast<const uint2 *>(sd0.passes + sd0.npasses);
+        for (int i = tid; i < sd0.nsegs; i += kThreads) reinterpret_cast<uint2 *>(s_sc.seg)[i] = __ldcg(src + i);
+        if (tid == 0) {
+          s_sc.slot = 0;
+          s_sc.gen = sd0.seq & kGenMask;
+          s_sc.pass = -2;
+        }
+      }
+    }
   }
   __syncthreads();
   for (;;) {
@@ -1281,9 +1314,20 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
     }
     const int slot = s_cl.slot;
     if (s_stage) {
+      // eight loads in flight per thread before their stores: one L2 round
+      // trip per 32 KiB instead of one per 4 KiB
       const int words = table_words(s_cl.sd);
+      const int nv = words / 4;
       const uint4 *src = reinterpret_cast<const uint4 *>(s_cl.sd.table + (size_t)s_cl.pd.j * (size_t)words);
-      for (int i = tid; i < words / 4; i += kThreads) tab4[i] = __ldcg(src + i);
+      for (int i0 = tid; i0 < nv; i0 += 8 * kThreads) {
+        uint4 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (i0 + u * kThreads < nv) v[u] = __ldcg(src + i0 + u * kThreads);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (i0 + u * kThreads < nv) tab4[i0 + u * kThreads] = v[u];
+      }
       __syncthreads();
     }
     unsigned long long count = 0;

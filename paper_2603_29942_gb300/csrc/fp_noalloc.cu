@@ -159,6 +159,7 @@ extern "C" int fpcode_min_distance_noalloc(int p, int n, int k, const uint8_t *G
   sd.seed_u = P.seed_u;
   sd.pair_sigp = P.pair ? P.pair_sigp : 0;
   sd.pair_quick_max = P.pair_quick_max;
+  sd.nsegs = (int)P.segs.size();
   sd.table = reinterpret_cast<const uint32_t *>(base + off_table);
   sd.passes = reinterpret_cast<const fpk::PassDesc *>(base + off_pass);
   std::memcpy(&img[off_slot - off_ctl], &sd, sizeof(sd));

@@ -93,6 +93,7 @@ struct fpcode_server {
   std::vector<Slot> slots;
   std::vector<std::pair<size_t, size_t>> free_ext;  // arena extents (offset, bytes), sorted
   uint64_t next_ticket = 1;
+  uint64_t launches = 0;  // kernel launches so far
   int running = 0;
   std::vector<std::pair<uint64_t, std::unique_ptr<fph::Prepared>>> host_done;  // nothing to run on the device
 };
@@ -154,6 +155,7 @@ int ensure_kernel(fpcode_server *s) {
   SV_CUDA(cudaLaunchKernel(s->fn, dim3(s->ctas), dim3(fpk::kThreads), args, (size_t)s->smem, s->kst));
   SV_CUDA(cudaEventRecord(s->kernel_done, s->kst));
   s->kernel_live = true;
+  ++s->launches;
   return FPCODE_OK;
 }
 
@@ -304,7 +306,7 @@ int fpcode_serve_submit(fpcode_server *s, const fpcode_desc *code, uint64_t *tic
     fph::set_error("serve: no device memory free for the tables");
     return FPCODE_EBUSY;
   }
-  fph::plan_tasks(P.get(), s->ctas, o.prefixes_per_lane, fph::kMinStepsServe, true);
+  fph::plan_tasks(P.get(), s->ctas, o.prefixes_per_lane, o.min_steps > 0 ? o.min_steps : fph::kMinStepsServe, true);
   const uint64_t tk = s->next_ticket++;
   char *stg = s->staging + (size_t)slot * s->stage_per_slot;
   const size_t o_pass = a256(sizeof(fpk::SlotDesc));
@@ -432,6 +434,12 @@ int fpcode_serve_drain(fpcode_server *s, int timeout_ms) {
     }
     std::this_thread::sleep_for(std::chrono::microseconds(50));
   }
+}
+
+int fpcode_serve_launches(const fpcode_server *s, uint64_t *n) {
+  if (!s || !n) return FPCODE_EINVAL;
+  *n = s->launches;
+  return FPCODE_OK;
 }
 
 void fpcode_serve_destroy(fpcode_server *s) {

@@ -224,7 +224,7 @@ struct SlotDesc {
   int32_t seed_u;                // > 0: least weight of the g = 1 passes, the search's first bound
   int32_t pair_sigp;             // > 0: pair-leaf passes (g >= 2), words per pair-table entry; 0: one-row leaves
   int32_t pair_quick_max;        // pair leaves: thresholds up to this take the one-popcount bound
-  int32_t pad_s[1];
+  int32_t nsegs;                 // pair leaves: segments of all passes (after the pass descriptors)
   const uint32_t *table;         // m * k * (p-1) * rwpad words, device
   const PassDesc *passes;        // npasses entries, device
   uint64_t seq;                  // serving: ticket of the code in this slot

@@ -506,7 +506,8 @@ def _code_hash(prep):
             h ^= (v >> (8 * b)) & 0xFF
             h = (h * 1099511628211) & 0xFFFFFFFFFFFFFFFF
     code = inputs.single("f7_n40_k20")
-    for v in (code.p, code.n, code.k, 0, 1, 1):  # per_round_check 0, defer 1, pair leaves (defaults, F_7)
+    pair = 1 if B.fpcode_test_pair_mode(prep) > 0 else 0
+    for v in (code.p, code.n, code.k, 0, 1, pair):  # per_round_check 0, defer 1 (defaults), the leaf form
         mix(v)
     for byte in np.asarray(code.G, dtype=np.uint8).reshape(-1):
         mix(int(byte), 1)
@@ -529,7 +530,7 @@ def test_stored_pair_table(p, n, k, lib):
     = 1 .. p-1 innermost; the words after the signature are zero; and
     slice 0 (bit 0 of every symbol) of B."""
     code = inputs.single_code(5 + n, p, n, k)
-    pr = _prep(code)
+    pr = _prep(code, pair_leaves=1)
     sigp = B.fpcode_test_pair_mode(pr)
     assert sigp > 0
     m, _kj, _np, _c = B.fpcode_prepared_shape(pr)
@@ -562,17 +563,22 @@ def test_stored_pair_table(p, n, k, lib):
 
 
 def test_pair_mode_selection(lib):
-    """Pair leaves are taken for p = 3, 7 with k >= 3 when a set's pair
-    table fits 40 KiB, and never when switched off, for other primes, or for
-    k < 3."""
+    """Pair leaves (pair_leaves = 1) are taken for p = 3, 7 with k >= 3 when a
+    set's pair table fits 40 KiB, and never when switched off, for other
+    primes, or for k < 3.  The default (2) takes them only for searches
+    expected to need 10^8 codewords or more."""
     def mode(p, n, k, **kw):
         return B.fpcode_test_pair_mode(_prep(inputs.single_code(9, p, n, k), **kw))
-    assert mode(3, 80, 40) == 2 and mode(7, 40, 20) == 2 and mode(3, 30, 15) == 1
+    assert mode(3, 80, 40, pair_leaves=1) == 2 and mode(7, 40, 20, pair_leaves=1) == 2
+    assert mode(3, 30, 15, pair_leaves=1) == 1
     assert mode(3, 80, 40, pair_leaves=0) == 0
-    assert mode(5, 40, 20) == 0 and mode(11, 30, 10) == 0 and mode(31, 40, 8) == 0
-    assert mode(3, 10, 2) == 0
-    assert mode(7, 100, 40) == 0  # 6 C(40,2) entries of 4 words: 75 KiB
-    assert mode(3, 160, 64) == 0  # 2 C(64,2) entries of 4 words: 64 KiB
+    assert mode(5, 40, 20, pair_leaves=1) == 0 and mode(11, 30, 10, pair_leaves=1) == 0
+    assert mode(31, 40, 8, pair_leaves=1) == 0 and mode(3, 10, 2, pair_leaves=1) == 0
+    assert mode(7, 100, 40, pair_leaves=1) == 0  # 6 C(40,2) entries of 2 + 4 words: 112 KiB
+    assert mode(3, 160, 64, pair_leaves=1) == 0  # 2 C(64,2) entries of 4 + 4 words: 126 KiB
+    # default: the large F_3 [80,40] search (2.7e8 codewords) takes them, the
+    # small ones (F_3 [30,15]: 450; F_7 [40,20]: 4.2e7) do not
+    assert mode(3, 80, 40) == 2 and mode(3, 30, 15) == 0 and mode(7, 40, 20) == 0
 
 
 @pytest.mark.parametrize("p,k", [(3, 5), (3, 7), (7, 5), (7, 6)])
@@ -586,7 +592,7 @@ def test_pair_pass_enumerates_each_class_once(p, k, lib):
     rng = np.random.default_rng(k)
     A = rng.integers(0, p, size=(k, k), dtype=np.uint8)
     code = inputs.systematic(p, 2 * k, k, A)
-    pr = _prep(code, budget=0, defer=0)
+    pr = _prep(code, budget=0, defer=0, pair_leaves=1)
     assert B.fpcode_test_pair_mode(pr) > 0
     inv = {a: pow(a, p - 2, p) for a in range(1, p)}
     for i, (g, j, _Lb, _La, _re, size, nstems) in enumerate(B.fpcode_prepared_passes(pr)):
@@ -614,7 +620,8 @@ def test_pair_tasks_tile_each_pass(name, ctas, lib):
     """The pair-leaf plan's tasks cover every stem of a pass exactly once and
     in order, and the work per task shrinks toward the end of the pass
     (guided by work): the last task is no larger than the first."""
-    pr = _prep(inputs.single(name))
+    pr = _prep(inputs.single(name), pair_leaves=1)
+    assert B.fpcode_test_pair_mode(pr) > 0
     passes = B.fpcode_prepared_passes(pr)
     for i, (g, _j, _Lb, _La, _re, _size, nstems) in enumerate(passes[:14]):
         if g < 2:
@@ -626,3 +633,43 @@ def test_pair_tasks_tile_each_pass(name, ctas, lib):
             assert lo == pos and hi > lo, (i, lo, hi, pos)
             pos = hi
         assert pos == nstems
+
+
+# ------------------------------------------------------------- autotuner ----
+
+def test_tune_search_finds_the_minimum_of_separable_costs(lib):
+    """The batch autotuner's coordinate search (fpcode_autotune_batch) on
+    synthetic cost tables: on a separable cost it reaches the global minimum
+    from any start in one round plus a confirming round, evaluating each grid
+    point at most once."""
+    sizes = [3, 5, 2]
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        parts = [rng.uniform(1, 10, size=s) for s in sizes]
+        cost = parts[0][:, None, None] + parts[1][None, :, None] + parts[2][None, None, :]
+        start = [int(rng.integers(0, s)) for s in sizes]
+        best, evals = B.fpcode_test_tune_search(sizes, start, cost)
+        assert tuple(best) == np.unravel_index(int(np.argmin(cost)), cost.shape)
+        assert evals <= cost.size
+
+
+def test_tune_search_moves_until_a_round_finds_nothing(lib):
+    """A cost whose best value along one setting depends on another: the search
+    keeps sweeping until no setting improves, ends at a point no single-setting
+    change improves (a coordinate-wise minimum), and never returns a point
+    marked as unable to run (negative cost)."""
+    sizes = [4, 4]
+    cost = np.array([[9, 8, 7, 6],
+                     [8, 7, 6, 5],
+                     [7, 6, 5, 4],
+                     [6, 5, 4, 1]], dtype=float)
+    best, _ = B.fpcode_test_tune_search(sizes, [0, 0], cost)
+    assert best == [3, 3]
+    cost2 = cost.copy()
+    cost2[3, 3] = -1.0  # cannot run
+    best, _ = B.fpcode_test_tune_search(sizes, [0, 0], cost2)
+    b0, b1 = best
+    assert cost2[b0, b1] >= 0
+    for v in range(4):  # a coordinate-wise minimum over the runnable points
+        assert cost2[v, b1] < 0 or cost2[v, b1] >= cost2[b0, b1]
+        assert cost2[b0, v] < 0 or cost2[b0, v] >= cost2[b0, b1]
