@@ -151,6 +151,29 @@ void add_sliced_words(int r, const uint32_t *a, const uint32_t *b, uint32_t *s, 
   }
 }
 
+// Pair table of one information set (pair leaves, p = 3 or 7): for y from
+// k - 2 down to 0, x from y + 1 up, c from 1 to p - 1, the signature words
+// B_i xor B_{i+1} of B = A[y] + c A[x] (the exact add of Alg. 3 / Alg. 4)
+// and B's slice 0.  rows: the set's multiples, rwpad words each.
+template <int P, int R>
+void build_pair_table(const uint32_t *rows, int k, int rwpad, int W, int sp, uint32_t *pt, uint32_t *p0) {
+  constexpr int b = P - 1;
+  size_t e = 0;
+  for (int y = k - 2; y >= 0; --y) {
+    const uint32_t *ay = rows + (size_t)y * b * rwpad;
+    for (int x = y + 1; x < k; ++x)
+      for (int c = 1; c <= b; ++c, ++e) {
+        const uint32_t *ax = rows + ((size_t)x * b + (c - 1)) * rwpad;
+        for (int w = 0; w < W; ++w) {
+          uint32_t sum[R];
+          fpbs::add_exact<P, R>(ay + w * R, ax + w * R, sum, P);
+          for (int i = 0; i + 1 < R; ++i) pt[e * sp + (size_t)w * (R - 1) + i] = sum[i] ^ sum[i + 1];
+          p0[e * W + w] = sum[0];
+        }
+      }
+  }
+}
+
 uint64_t sat_mul(uint64_t a, uint64_t b) {
   if (a == 0 || b == 0) return 0;
   if (a > ~0ull / b) return ~0ull;
@@ -367,23 +390,14 @@ int prepare(int p, int n, int k, const uint8_t *G, const fpcode_opts &opts, Prep
   // B_i xor B_{i+1} of B = A[y] + c A[x] (exact bit-sliced add), word w's
   // r - 1 words at [w * (r - 1)], padded to pair_sigp words.
   if (P->pair) {
-    const int b = p - 1, SP = P->pair_sigp;
+    const int SP = P->pair_sigp;
     const size_t NE = P->pair_entries();
-    std::vector<uint32_t> Bv((size_t)R * W);
     for (int j = 0; j < m; ++j) {
       const uint32_t *rows = &P->table[(size_t)j * set_words];
-      uint32_t *pt = &P->table[(size_t)j * set_words + (size_t)k * b * RWP];
+      uint32_t *pt = &P->table[(size_t)j * set_words + (size_t)k * (p - 1) * RWP];
       uint32_t *p0 = pt + ((NE * (size_t)SP + 3) & ~(size_t)3);  // slice 0 of each entry
-      size_t e = 0;
-      for (int y = k - 2; y >= 0; --y)
-        for (int x = y + 1; x < k; ++x)
-          for (int c = 1; c <= b; ++c, ++e) {
-            add_sliced_words(R, rows + (size_t)y * b * RWP, rows + ((size_t)x * b + (c - 1)) * RWP, Bv.data(), W, p);
-            for (int w = 0; w < W; ++w) {
-              for (int i = 0; i + 1 < R; ++i) pt[e * SP + (size_t)w * (R - 1) + i] = Bv[w * R + i] ^ Bv[w * R + i + 1];
-              p0[e * W + w] = Bv[w * R];
-            }
-          }
+      if (p == 3) build_pair_table<3, 2>(rows, k, RWP, W, SP, pt, p0);
+      else build_pair_table<7, 3>(rows, k, RWP, W, SP, pt, p0);
     }
     // The one-popcount bound ORs the words of a pair mask before counting,
     // so a bit of it covers one position per word.  A position is set in a

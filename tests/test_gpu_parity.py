@@ -267,6 +267,29 @@ def _pass_minimum(gamma, p, g):
     return best
 
 
+def test_batch_autotune_keeps_results_and_caches():
+    """The batch autotuner picks settings from its grid by measurement; a second
+    call for the same workload class comes from the cache (nothing measured);
+    and the batch searched with the tuned settings gives every code the same
+    status, d, [L, U] and per-level counts as with the defaults."""
+    codes = inputs.batch_codes(64, seed=7)
+    budgets = [10 ** 6] * len(codes)
+    t = B.fpcode_autotune_batch(codes, budgets=budgets, reps=1)
+    assert t["ctas_per_sm"] in (0, 2, 3) and t["min_steps"] in (8, 16, 32, 64, 128) and t["batch_words"] in (2, 4)
+    assert t["evaluated"] >= 1 and t["ms"] > 0 and t["ms_default"] > 0 and "k" in t["workload_class"]
+    again = B.fpcode_autotune_batch(codes, budgets=budgets, reps=1)
+    assert again["evaluated"] == 0
+    assert (again["ctas_per_sm"], again["min_steps"], again["batch_words"]) == (
+        t["ctas_per_sm"], t["min_steps"], t["batch_words"])
+    ref = B.fpcode_min_distance_batch(codes, budgets=budgets, want_witness=False)
+    for wide in (2, 4):  # also the other grouping, whichever was chosen
+        o = t["opts"]
+        o.batch_words = wide
+        got = B.fpcode_min_distance_batch(codes, opts=o, budgets=budgets, want_witness=False)
+        for r, q in zip(ref, got):
+            assert (r.status, r.d, r.L, r.U, r.counts) == (q.status, q.d, q.L, q.U, q.counts)
+
+
 @pytest.mark.parametrize("name,g", [("f3_n30_k15", 3), ("f7_n40_k20", 3), ("f3_n80_k40", 2)])
 def test_single_pass_probe(name, g):
     """One pass alone (termination off): every codeword of the pass is
