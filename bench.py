@@ -61,6 +61,8 @@ WORKLOADS = {
                            "C(40,8) 2^7 = 9 843 799 680 codewords",
     "probe_f7_n40_k20_g7": "one pass (g=7, Gamma_1) of the F_7 [40,20] code alone, termination off, U seeded at d: "
                            "C(20,7) 6^6 = 3 616 773 120 codewords",
+    "f3_n80_k40_split": "the F_3 [80,40] search (PCG64 seed 2) split over the ranks: every pass's tasks in contiguous "
+                        "ranges, one allreduce-min of the 8-byte packed key per pass before its termination test",
     "batch512": "512 random codes, p in {3,7}, n in {24,...,64}, k = round(r n), r ~ U[1/3,2/3], PCG64 seed 3",
     "serve": "Poisson arrivals (200/s) of 10 000 random codes, p in {3,5,7}, n ~ U[20,72], k ~ U[n/3,2n/3], "
              "PCG64 seed 4",
@@ -674,6 +676,58 @@ def run_serve(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def run_split(args, rank, world, local):
+    """One search split over the ranks (paper_2603_29942_gb300.shard): each
+    pass's tasks in contiguous ranges, one allreduce-min of the packed key per
+    pass (NCCL).  Strong scaling: the work of one search over all ranks."""
+    from paper_2603_29942_gb300 import inputs, shard
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle is timed on the single-code "
+                              "workloads; the split search has no reference arm"}))
+        return
+    torch, B = _cuda(local)
+    dist_init(world, local)
+    code = inputs.single("f3_n80_k40")
+    stream = torch.cuda.Stream()
+    device = torch.device("cuda", local) if world > 1 else None
+    ref = B.fpcode_min_distance_ex(B.fpcode_prepare(code.p, code.n, code.k, code.G), stream)
+    mn, sm = shard.torch_reducers(device) if world > 1 else ((lambda x: x), (lambda x: x))
+    prep = B.fpcode_prepare(code.p, code.n, code.k, code.G)
+    B.fpcode_prepared_upload(prep, stream)
+    sched = B.fpcode_prepared_schedule(prep)
+    gpu = shard.GpuSlices(B, prep, stream)
+
+    def one():
+        return shard.split_search(sched, n=code.n, k=code.k, per_round_check=False, complete=True, rank=rank,
+                                  world=world, search_slice=gpu, min_over_ranks=mn, sum_over_ranks=sm)
+
+    for _ in range(args.warmup):
+        r = one()
+    assert r.d == ref.d and r.counts == ref.counts
+    max_over_ranks(0.0, world)
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            r = one()
+        torch.cuda.synchronize()
+        dt = max_over_ranks(time.perf_counter() - t0, world)
+    line = {
+        "metric": "codewords_per_s", "value": sum(r.counts) * args.steps / dt, "unit": "codewords/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "d": r.d,
+                   "passes": r.npasses, "parallelism": f"one search split over {world} rank(s)",
+                   "timing": "host clock around whole searches (per pass: slice upload, search, read-back, allreduce)"},
+        "gpu_launches": args.steps * r.npasses, "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def run_additions(args, rank, world, local):
     """The additions benchmark of Sec. 5.1 on the GPU: two sets of 10 000
     vectors of 512 symbols added pairwise 10 000 times (a dependent chain),
@@ -743,6 +797,8 @@ def main():
         return run_additions(args, rank, world, local)
     if args.workload == "serve":
         return run_serve(args, rank, world, local)
+    if args.workload == "f3_n80_k40_split":
+        return run_split(args, rank, world, local)
     return run_default(args, rank, world, local)
 
 

@@ -138,6 +138,8 @@ typedef struct fpcode_result {
   double t_kernel_ms;  /* device search (CUDA events) */
   double t_d2h_ms;     /* result read-back */
   double t_total_ms;   /* whole call, host clock */
+  uint64_t best_key;   /* packed key of the best codeword found (all ones:
+                          none); fpcode_prepared_codeword rebuilds it */
 } fpcode_result;
 
 typedef struct fpcode_prepared fpcode_prepared; /* opaque, library-owned */
@@ -207,6 +209,29 @@ int fpcode_search_checkpoint(const fpcode_prepared *prep, fpcode_checkpoint *out
  * or other schedule options, if `prep`'s schedule has no pass after it, or
  * if `prep` is not uploaded. */
 int fpcode_search_resume(fpcode_prepared *prep, const fpcode_checkpoint *ck, void *stream, const fpcode_opts *opts);
+
+/* One search split over several GPUs (one process per GPU): the paper's
+ * parallel search (Sec. 5.2, Table 4) carried to GPUs.  Every rank prepares
+ * and uploads the same code (the same GPU type gives every rank the same
+ * task plan: fpcode_pass_info.ntasks), then for each pass of the schedule in
+ * order searches its own contiguous range of the pass's tasks, starting
+ * from the best weight found so far; the ranks then take the minimum of
+ * their packed keys (an allreduce of 8 bytes) and all apply the same
+ * termination test L >= U (Alg. 6) to it.  paper_2603_29942_gb300/shard.py
+ * drives this over torch.distributed.
+ *
+ * fpcode_prepared_pass_slice: *out (to free with fpcode_prepared_free) is
+ * tasks [task_lo, task_hi) of pass `pass` of the uploaded `src`, alone, its
+ * termination test off, with u_init (> 0) as its first bound: search it
+ * with fpcode_min_distance_ex; the result's best_key (all ones: nothing at
+ * or under the bound) carries pass field 0, the slice's one pass.
+ * Errors: FPCODE_EINVAL (no such pass, an empty range). */
+int fpcode_prepared_pass_slice(const fpcode_prepared *src, int pass, uint64_t task_lo, uint64_t task_hi, int u_init,
+                               fpcode_prepared **out);
+/* The codeword (n bytes, caller-owned) a packed key of `prep`'s schedule
+ * stands for, rebuilt exactly from its Gamma_j rows, and its weight.
+ * Errors: FPCODE_EINVAL (the key names no codeword). */
+int fpcode_prepared_codeword(const fpcode_prepared *prep, uint64_t key, uint8_t *codeword, int *weight);
 
 /* Upload (if needed) + enqueue + finish. */
 int fpcode_min_distance_ex(fpcode_prepared *prep, void *stream, const fpcode_opts *opts, fpcode_result *res,

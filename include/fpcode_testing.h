@@ -49,7 +49,8 @@ int fpcode_test_prefix_walk(uint64_t I, uint64_t steps, int k, int g, int p, int
 
 /* Introspection of a prepared object. */
 typedef struct fpcode_pass_info {
-  int g, j, L_before, L_after, round_end, reserved;
+  int g, j, L_before, L_after, round_end;
+  int ntasks;  /* CTA tasks of the pass under the plan of the code's upload (0 before it) */
   uint64_t size;
   uint64_t nprefix;
 } fpcode_pass_info;

@@ -77,6 +77,7 @@ class fpcode_result(ctypes.Structure):
         ("t_kernel_ms", ctypes.c_double),
         ("t_d2h_ms", ctypes.c_double),
         ("t_total_ms", ctypes.c_double),
+        ("best_key", ctypes.c_uint64),
     ]
 
 
@@ -121,7 +122,7 @@ class fpcode_pass_info(ctypes.Structure):
         ("L_before", ctypes.c_int),
         ("L_after", ctypes.c_int),
         ("round_end", ctypes.c_int),
-        ("reserved", ctypes.c_int),
+        ("ntasks", ctypes.c_int),
         ("size", ctypes.c_uint64),
         ("nprefix", ctypes.c_uint64),
     ]
@@ -192,6 +193,9 @@ def _declare(lib):
         "fpcode_test_pair_mode": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint32)]),
         "fpcode_test_key_coefficients": (ctypes.c_int, [_VP, ctypes.c_uint64, _IP, _IP, _IP]),
         "fpcode_test_pair_entry": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]),
+        "fpcode_prepared_pass_slice": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
+                                                      ctypes.POINTER(_VP)]),
+        "fpcode_prepared_codeword": (ctypes.c_int, [_VP, ctypes.c_uint64, _U8P, _IP]),
         "fpcode_autotune_batch": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(fpcode_desc), _VP,
                                                  ctypes.POINTER(fpcode_opts), ctypes.c_int,
                                                  ctypes.POINTER(fpcode_tuning)]),
@@ -279,11 +283,13 @@ class Result:
     t_total_ms: float
     witness: np.ndarray | None = field(default=None, repr=False)
     launch: int = 0
+    best_key: int = (1 << 64) - 1
 
     @classmethod
     def of(cls, r: fpcode_result, k: int, witness=None) -> "Result":
         return cls(r.status, r.d, r.L, r.U, r.m, r.npasses, int(r.enumerated), [int(x) for x in r.counts[:k + 1]],
-                   [int(x) for x in r.kj[:r.m]], r.t_prepare_ms, r.t_kernel_ms, r.t_total_ms, witness, r.launch)
+                   [int(x) for x in r.kj[:r.m]], r.t_prepare_ms, r.t_kernel_ms, r.t_total_ms, witness, r.launch,
+                   int(r.best_key))
 
 
 class Prepared:
@@ -392,7 +398,7 @@ def _results_of(res: np.ndarray, ks, ns, wit) -> list[Result]:
     """Result objects from a structured array of fpcode_result (field by
     field, vectorised, so that a large batch costs little Python)."""
     cols = {f: res[f].tolist() for f in ("status", "d", "L", "U", "m", "npasses", "enumerated", "t_prepare_ms",
-                                         "t_kernel_ms", "t_total_ms", "launch")}
+                                         "t_kernel_ms", "t_total_ms", "launch", "best_key")}
     counts, kj = res["counts"], res["kj"]
     out = []
     off = 0
@@ -403,7 +409,7 @@ def _results_of(res: np.ndarray, ks, ns, wit) -> list[Result]:
         out.append(Result(cols["status"][i], cols["d"][i], cols["L"][i], cols["U"][i], m, cols["npasses"][i],
                           cols["enumerated"][i], counts[i, :k + 1].tolist(), kj[i, :max(m, 0)].tolist(),
                           cols["t_prepare_ms"][i], cols["t_kernel_ms"][i], cols["t_total_ms"][i], w,
-                          cols["launch"][i]))
+                          cols["launch"][i], int(cols["best_key"][i])))
     return out
 
 
@@ -592,6 +598,33 @@ def fpcode_prepared_single_pass(prep: Prepared, pass_index: int, u_init: int = 0
     _check(lib().fpcode_prepared_single_pass(prep.handle, int(pass_index), int(u_init), ctypes.byref(h)),
            "fpcode_prepared_single_pass")
     return Prepared(h.value, prep.p, prep.n, prep.k)
+
+
+def fpcode_prepared_schedule(prep: Prepared) -> list[dict]:
+    """The passes of the schedule with their bounds, sizes and (after an
+    upload) the tasks of each under the plan."""
+    arr = (fpcode_pass_info * 256)()
+    n = lib().fpcode_prepared_passes(prep.handle, arr, 256)
+    return [{"g": arr[i].g, "j": arr[i].j, "L_before": arr[i].L_before, "L_after": arr[i].L_after,
+             "round_end": arr[i].round_end, "ntasks": arr[i].ntasks, "size": int(arr[i].size)} for i in range(n)]
+
+
+def fpcode_prepared_pass_slice(prep: Prepared, pass_index: int, task_lo: int, task_hi: int, u_init: int) -> Prepared:
+    """Tasks [task_lo, task_hi) of one pass of the uploaded prep, alone, with
+    the first bound u_init (multi-GPU split of one search)."""
+    h = _VP()
+    _check(lib().fpcode_prepared_pass_slice(prep.handle, int(pass_index), int(task_lo), int(task_hi), int(u_init),
+                                            ctypes.byref(h)), "fpcode_prepared_pass_slice")
+    return Prepared(h.value, prep.p, prep.n, prep.k)
+
+
+def fpcode_prepared_codeword(prep: Prepared, key: int):
+    """(codeword, weight) of a packed key of prep's schedule."""
+    cw = np.zeros(prep.n, dtype=np.uint8)
+    w = ctypes.c_int(0)
+    _check(lib().fpcode_prepared_codeword(prep.handle, ctypes.c_uint64(key), cw.ctypes.data_as(_U8P), ctypes.byref(w)),
+           "fpcode_prepared_codeword")
+    return cw, int(w.value)
 
 
 def fpcode_prepared_bytes(prep: Prepared) -> tuple[int, int]:

@@ -284,6 +284,13 @@ int plan_one(fpcode_prepared *prep, const DevCtx &c) {
   prep->ctas = c.sms * per_sm;
   fph::plan_tasks(&P, prep->ctas, P.opts.prefixes_per_lane, P.opts.min_steps > 0 ? P.opts.min_steps : fph::kMinStepsSingle,
                   true);
+  if (prep->slice_hi > 0) {  // a slice of the one pass: its tasks under the same plan
+    fpk::PassDesc &d = P.passes[0];
+    const uint64_t hi = std::min<uint64_t>(prep->slice_hi, d.ntasks);
+    const uint64_t lo = std::min<uint64_t>(prep->slice_lo, hi);
+    d.task_off = (uint32_t)lo;
+    d.ntasks = (uint32_t)(hi - lo);
+  }
   return FPCODE_OK;
 }
 
@@ -450,6 +457,23 @@ int fpcode_prepared_single_pass(const fpcode_prepared *src, int pass, int u_init
   prep->host.complete = 0;
   prep->host.seed_u = 0;  // the probe's bound is u_init
   prep->init_u = u_init;
+  *out = prep;
+  return FPCODE_OK;
+}
+
+int fpcode_prepared_pass_slice(const fpcode_prepared *src, int pass, uint64_t task_lo, uint64_t task_hi, int u_init,
+                               fpcode_prepared **out) {
+  if (!out) return FPCODE_EINVAL;
+  *out = nullptr;
+  if (!src || task_hi <= task_lo) {
+    fph::set_error("fpcode_prepared_pass_slice: need a prepared code and task_lo < task_hi");
+    return FPCODE_EINVAL;
+  }
+  fpcode_prepared *prep = nullptr;
+  int s = fpcode_prepared_single_pass(src, pass, u_init, &prep);
+  if (s) return s;
+  prep->slice_lo = task_lo;
+  prep->slice_hi = task_hi;
   *out = prep;
   return FPCODE_OK;
 }

@@ -752,6 +752,7 @@ int decode_result(const Prepared &P, const DeviceOutcome &o, fpcode_result *res,
   const bool seeded = o.best_key != fpk::kNoKey && fpk::key_pass(o.best_key) >= P.passes.size();
   const bool have = o.best_key != fpk::kNoKey && !seeded;
   res->U = o.best_key != fpk::kNoKey ? std::min<int>((int)fpk::key_weight(o.best_key), singleton) : singleton;
+  res->best_key = have ? o.best_key : fpk::kNoKey;
   res->status = o.status < 0 ? FPCODE_ETIMEOUT : o.status;
   res->d = -1;
   if (res->status == FPCODE_OK) {
@@ -1004,6 +1005,28 @@ int fpcode_test_pair_entry(const fpcode_prepared *prep, int j, uint32_t e, uint3
   return P->pair_sigp + P->W;
 }
 
+int fpcode_prepared_codeword(const fpcode_prepared *prep, uint64_t key, uint8_t *codeword, int *weight) {
+  if (!prep || !codeword) return FPCODE_EINVAL;
+  const fph::Prepared &P = prep->host;
+  int g = 0, j = 0;
+  std::vector<int> coef;
+  if (key == fpk::kNoKey || !fph::key_coefficients(P, key, &g, &j, coef)) {
+    fph::set_error("fpcode_prepared_codeword: the key names no codeword of the schedule");
+    return FPCODE_EINVAL;
+  }
+  std::vector<uint8_t> cw(P.n, 0);
+  for (int t = 0; t < P.k; ++t)
+    if (coef[t]) {
+      const uint8_t *row = &P.gam[((size_t)j * P.k + t) * P.n];
+      for (int c = 0; c < P.n; ++c) cw[c] = (uint8_t)((cw[c] + coef[t] * row[c]) % P.p);
+    }
+  int wt = 0;
+  for (int c = 0; c < P.n; ++c) wt += cw[c] != 0;
+  std::memcpy(codeword, cw.data(), (size_t)P.n);
+  if (weight) *weight = wt;
+  return FPCODE_OK;
+}
+
 int fpcode_prepared_passes(const fpcode_prepared *prep, fpcode_pass_info *passes, int max) {
   const fph::Prepared *P = prep ? &prep->host : nullptr;
   if (!P || !passes) return FPCODE_EINVAL;
@@ -1015,7 +1038,7 @@ int fpcode_prepared_passes(const fpcode_prepared *prep, fpcode_pass_info *passes
     passes[i].L_before = d.L_before;
     passes[i].L_after = d.L_after;
     passes[i].round_end = d.round_end;
-    passes[i].reserved = 0;
+    passes[i].ntasks = (int)d.ntasks;
     passes[i].size = d.size;
     passes[i].nprefix = d.nprefix;
   }

@@ -113,6 +113,7 @@ struct fpcode_prepared {
   int smem = 0;         // dynamic shared memory of one launch
   int init_u = 0;       // > 0: the search starts with this upper bound (single-pass probes)
   int resume_from = 0;  // > 0: the next search starts at this pass (fpcode_search_resume)
+  uint64_t slice_lo = 0, slice_hi = 0;  // slice_hi > 0: only tasks [slice_lo, slice_hi) of the one pass
   uint64_t resume_key = ~0ull;  // ... with this best key
   int last_status = -100;       // outcome of the last finished search (for checkpoints)
   int last_stop = -1;

@@ -63,8 +63,8 @@ struct KParams {
 
 // Launch-wide dynamic flags (zeroed before each launch).
 struct CtlDyn {
-  int32_t err;   // 1: a hand-off wait gave up; 2: time limit reached
-  int32_t pad;
+  int32_t err;      // 1: a hand-off wait gave up; 2: time limit reached
+  int32_t leaving;  // serving: the kernel is retiring (idle); claims exit, the host launches again
   unsigned long long last_busy;  // serving: %globaltimer of a recent claim that found work (max over CTAs)
 };
 
@@ -917,7 +917,7 @@ __device__ __forceinline__ void slot_leave(const CtlStatic &cs, int s) {
 template <class SC>
 __device__ __forceinline__ void take(SlotState *st, const KParams &kp, bool serve, int s, unsigned long long w,
                                     uint64_t key, Claim *o, ClaimCache &cc, SC &sc, const fpenum::BinomCols &B) {
-  const unsigned long long t = w & kTaskMask;
+  const unsigned long long t = w & kTaskMask;  // a slice of a pass numbers its tasks from task_off
   // the bound: the best recorded weight, else n - k + 2 (the skip rule uses
   // this one: it needs a recorded key); the g = 1 passes' least weight
   // (known before the search) caps the bound the task filters against, so
@@ -928,7 +928,7 @@ __device__ __forceinline__ void take(SlotState *st, const KParams &kp, bool serv
   const int mid = kp.mid_pass < 0 ? cc.sd.mid_pass_exit : kp.mid_pass;
   o->sd = cc.sd;
   o->pd = cc.pd;
-  o->task = t - cc.pd.task_base;
+  o->task = t - cc.pd.task_base + cc.pd.task_off;
   o->lsplit = 0;
   if (cc.pd.g > 1 && cc.pd.nseg > 0) {
     // pair-leaf pass: its segments from the CTA's copy of the whole list,
@@ -1005,6 +1005,10 @@ __device__ __forceinline__ int claim(const SlotDesc *slots, SlotState *states, c
     atomicExch(&cd->err, 2);
     return kCmdExit;
   }
+  // serving: once one CTA has decided the kernel retires, all leave at their
+  // next claim, so that no code that arrives meanwhile runs on a shrinking
+  // grid (the host launches the kernel again for it)
+  if (cs.serve && ld_vol(&cd->leaving)) return kCmdExit;
   // Fast path: the slot served last, descriptors cached.  The task counter,
   // the finished flag and the best key are read in one round trip.  A task
   // taken from a code that has finished is dropped (nothing is left to
@@ -1114,7 +1118,10 @@ __device__ __forceinline__ int claim(const SlotDesc *slots, SlotState *states, c
     // codes, and a large code arriving then ran on those few)
     const unsigned long long busy = ld_vol(&cd->last_busy);
     const unsigned long long since = busy > wait_t0 ? busy : wait_t0;
-    if (now > since && now - since > kp.idle_limit_ns) return kCmdExit;
+    if (now > since && now - since > kp.idle_limit_ns) {
+      atomicExch(&cd->leaving, 1);
+      return kCmdExit;
+    }
   }
   __nanosleep(cc.sleep_ns);  // back off: idle probes must not crowd the state's cache lines
   if (cc.sleep_ns < 4096) cc.sleep_ns <<= 1;

@@ -54,7 +54,7 @@ struct PassDesc {
   uint32_t task_base;      // tasks of all earlier passes
   uint32_t seg_off;        // pair-leaf passes: first segment of the pass in the code's segment list
   uint32_t nseg;           // pair-leaf passes: its segments (0: a one-row-leaf pass)
-  uint32_t pad2;
+  uint32_t task_off;       // a slice of the pass (fpcode_prepared_pass_slice): its first task in the pass's plan
 };
 
 // Words per row of the pair-signature table (Mersenne p = 3, 7): for each

@@ -267,6 +267,41 @@ def _pass_minimum(gamma, p, g):
     return best
 
 
+@pytest.mark.parametrize("name", ["f7_n40_k20", "f3_n80_k40", "f3_n30_k15"])
+def test_split_search_gpu_slices(name):
+    """One search split over ranks (paper_2603_29942_gb300.shard), each rank's
+    slice of every pass searched on the GPU (fpcode_prepared_pass_slice): with
+    the ranks emulated one after another on this GPU, 2 and 3 ranks give the
+    d, L, U, stop pass and per-level counts of the one-launch search, every
+    codeword counted once, and a best key whose codeword has weight d and lies
+    in the code."""
+    from paper_2603_29942_gb300 import shard
+
+    code = inputs.single(name)
+    ref, _ = run(code, mid_pass_exit=0)
+    prep = B.fpcode_prepare(code.p, code.n, code.k, code.G)
+    B.fpcode_prepared_upload(prep)
+    sched = B.fpcode_prepared_schedule(prep)
+    assert all(s["ntasks"] >= 1 for s in sched)
+    gpu = shard.GpuSlices(B, prep)
+    for world in (2, 3):
+        def search_slice(P, lo, hi, u):
+            best, ev = shard.NO_KEY, 0
+            for r in range(world):  # the ranks, one after another
+                a, b = shard.rank_range(hi - lo, r, world)
+                if b > a:
+                    key, e = gpu(P, lo + a, lo + b, u)
+                    best, ev = min(best, key), ev + e
+            return best, ev
+        res = shard.split_search(sched, n=code.n, k=code.k, per_round_check=False, complete=True, rank=0, world=1,
+                                 search_slice=search_slice, min_over_ranks=lambda x: x, sum_over_ranks=lambda x: x)
+        assert (res.status, res.d, res.L, res.U, res.npasses) == (B.OK, ref.d, ref.L, ref.U, ref.npasses)
+        assert res.counts == ref.counts and res.evaluated == sum(ref.counts)
+        cw, wt = B.fpcode_prepared_codeword(prep, res.best_key)
+        assert wt == ref.d
+        check_witness(code, ref.d, cw)
+
+
 def test_batch_autotune_keeps_results_and_caches():
     """The batch autotuner picks settings from its grid by measurement; a second
     call for the same workload class comes from the cache (nothing measured);
