@@ -93,7 +93,7 @@ int ws_reserve(DevCtx &c, size_t dev_bytes, size_t pinned_bytes) {
     c.ws_pinned = nullptr;
     c.ws_pinned_bytes = 0;
     size_t want = std::max(pinned_bytes, (size_t)1 << 20);
-    FP_CUDA(cudaMallocHost(&c.ws_pinned, want));
+    FP_CUDA(cudaHostAlloc(&c.ws_pinned, want, cudaHostAllocMapped));  // mapped: kernels write outcomes into it
     c.ws_pinned_bytes = want;
   }
   return FPCODE_OK;
@@ -192,14 +192,23 @@ Layout make_layout(const std::vector<const fph::Prepared *> &codes) {
 }
 
 // Write the static part for `codes` into host staging `h` (device base `d`).
+// outcome: for one code, the device address of a host-mapped copy of its
+// dynamic state ([SlotState][CtlDyn], L.dyn_bytes): the kernel's last CTA
+// writes it there and zeroes the state for the next launch (else null: the
+// caller zeroes the state before and copies it back after each launch).
 void fill_static(const Layout &L, const std::vector<const fph::Prepared *> &codes, const DevCtx &c, char *h,
-                 char *d, int serve) {
+                 char *d, int serve, char *outcome = nullptr) {
   CtlStatic cs{};
   cs.binom = c.binom;
   cs.aux = reinterpret_cast<fpk::SlotAux *>(d + L.off_aux);
   cs.slot_flags = reinterpret_cast<uint32_t *>(d + L.off_flags);
   cs.nslots = (int)codes.size();
   cs.serve = serve;
+  if (outcome && codes.size() == 1 && !serve) {
+    cs.outcome = outcome;
+    cs.dyn_bytes = (uint32_t)L.dyn_bytes;
+    cs.clean_bytes = (uint32_t)(L.off_times - L.off_states);
+  }
   std::memcpy(h + L.off_ctl, &cs, sizeof(cs));
   for (size_t i = 0; i < codes.size(); ++i) {
     const fph::Prepared &P = *codes[i];
@@ -296,7 +305,9 @@ int plan_one(fpcode_prepared *prep, const DevCtx &c) {
 
 // Upload one planned code (plan_one) into device buffer `d` via pinned
 // staging `h`.
-int upload_one(fpcode_prepared *prep, cudaStream_t st, DevCtx &c, char *d, char *h, bool with_state = false) {
+// readback: the host-mapped buffer the kernel copies the outcome into.
+int upload_one(fpcode_prepared *prep, cudaStream_t st, DevCtx &c, char *d, char *h, char *readback,
+               bool with_state = false) {
   fph::Prepared &P = prep->host;
   Layout L = make_layout({&P});
   prep->off_ctl = L.off_ctl;
@@ -306,14 +317,21 @@ int upload_one(fpcode_prepared *prep, cudaStream_t st, DevCtx &c, char *d, char 
   prep->off_state = L.off_states;
   prep->dyn_bytes = L.dyn_bytes;
   prep->dev_bytes = L.total;
-  fill_static(L, {&P}, c, h, d, 0);
+  char *outcome = nullptr;
+  if (readback && cudaHostGetDevicePointer((void **)&outcome, readback, 0) != cudaSuccess) {
+    (void)cudaGetLastError();  // not mapped: the state is reset and copied back per search instead
+    outcome = nullptr;
+  }
+  prep->mapped_outcome = outcome != nullptr;
+  fill_static(L, {&P}, c, h, d, 0, outcome);
   SlotDesc *sd = reinterpret_cast<SlotDesc *>(h + L.off_slots);
   sd->pass_times = reinterpret_cast<unsigned long long *>(d + L.off_times);
   size_t bytes = L.static_bytes;
+  prep->state_clean = false;
   if (with_state) {
     std::memset(h + L.off_states, 0, L.off_times - L.off_states);
     bytes = L.off_times;
-    prep->state_ready = true;
+    prep->state_clean = true;
   }
   FP_CUDA(cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, st));
   return FPCODE_OK;
@@ -322,9 +340,11 @@ int upload_one(fpcode_prepared *prep, cudaStream_t st, DevCtx &c, char *d, char 
 int enqueue_one(fpcode_prepared *prep, cudaStream_t st, const fpcode_opts &o) {
   fph::Prepared &P = prep->host;
   Layout L = make_layout({&P});
-  const bool preloaded = prep->state_ready && prep->resume_from == 0 && prep->init_u == 0;
-  prep->state_ready = false;  // one search
-  if (!preloaded) FP_CUDA(cudaMemsetAsync(prep->dev + L.off_states, 0, L.dyn_bytes + L.aux_bytes, st));
+  // the state is zero after the upload that wrote it and after every
+  // search whose kernel cleaned up behind itself (mapped outcome); else reset it
+  const bool clean = prep->state_clean;
+  prep->state_clean = false;  // until this search has finished
+  if (!clean) FP_CUDA(cudaMemsetAsync(prep->dev + L.off_states, 0, L.dyn_bytes + L.aux_bytes, st));
   const bool resumed = prep->resume_from > 0;
   // the first state's values, staged in pinned memory (a copy from pageable
   // memory would wait for the stream)
@@ -360,7 +380,8 @@ int enqueue_one(fpcode_prepared *prep, cudaStream_t st, const fpcode_opts &o) {
     if (s) return s;
     FP_CUDA(cudaEventRecord((cudaEvent_t)prep->ev1, st));
   }
-  FP_CUDA(cudaMemcpyAsync(prep->pinned, prep->dev + L.off_states, L.dyn_bytes, cudaMemcpyDeviceToHost, st));
+  if (!prep->mapped_outcome || P.passes.empty())
+    FP_CUDA(cudaMemcpyAsync(prep->pinned, prep->dev + L.off_states, L.dyn_bytes, cudaMemcpyDeviceToHost, st));
   prep->run_opts = o;
   return FPCODE_OK;
 }
@@ -368,6 +389,7 @@ int enqueue_one(fpcode_prepared *prep, cudaStream_t st, const fpcode_opts &o) {
 int finish_one(fpcode_prepared *prep, cudaStream_t st, fpcode_result *res, uint8_t *witness) {
   FP_CUDA(cudaStreamSynchronize(st));
   const fph::Prepared &P = prep->host;
+  prep->state_clean = prep->mapped_outcome && !P.passes.empty();  // the kernel's last CTA zeroed it
   if (P.passes.empty()) {  // budget below the first pass
     fph::DeviceOutcome o{fpk::kNoKey, 0, FPCODE_EBUDGET, -1};
     return fph::decode_result(P, o, res, witness);
@@ -504,8 +526,8 @@ int fpcode_prepared_upload(fpcode_prepared *prep, void *stream) {
   Layout L = make_layout({&prep->host});
   FP_CUDA(cudaMalloc(&prep->dev, L.total));
   prep->stage_off = align256(std::max(L.static_bytes, L.dyn_bytes));
-  FP_CUDA(cudaMallocHost(&prep->pinned, prep->stage_off + 64));
-  s = upload_one(prep, st, *c, prep->dev, prep->pinned);
+  FP_CUDA(cudaHostAlloc(&prep->pinned, prep->stage_off + 64, cudaHostAllocMapped));  // mapped: the outcome lands here
+  s = upload_one(prep, st, *c, prep->dev, prep->pinned, prep->pinned);
   if (s) return s;
   FP_CUDA(cudaStreamSynchronize(st));
   prep->uploaded = true;
@@ -612,7 +634,7 @@ int fpcode_min_distance(int p, int n, int k, const uint8_t *G, void *stream, int
   prep.ev1 = c->ev1;
   prep.external = true;
   prep.dev = c->ws;
-  s = upload_one(&prep, st, *c, prep.dev, c->ws_pinned, true);
+  s = upload_one(&prep, st, *c, prep.dev, c->ws_pinned, c->ws_pinned + rb_off, true);
   if (s) return s;
   prep.pinned = c->ws_pinned + rb_off;
   prep.stage_off = stage_off - rb_off;

@@ -125,7 +125,8 @@ struct fpcode_prepared {
   size_t off_ctl = 0, off_slot = 0, off_pass = 0, off_table = 0, off_state = 0, dyn_bytes = 0;
   char *pinned = nullptr; // read-back of the dynamic part
   size_t stage_off = 0;   // pinned + stage_off: 64 bytes staging the first state's values (bound, resume)
-  bool state_ready = false;  // the upload also wrote the first state: the next search skips its reset
+  bool state_clean = false;     // the dynamic state is zero (upload with state, or a kernel that cleaned up)
+  bool mapped_outcome = false;  // the kernel writes its outcome into `pinned` and zeroes its state
   void *ev0 = nullptr, *ev1 = nullptr;  // cudaEvent_t around the kernel
   fpcode_opts run_opts{};
 };

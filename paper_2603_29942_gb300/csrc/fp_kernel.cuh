@@ -38,8 +38,11 @@ struct CtlStatic {
   SlotAux *aux;           // per-slot pass minima and counts (zeroed with the states)
   uint32_t *slot_flags;   // per slot, padded to a multiple of four: see kSlotFinished
   uint32_t *inflight;     // serving: claims in flight per slot (kInflightStride apart); null otherwise
+  char *outcome;          // one-code launches: host-mapped copy of the dynamic state (else null), see below
   int32_t nslots;
   int32_t serve;          // serving: slots appear while the kernel runs
+  uint32_t dyn_bytes;     // outcome: bytes of [SlotState][CtlDyn] copied out
+  uint32_t clean_bytes;   // outcome: bytes of the dynamic state (states, aux, flags) zeroed for the next launch
 };
 
 // A slot's flag word: (generation << 16) | kSlotFinished | kSlotExhausted.
@@ -66,6 +69,8 @@ struct CtlDyn {
   int32_t err;      // 1: a hand-off wait gave up; 2: time limit reached
   int32_t leaving;  // serving: the kernel is retiring (idle); claims exit, the host launches again
   unsigned long long last_busy;  // serving: %globaltimer of a recent claim that found work (max over CTAs)
+  uint32_t exited;  // one-code launches with an outcome copy: CTAs that have left
+  uint32_t pad;
 };
 
 // Shared memory: binomial columns C(n, t), t < kBinomCols, then the staged
@@ -772,6 +777,7 @@ template <int P, int R, int W, int UNR = LeafFilter<P, R, W>::kUnroll, bool PAIR
 struct Fixed {
   static constexpr int DB = P == 3 ? 1 : (P == 5 || P == 7) ? 4 : 8;  // as the host's digit width
   static constexpr int kSegCache = PAIRS ? 768 : 1;  // pair-leaf segments held in shared memory
+  static constexpr int kPassCache = 24;                // pass descriptors held in shared memory (one code)
   static __device__ __forceinline__ void run(const SlotDesc &sd, const PassDesc &pd, int pass, const uint32_t *tab,
                                              const fpenum::BinomCols &B, uint64_t ulo, uint64_t uhi, int lsplit,
                                              int U, SlotState *st, SlotAux *ax, unsigned long long &count) {
@@ -798,6 +804,7 @@ struct Fixed {
 template <int WMAX>
 struct Multi357 {
   static constexpr int kSegCache = 1;  // batches take one-row leaves
+  static constexpr int kPassCache = 1;  // and read their pass descriptors from global memory
   static __device__ __forceinline__ void run(const SlotDesc &sd, const PassDesc &pd, int pass, const uint32_t *tab,
                                              const fpenum::BinomCols &B, uint64_t ulo, uint64_t uhi, int lsplit,
                                              int U, SlotState *st, SlotAux *ax, unsigned long long &count) {
@@ -825,9 +832,7 @@ struct Multi357 {
 enum { kCmdRun = 0, kCmdWait = 1, kCmdExit = 2 };
 
 // What thread 0 hands to its CTA for one task.
-struct Claim {
-  SlotDesc sd;
-  PassDesc pd;              // the task's pass
+struct Claim {  // the task taken (its code's and pass's descriptors: the ClaimCache)
   unsigned long long task;  // task index within the pass
   uint64_t ulo, uhi;        // its unit range (g >= 2; pair-leaf passes: stems; g == 1: task, task + 1)
   int slot, pass, U, skip;
@@ -859,32 +864,42 @@ struct ClaimCache {
 };
 
 // Pass of global task t: the cached pass, the next one, else a binary
-// search over the passes' task_base fields.
-__device__ __forceinline__ bool locate(ClaimCache &cc, unsigned long long t) {
+// search over the passes' task_base fields.  pc: the launch's copy of its
+// first npc pass descriptors in shared memory (one-code launches; 0 for
+// the others), the rest come from global memory.
+__device__ __forceinline__ bool locate(ClaimCache &cc, const PassDesc *pc, int npc, unsigned long long t) {
+  auto tbase = [&](int i) -> unsigned long long {
+    return i < npc ? (unsigned long long)pc[i].task_base : (unsigned long long)__ldcg(&cc.sd.passes[i].task_base);
+  };
+  auto tend = [&](int i) -> unsigned long long {
+    return i < npc ? (unsigned long long)pc[i].task_base + pc[i].ntasks
+                   : (unsigned long long)__ldcg(&cc.sd.passes[i].task_base) + __ldcg(&cc.sd.passes[i].ntasks);
+  };
+  auto take_pass = [&](int i) {
+    cc.P = i;
+    if (i < npc) cc.pd = pc[i];
+    else cc.pd = load_cg(&cc.sd.passes[i]);
+  };
   if (cc.P >= 0 && t >= cc.pd.task_base) {
     if (t < (unsigned long long)cc.pd.task_base + cc.pd.ntasks) return true;
     if (cc.P + 1 >= cc.sd.npasses) return false;
-    const PassDesc nx = load_cg(&cc.sd.passes[cc.P + 1]);
-    if (t < (unsigned long long)nx.task_base + nx.ntasks) {
-      ++cc.P;
-      cc.pd = nx;
+    if (t < tend(cc.P + 1)) {
+      take_pass(cc.P + 1);
       return true;
     }
   }
-  const PassDesc last = load_cg(&cc.sd.passes[cc.sd.npasses - 1]);
-  if (t >= (unsigned long long)last.task_base + last.ntasks) {
-    cc.P = cc.sd.npasses - 1;
-    cc.pd = last;
+  const int last = cc.sd.npasses - 1;
+  if (t >= tend(last)) {
+    take_pass(last);
     return false;
   }
-  int lo = 0, hi = cc.sd.npasses - 1;  // the pass with the largest task_base <= t
+  int lo = 0, hi = last;  // the pass with the largest task_base <= t
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (__ldcg(&cc.sd.passes[mid].task_base) <= t) lo = mid;
+    if (tbase(mid) <= t) lo = mid;
     else hi = mid - 1;
   }
-  cc.P = lo;
-  cc.pd = load_cg(&cc.sd.passes[lo]);
+  take_pass(lo);
   return true;
 }
 
@@ -892,6 +907,14 @@ __device__ __forceinline__ bool locate(ClaimCache &cc, unsigned long long t) {
 __device__ __forceinline__ void mark_exhausted(const CtlStatic &cs, int s, unsigned long long gen) {
   const uint32_t g = slot_flag_gen(gen);
   atomicCAS(&cs.slot_flags[s], g, g | kSlotExhausted);
+}
+
+// Thread 0: take up the descriptor of slot s (coherent loads: the host
+// rewrites it between codes); no pass is cached for it yet.
+__device__ __forceinline__ void refresh_desc(ClaimCache &cc, const SlotDesc *slots, int s) {
+  cc.sd = load_cg(&slots[s]);
+  cc.gen = cc.sd.seq & kGenMask;
+  cc.P = -1;
 }
 
 // Serving: a claim enters the slot before it reads the finished flag and
@@ -926,8 +949,6 @@ __device__ __forceinline__ void take(SlotState *st, const KParams &kp, bool serv
   const int Ukey = key == kNoKey ? cc.sd.n - cc.sd.k + 2 : (int)key_weight(key);
   const int U = cc.sd.seed_u > 0 ? min(Ukey, cc.sd.seed_u) : Ukey;
   const int mid = kp.mid_pass < 0 ? cc.sd.mid_pass_exit : kp.mid_pass;
-  o->sd = cc.sd;
-  o->pd = cc.pd;
   o->task = t - cc.pd.task_base + cc.pd.task_off;
   o->lsplit = 0;
   if (cc.pd.g > 1 && cc.pd.nseg > 0) {
@@ -998,7 +1019,7 @@ template <class SC>
 __device__ __forceinline__ int claim(const SlotDesc *slots, SlotState *states, const CtlStatic &cs,
                                      const KParams &kp, CtlDyn *cd, int &rr, unsigned long long &wait_t0,
                                      unsigned long long t_start, Claim *o, ClaimCache &cc, SC &sc,
-                                     const fpenum::BinomCols &B) {
+                                     const PassDesc *pc, int npc, const fpenum::BinomCols &B) {
   const int nslots = cs.nslots;
   unsigned long long now = globaltimer();
   if (kp.timeout_ns && now - t_start > kp.timeout_ns) {
@@ -1012,62 +1033,56 @@ __device__ __forceinline__ int claim(const SlotDesc *slots, SlotState *states, c
   // Fast path: the slot served last, descriptors cached.  The task counter,
   // the finished flag and the best key are read in one round trip.  A task
   // taken from a code that has finished is dropped (nothing is left to
-  // count for it); one taken from a newer code in the slot is run.
+  // count for it); one taken from a newer code in the slot is run.  Both
+  // paths end in the one call of take() below.
+  int got = -1;  // the slot of the task taken
+  unsigned long long w = 0;
+  uint64_t key = kNoKey;
   if (kp.lookahead && cc.slot >= 0 && cc.P >= 0) {
     const int s = cc.slot;
     SlotState *st = &states[s];
-    unsigned long long w = atomicAdd(&st->word, 1ull);
+    w = atomicAdd(&st->word, 1ull);
     slot_enter(cs, s);
     int fin = ld_vol(&st->finished);
-    uint64_t key = best_key(st);
+    key = best_key(st);
     if ((w >> kGenShift) != cc.gen) {
       __threadfence();  // the descriptor was written before the state was reset
-      cc.sd = load_cg(&slots[s]);
-      cc.gen = cc.sd.seq & kGenMask;
-      cc.P = -1;
+      refresh_desc(cc, slots, s);
       fin = ld_vol(&st->finished);
       key = best_key(st);
     }
     if ((w >> kGenShift) == cc.gen && cc.sd.npasses > 0 && fin != fin_tag(cc.gen)) {
-      if (locate(cc, w & kTaskMask)) {
-        take(st, kp, cs.serve != 0, s, w, key, o, cc, sc, B);
-        rr = s;
-        wait_t0 = 0;
-        cc.sleep_ns = 128;
-        return kCmdRun;
-      }
-      mark_exhausted(cs, s, cc.gen);
+      if (locate(cc, pc, npc, w & kTaskMask)) got = s;
+      else mark_exhausted(cs, s, cc.gen);
     }
-    slot_leave(cs, s);
+    if (got < 0) slot_leave(cs, s);
   }
   bool live = false;
   // four slot flags per load, from the group of the slot served last
   const int ngroups = (nslots + 3) >> 2;
   int q = rr >> 2;
-  for (int qi = 0; qi < ngroups; ++qi, ++q) {
+  for (int qi = 0; qi < ngroups && got < 0; ++qi, ++q) {
     if (q >= ngroups) q = 0;
     const uint4 f4 = __ldcg(reinterpret_cast<const uint4 *>(cs.slot_flags) + q);
-    const uint32_t fl[4] = {f4.x, f4.y, f4.z, f4.w};
 #pragma unroll 1
     for (int b = 0; b < 4; ++b) {
       const int s = 4 * q + b;
       if (s >= nslots) break;
-      if (fl[b] & (kSlotFinished | kSlotExhausted)) continue;
+      const uint32_t fl = b == 0 ? f4.x : b == 1 ? f4.y : b == 2 ? f4.z : f4.w;
+      if (fl & (kSlotFinished | kSlotExhausted)) continue;
       SlotState *st = &states[s];
       if (ld_vol(&st->finished)) continue;
-      unsigned long long w = ld_vol(&st->word);
+      w = ld_vol(&st->word);
       const unsigned long long wgen = w >> kGenShift;
       if (cc.slot != s || cc.gen != wgen) {
         __threadfence();  // the descriptor was written before the state was reset
-        cc.sd = load_cg(&slots[s]);
         cc.slot = s;
-        cc.gen = cc.sd.seq & kGenMask;
-        cc.P = -1;
+        refresh_desc(cc, slots, s);
       }
       if (cc.sd.npasses <= 0) continue;
       live = true;
       if (wgen != cc.gen) continue;  // slot in transition between two codes
-      if (!locate(cc, w & kTaskMask)) {  // every task handed out
+      if (!locate(cc, pc, cc.slot == 0 ? npc : 0, w & kTaskMask)) {  // every task handed out
         mark_exhausted(cs, s, wgen);
         continue;
       }
@@ -1078,15 +1093,13 @@ __device__ __forceinline__ int claim(const SlotDesc *slots, SlotState *states, c
         // the slot now holds a newer code; its descriptor was written before
         // its state, so re-reading it gives the code this task belongs to
         __threadfence();
-        cc.sd = load_cg(&slots[s]);
-        cc.gen = cc.sd.seq & kGenMask;
-        cc.P = -1;
+        refresh_desc(cc, slots, s);
         if (cc.gen != (w >> kGenShift)) {
           slot_leave(cs, s);
           continue;
         }
       }
-      if (!locate(cc, w & kTaskMask)) {
+      if (!locate(cc, pc, cc.slot == 0 ? npc : 0, w & kTaskMask)) {
         mark_exhausted(cs, s, cc.gen);
         slot_leave(cs, s);
         continue;
@@ -1095,12 +1108,17 @@ __device__ __forceinline__ int claim(const SlotDesc *slots, SlotState *states, c
         slot_leave(cs, s);
         continue;
       }
-      take(st, kp, cs.serve != 0, s, w, best_key(st), o, cc, sc, B);
-      rr = s;
-      wait_t0 = 0;
-      cc.sleep_ns = 128;
-      return kCmdRun;
+      key = best_key(st);
+      got = s;
+      break;
     }
+  }
+  if (got >= 0) {
+    take(&states[got], kp, cs.serve != 0, got, w, key, o, cc, sc, B);
+    rr = got;
+    wait_t0 = 0;
+    cc.sleep_ns = 128;
+    return kCmdRun;
   }
   if (!live && !cs.serve) return kCmdExit;
   if (ld_vol(&cd->err)) return kCmdExit;
@@ -1242,6 +1260,8 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
   __shared__ Claim s_cl;
   __shared__ ClaimCache s_cc;
   __shared__ SegCache<V::kSegCache> s_sc;
+  __shared__ __align__(16) PassDesc s_pc[V::kPassCache];  // copied in 16-byte pieces
+  __shared__ int s_npc;
   __shared__ int s_cmd, s_stage;
   __shared__ unsigned long long s_count, s_staged_seq;
   __shared__ int s_staged_slot, s_staged_j;
@@ -1263,6 +1283,7 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
     s_sc.slot = -1;
     s_sc.pass = -1;
     s_sc.gen = 0;
+    s_npc = 0;
   }
   {
     static_assert(kBinomBytes == sizeof(cs.binom->cols), "staged binomial columns");
@@ -1274,10 +1295,19 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
     const SlotDesc sd0 = load_cg(&slots[0]);
     if (sd0.pass_times) sd0.pass_times[kMaxPasses] = t_start;  // launch start
   }
-  if constexpr (V::kSegCache > kSegPass) {
-    // one code: the whole segment list, staged once by every thread
-    if (cs.nslots == 1 && !cs.serve) {
-      const SlotDesc sd0 = load_cg(&slots[0]);
+  if (cs.nslots == 1 && !cs.serve) {
+    // One code: its descriptor, its pass descriptors (when they fit) and
+    // its pair-leaf segments are staged once, so the first claim already
+    // takes the fast path and locates its pass in shared memory.
+    const SlotDesc sd0 = load_cg(&slots[0]);
+    const int np = sd0.npasses;
+    const int npc = np < V::kPassCache ? np : V::kPassCache;  // the first passes: where every CTA starts
+    {
+      const uint4 *src = reinterpret_cast<const uint4 *>(sd0.passes);
+      for (int i = tid; i < npc * (int)(sizeof(PassDesc) / 16); i += kThreads)
+        reinterpret_cast<uint4 *>(s_pc)[i] = __ldcg(src + i);
+    }
+    if constexpr (V::kSegCache > kSegPass) {
       if (sd0.nsegs > 0 && sd0.nsegs <= V::kSegCache) {
         const uint2 *src = reinterpret_cast<const uint2 *>(sd0.passes + sd0.npasses);
         for (int i = tid; i < sd0.nsegs; i += kThreads) reinterpret_cast<uint2 *>(s_sc.seg)[i] = __ldcg(src + i);
@@ -1288,11 +1318,23 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
         }
       }
     }
+    if (tid == 0) {
+      s_cc.sd = sd0;
+      s_cc.slot = 0;
+      s_cc.gen = sd0.seq & kGenMask;
+      s_cc.P = -1;
+      s_npc = npc;
+    }
+    __syncthreads();
+    if (tid == 0 && np > 0) {
+      s_cc.pd = npc ? s_pc[0] : load_cg(&sd0.passes[0]);
+      s_cc.P = 0;
+    }
   }
   __syncthreads();
   for (;;) {
     if (tid == 0) {
-      const int cmd = claim(slots, states, cs, kp, cdyn, rr, wait_t0, t_start, &s_cl, s_cc, s_sc, binom);
+      const int cmd = claim(slots, states, cs, kp, cdyn, rr, wait_t0, t_start, &s_cl, s_cc, s_sc, s_pc, s_npc, binom);
       s_cmd = cmd;
       if (cmd == kCmdRun && cs.serve) {  // keep the serving kernel whole (at most one note per 0.5 ms)
         const unsigned long long now = globaltimer();
@@ -1302,12 +1344,12 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
         }
       }
       if (cmd == kCmdRun) {
-        s_stage = (!s_cl.skip && (s_cl.slot != s_staged_slot || s_cl.pd.j != s_staged_j ||
-                                  s_cl.sd.seq != s_staged_seq)) ? 1 : 0;
+        s_stage = (!s_cl.skip && (s_cl.slot != s_staged_slot || s_cc.pd.j != s_staged_j ||
+                                  s_cc.sd.seq != s_staged_seq)) ? 1 : 0;
         if (s_stage) {
           s_staged_slot = s_cl.slot;
-          s_staged_j = s_cl.pd.j;
-          s_staged_seq = s_cl.sd.seq;
+          s_staged_j = s_cc.pd.j;
+          s_staged_seq = s_cc.sd.seq;
         }
       }
       s_count = 0;
@@ -1323,9 +1365,9 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
     if (s_stage) {
       // eight loads in flight per thread before their stores: one L2 round
       // trip per 32 KiB instead of one per 4 KiB
-      const int words = table_words(s_cl.sd);
+      const int words = table_words(s_cc.sd);
       const int nv = words / 4;
-      const uint4 *src = reinterpret_cast<const uint4 *>(s_cl.sd.table + (size_t)s_cl.pd.j * (size_t)words);
+      const uint4 *src = reinterpret_cast<const uint4 *>(s_cc.sd.table + (size_t)s_cc.pd.j * (size_t)words);
       for (int i0 = tid; i0 < nv; i0 += 8 * kThreads) {
         uint4 v[8];
 #pragma unroll
@@ -1340,7 +1382,7 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
     unsigned long long count = 0;
     SlotAux *ax = cs.aux + slot;
     if (!s_cl.skip)
-      V::run(s_cl.sd, s_cl.pd, s_cl.pass, tab, binom, s_cl.ulo, s_cl.uhi, s_cl.lsplit, s_cl.U, &states[slot], ax, count);
+      V::run(s_cc.sd, s_cc.pd, s_cl.pass, tab, binom, s_cl.ulo, s_cl.uhi, s_cl.lsplit, s_cl.U, &states[slot], ax, count);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) count += __shfl_xor_sync(0xffffffffu, count, o);
     if ((tid & 31) == 0 && count) atomicAdd(&s_count, count);
@@ -1350,11 +1392,32 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
         atomicAdd(&states[slot].enumerated, s_count);
         atomicAdd(&ax->pass_count[s_cl.pass], s_count);
       }
-      finish_task(cs, kp, cdyn, s_cl.sd, &states[slot], ax, slot, s_cl.pass, s_cl.pd, s_cl.ndone);
+      finish_task(cs, kp, cdyn, s_cc.sd, &states[slot], ax, slot, s_cl.pass, s_cc.pd, s_cl.ndone);
       if (cs.inflight) {
         __threadfence();  // the task's writes before it leaves the slot
         slot_leave(cs, slot);
       }
+    }
+  }
+  if (cs.outcome) {
+    // One-code launch: the last CTA to leave copies the final state (the
+    // outcome and the count of every CTA's codewords) to host-mapped memory
+    // and zeroes the dynamic state, so the next search of the code needs no
+    // reset and its result no copy of its own.
+    __shared__ int s_last;
+    if (tid == 0) {
+      __threadfence();  // this CTA's writes before its count
+      s_last = atomicAdd(&cdyn->exited, 1u) == gridDim.x - 1 ? 1 : 0;
+      if (s_last) __threadfence();
+    }
+    __syncthreads();
+    if (s_last) {
+      const uint4 *src = reinterpret_cast<const uint4 *>(states);
+      uint4 *dst = reinterpret_cast<uint4 *>(cs.outcome);
+      for (int i = tid; i < (int)(cs.dyn_bytes / 16); i += kThreads) dst[i] = __ldcg(src + i);
+      __syncthreads();
+      uint4 *z = reinterpret_cast<uint4 *>(states);
+      for (int i = tid; i < (int)(cs.clean_bytes / 16); i += kThreads) z[i] = make_uint4(0u, 0u, 0u, 0u);
     }
   }
 }
