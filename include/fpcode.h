@@ -170,10 +170,14 @@ void fpcode_prepared_free(fpcode_prepared *prep);
  * Errors: FPCODE_ENOMEM, FPCODE_ECUDA. */
 int fpcode_prepared_upload(fpcode_prepared *prep, void *stream);
 
-/* Enqueue one device search on the uploaded `prep` (state reset, the
- * persistent kernel, and the read-back into pinned host memory of `prep`)
- * without synchronising.  Pair with fpcode_search_finish on the same
- * stream.  Errors: FPCODE_EINVAL (not uploaded), FPCODE_ECUDA. */
+/* Enqueue one device search on the uploaded `prep` without synchronising:
+ * the persistent kernel, whose last CTA copies the final state into
+ * host-mapped memory of `prep` and zeroes the device state for the next
+ * search.  The first search after fpcode_prepared_upload is preceded by a
+ * state reset; where the memory cannot be mapped, every search is, and its
+ * state is copied back after the kernel.  Pair with fpcode_search_finish on the same stream; one search
+ * of a prepared object at a time.  Errors: FPCODE_EINVAL (not uploaded),
+ * FPCODE_ECUDA. */
 int fpcode_search_enqueue(fpcode_prepared *prep, void *stream, const fpcode_opts *opts);
 
 /* Synchronise `stream` and decode the last enqueued search into *res and,
