@@ -78,12 +78,19 @@ int fpcode_test_task_ranges(fpcode_prepared *prep, int pass, int ctas, int fixed
  * (p-1) C(k-1-q, 2) with q the stem's largest row (g = 2: all pairs).
  * Returns the words per entry, or a negative status. */
 int fpcode_test_pair_mode(const fpcode_prepared *prep, int pass, uint64_t J, uint32_t *entries);
-/* Stored pair-table entry e of Gamma_j (pair leaves): its pair_sigp words
- * (the signature words of B = A_j[y] + c A_j[x], word w's r - 1 words at
- * [w * (r - 1)], then zeros), followed by slice 0 of B (W words).  `sig`
- * holds up to 12 words.  Returns the number of words, or a negative
- * status. */
+/* Pair-table entry e of Gamma_j (pair leaves), computed on the host from
+ * the prepared multiples: its pair_sigp words (the signature words of
+ * B = A_j[y] + c A_j[x], word w's r - 1 words at [w * (r - 1)], then
+ * zeros), followed by slice 0 of B (W words).  `sig` holds up to 12 words.
+ * Returns the number of words, or a negative status. */
 int fpcode_test_pair_entry(const fpcode_prepared *prep, int j, uint32_t e, uint32_t *sig);
+/* The pair table of Gamma_j as the kernels build it in shared memory
+ * (Sec. 4.3 with pair leaves): one CTA stages the set's multiples, runs the
+ * builder and copies the table out: all entries' pair_sigp signature words
+ * (padded to 16 bytes), then all entries' slice 0 (W words each).  `out`
+ * holds max_words u32 (host memory); runs on the current device,
+ * synchronously.  Returns the table's words, or a negative status. */
+int fpcode_test_pair_table_device(const fpcode_prepared *prep, int j, uint32_t *out, int max_words);
 /* The coordinate search of fpcode_autotune_batch over a synthetic cost
  * table: ndim settings with sizes[i] values each, cost[] in row-major order
  * (the last setting fastest), starting at index vector `start`.  best

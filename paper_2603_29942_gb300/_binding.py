@@ -193,6 +193,7 @@ def _declare(lib):
         "fpcode_test_pair_mode": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint32)]),
         "fpcode_test_key_coefficients": (ctypes.c_int, [_VP, ctypes.c_uint64, _IP, _IP, _IP]),
         "fpcode_test_pair_entry": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]),
+        "fpcode_test_pair_table_device": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int]),
         "fpcode_prepared_pass_slice": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
                                                       ctypes.POINTER(_VP)]),
         "fpcode_prepared_codeword": (ctypes.c_int, [_VP, ctypes.c_uint64, _U8P, _IP]),
@@ -736,13 +737,25 @@ def fpcode_test_pair_mode(prep: Prepared, pass_index: int = -1, J: int = 0):
 
 
 def fpcode_test_pair_entry(prep: Prepared, j: int, e: int) -> list[int]:
-    """The stored words of pair-table entry e of information set j: its
-    signature (pair_sigp words), then slice 0 of B (W words)."""
+    """The words of pair-table entry e of information set j, computed on
+    the host: its signature (pair_sigp words), then slice 0 of B (W words)."""
     sig = (ctypes.c_uint32 * 16)()
     n = lib().fpcode_test_pair_entry(prep.handle, int(j), int(e), sig)
     if n < 0:
         raise FpcodeError(-n, "fpcode_test_pair_entry")
     return [int(sig[i]) for i in range(n)]
+
+
+def fpcode_test_pair_table_device(prep: Prepared, j: int) -> np.ndarray:
+    """The pair table of information set j as the kernels build it in shared
+    memory (u32 words: signatures of all entries, padded, then slice 0)."""
+    cap = 1 << 16
+    out = np.zeros(cap, dtype=np.uint32)
+    n = lib().fpcode_test_pair_table_device(prep.handle, int(j), out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                            cap)
+    if n < 0:
+        raise FpcodeError(-n, "fpcode_test_pair_table_device")
+    return out[:n].copy()
 
 
 def fpcode_test_key_coefficients(prep: Prepared, key: int):

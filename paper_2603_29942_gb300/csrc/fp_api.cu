@@ -270,7 +270,7 @@ int launch(const void *fn, int ctas, int smem, cudaStream_t st, char *d, const L
 // of one information set.
 int smem_for(const std::vector<const fph::Prepared *> &codes) {
   size_t s = 16;
-  for (auto *P : codes) s = std::max(s, P->table_bytes_per_set());
+  for (auto *P : codes) s = std::max(s, P->smem_bytes_per_set());
   return (int)(((s + 15) & ~(size_t)15) + fpk::kBinomBytes);
 }
 
@@ -855,6 +855,36 @@ int fpcode_test_pass_times(fpcode_prepared *prep, void *stream, double *us, int 
   const int n = std::min<int>(max, (int)prep->host.passes.size());
   for (int i = 0; i < n; ++i) us[i] = t[i] >= t[fpk::kMaxPasses] ? (double)(t[i] - t[fpk::kMaxPasses]) * 1e-3 : -1.0;
   return n;
+}
+
+int fpcode_test_pair_table_device(const fpcode_prepared *prep, int j, uint32_t *out, int max_words) {
+  const fph::Prepared *P = prep ? &prep->host : nullptr;
+  if (!P || !P->pair || j < 0 || j >= P->m || !out || max_words < 0) return -FPCODE_EINVAL;
+  const int words = (int)P->pair_words_per_set();
+  if (words > max_words) return -FPCODE_EINVAL;
+  const void *fn = P->p == 3 ? fpk::pair_table_kernel_p3(P->W) : fpk::pair_table_kernel_p7(P->W);
+  if (!fn) return -FPCODE_EINVAL;
+  const size_t mw = P->table_words_per_set();
+  const int smem = (int)P->smem_bytes_per_set();
+  uint32_t *d_rows = nullptr, *d_out = nullptr;
+  cudaError_t e = cudaMalloc(&d_rows, mw * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&d_out, (size_t)words * 4 + 4);
+  if (e == cudaSuccess) e = cudaMemcpy(d_rows, &P->table[(size_t)j * mw], mw * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && smem > 48 * 1024) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) {
+    const uint32_t *rows = d_rows;
+    int k = P->k, rwpad = P->rwpad, sigp = P->pair_sigp, ow = words;
+    void *args[] = {(void *)&rows, (void *)&k, (void *)&rwpad, (void *)&sigp, (void *)&d_out, (void *)&ow};
+    e = cudaLaunchKernel(fn, dim3(1), dim3(fpk::kThreads), args, (size_t)smem, 0);
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(out, d_out, (size_t)words * 4, cudaMemcpyDeviceToHost);
+  if (d_rows) cudaFree(d_rows);
+  if (d_out) cudaFree(d_out);
+  if (e != cudaSuccess) {
+    fph::set_error(cudaGetErrorString(e));
+    return -FPCODE_ECUDA;
+  }
+  return words;
 }
 
 int fpcode_prepared_bytes(const fpcode_prepared *prep, uint64_t *h2d, uint64_t *d2h) {

@@ -151,26 +151,25 @@ void add_sliced_words(int r, const uint32_t *a, const uint32_t *b, uint32_t *s, 
   }
 }
 
-// Pair table of one information set (pair leaves, p = 3 or 7): for y from
-// k - 2 down to 0, x from y + 1 up, c from 1 to p - 1, the signature words
-// B_i xor B_{i+1} of B = A[y] + c A[x] (the exact add of Alg. 3 / Alg. 4)
-// and B's slice 0.  rows: the set's multiples, rwpad words each.
+// Entry e of an information set's pair table (pair leaves, p = 3 or 7),
+// as the kernel builds it in shared memory: entries run over y from k - 2
+// down to 0, x from y + 1 up, c from 1 to p - 1; entry (y, x, c) holds the
+// signature words B_i xor B_{i+1} of B = A[y] + c A[x] (the exact add of
+// Alg. 3 / Alg. 4), zero-padded to sp words, then B's slice 0 (W words).
+// rows: the set's multiples, rwpad words each.
 template <int P, int R>
-void build_pair_table(const uint32_t *rows, int k, int rwpad, int W, int sp, uint32_t *pt, uint32_t *p0) {
+void pair_entry(const uint32_t *rows, int k, int rwpad, int W, int sp, uint32_t e, uint32_t *out) {
   constexpr int b = P - 1;
-  size_t e = 0;
-  for (int y = k - 2; y >= 0; --y) {
-    const uint32_t *ay = rows + (size_t)y * b * rwpad;
-    for (int x = y + 1; x < k; ++x)
-      for (int c = 1; c <= b; ++c, ++e) {
-        const uint32_t *ax = rows + ((size_t)x * b + (c - 1)) * rwpad;
-        for (int w = 0; w < W; ++w) {
-          uint32_t sum[R];
-          fpbs::add_exact<P, R>(ay + w * R, ax + w * R, sum, P);
-          for (int i = 0; i + 1 < R; ++i) pt[e * sp + (size_t)w * (R - 1) + i] = sum[i] ^ sum[i + 1];
-          p0[e * W + w] = sum[0];
-        }
-      }
+  int y = 0, x = 0, c = 0;
+  fpk::pair_entry_rows(k, b, e, &y, &x, &c);
+  const uint32_t *ay = rows + (size_t)y * b * rwpad;
+  const uint32_t *ax = rows + ((size_t)x * b + (c - 1)) * rwpad;
+  for (int q = 0; q < sp; ++q) out[q] = 0;
+  for (int w = 0; w < W; ++w) {
+    uint32_t sum[R];
+    fpbs::add_exact<P, R>(ay + w * R, ax + w * R, sum, P);
+    for (int i = 0; i + 1 < R; ++i) out[w * (R - 1) + i] = sum[i] ^ sum[i + 1];
+    out[sp + w] = sum[0];
   }
 }
 
@@ -287,7 +286,7 @@ int prepare(int p, int n, int k, const uint8_t *G, const fpcode_opts &opts, Prep
     }
     P->code_hash = h;
   }
-  if (P->table_bytes_per_set() > 96 * 1024) {
+  if (P->smem_bytes_per_set() > 96 * 1024) {
     set_error("bit-sliced multiples of one information set exceed 96 KiB (k (p-1) r W too large)");
     return FPCODE_EINVAL;
   }
@@ -385,20 +384,10 @@ int prepare(int p, int n, int k, const uint8_t *G, const fpcode_opts &opts, Prep
       }
     }
 
-  // Pair table of each set (pair leaves): for y from k - 2 down to 0, x
-  // from y + 1 up, c from 1 to p - 1: the pair signature words
-  // B_i xor B_{i+1} of B = A[y] + c A[x] (exact bit-sliced add), word w's
-  // r - 1 words at [w * (r - 1)], padded to pair_sigp words.
+  // Pair leaves: the kernel builds each set's pair table from the staged
+  // multiples (fp_kernel.cuh, build_pairs); only its threshold rule is
+  // set here.
   if (P->pair) {
-    const int SP = P->pair_sigp;
-    const size_t NE = P->pair_entries();
-    for (int j = 0; j < m; ++j) {
-      const uint32_t *rows = &P->table[(size_t)j * set_words];
-      uint32_t *pt = &P->table[(size_t)j * set_words + (size_t)k * (p - 1) * RWP];
-      uint32_t *p0 = pt + ((NE * (size_t)SP + 3) & ~(size_t)3);  // slice 0 of each entry
-      if (p == 3) build_pair_table<3, 2>(rows, k, RWP, W, SP, pt, p0);
-      else build_pair_table<7, 3>(rows, k, RWP, W, SP, pt, p0);
-    }
     // The one-popcount bound ORs the words of a pair mask before counting,
     // so a bit of it covers one position per word.  A position is set in a
     // pair mask with chance rho (p = 3: 4/9, p = 7: 36/49, for random
@@ -530,16 +519,17 @@ void plan_pair_pass(Prepared *P, fpk::PassDesc &d, uint64_t C) {
       for (int q = g - 3; q <= k - 3; ++q)
         blks.push_back({h, q, binom().c[q][g - 3] * d.NC, (uint64_t)fpk::pair_entries_above(k, q, b)});
   }
-  long double rem = 0;
-  for (auto &x : blks) rem += (long double)x.n * (long double)(x.E + kStemCost);
+  // work in entries plus the stems' cost: below 2^33 stems x 2^14 entries per block, so exact in 64 bits
+  uint64_t rem = 0;
+  for (auto &x : blks) rem += x.n * (x.E + kStemCost);
   // A small pass (the first passes of a search, which run before records
   // exist and send most entries down the exact path) is spread as wide as
   // the grid allows: one stem per group, a stem's entries over as many
   // lanes as keeps two loads per lane.
-  const bool spread = rem <= (long double)(C * lanes * kSpreadLane);
+  const bool spread = rem <= C * lanes * kSpreadLane;
   const uint64_t Tmin = P->opts.task_work > 0 ? (uint64_t)P->opts.task_work : kMinTaskLane;
   const uint64_t share = P->opts.task_share > 0 ? (uint64_t)P->opts.task_share : kTaskShare;
-  const uint64_t T_spread = std::max<uint64_t>(2, (uint64_t)(rem / (long double)(C * lanes)) + 1);
+  const uint64_t T_spread = std::max<uint64_t>(2, rem / (C * lanes) + 1);
   // Stems of one group start on the same phase of the coefficient counter
   // (units of (p-1)^t stems, t <= g - 3), so the lanes of a warp take the
   // same Gray steps and rebuild their sums at the same stem.
@@ -556,7 +546,7 @@ void plan_pair_pass(Prepared *P, fpk::PassDesc &d, uint64_t C) {
   };
   for (auto &x : blks) {
     const uint64_t T =
-        spread ? T_spread : std::max<uint64_t>(Tmin, (uint64_t)(rem / (long double)(share * C * lanes)));
+        spread ? T_spread : std::max<uint64_t>(Tmin, rem / (share * C * lanes));
     int l = 0;
     // split a stem's entries while one lane's share exceeds the target, or
     // while the block cannot give every group a stem (at least two entry
@@ -585,7 +575,7 @@ void plan_pair_pass(Prepared *P, fpk::PassDesc &d, uint64_t C) {
       cur_n = 0;
     }
     cur_n += x.n;
-    rem -= (long double)x.n * (long double)(x.E + kStemCost);
+    rem -= x.n * (x.E + kStemCost);
   }
   close();
   d.nseg = (uint32_t)P->segs.size() - d.seg_off;
@@ -997,11 +987,9 @@ int fpcode_test_pair_entry(const fpcode_prepared *prep, int j, uint32_t e, uint3
   if (!P || !P->pair || j < 0 || j >= P->m || !sig) return -FPCODE_EINVAL;
   const uint32_t ne = (uint32_t)(P->p - 1) * (uint32_t)(P->k * (P->k - 1) / 2);
   if (e >= ne) return -FPCODE_EINVAL;
-  const size_t set_words = P->table_words_per_set();
-  const uint32_t *pt = &P->table[(size_t)j * set_words + (size_t)P->k * (P->p - 1) * P->rwpad];
-  std::memcpy(sig, pt + (size_t)e * P->pair_sigp, (size_t)P->pair_sigp * sizeof(uint32_t));
-  const uint32_t *p0 = pt + ((P->pair_entries() * (size_t)P->pair_sigp + 3) & ~(size_t)3);
-  std::memcpy(sig + P->pair_sigp, p0 + (size_t)e * P->W, (size_t)P->W * sizeof(uint32_t));
+  const uint32_t *rows = &P->table[(size_t)j * P->table_words_per_set()];
+  if (P->p == 3) fph::pair_entry<3, 2>(rows, P->k, P->rwpad, P->W, P->pair_sigp, e, sig);
+  else fph::pair_entry<7, 3>(rows, P->k, P->rwpad, P->W, P->pair_sigp, e, sig);
   return P->pair_sigp + P->W;
 }
 

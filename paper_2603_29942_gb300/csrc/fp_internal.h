@@ -37,7 +37,7 @@ struct Prepared {
   std::vector<uint8_t> gam;      // m * k * n: Gamma_j, rows in pivot order
   std::vector<int> piv;          // m * k pivot columns (increasing)
   std::vector<int> red;          // m * (n - k) non-pivot columns (increasing)
-  std::vector<uint32_t> table;   // per set: k * (p-1) * rwpad bit-sliced multiples, then its signatures
+  std::vector<uint32_t> table;   // per set: k * (p-1) * rwpad bit-sliced multiples, then (one-row leaves) the row signatures
   std::vector<fpk::PassDesc> passes;
   // Pair leaves (fp_types.h): passes with g >= 2 read a table of pair
   // signatures of A[y] + c A[x] and the segments of the task plan.
@@ -58,11 +58,16 @@ struct Prepared {
                 : 0;
   }
   int pair_quick_max = 0;        // thresholds up to this take the one-popcount pair bound
+  // Words of one information set in the uploaded table: the multiples, and
+  // for one-row leaves the row signatures.  Pair leaves upload only the
+  // multiples; the kernel builds the pair table from them in shared memory.
   size_t table_words_per_set() const {
-    return pair ? (size_t)k * (size_t)(p - 1) * rwpad + pair_words_per_set()
+    return pair ? (size_t)k * (size_t)(p - 1) * rwpad
                 : (size_t)k * ((size_t)(p - 1) * rwpad + fpk::sig_words(p, r, W));
   }
   size_t table_bytes_per_set() const { return table_words_per_set() * 4; }
+  // Shared memory one staged information set takes (with the pair table).
+  size_t smem_bytes_per_set() const { return (table_words_per_set() + pair_words_per_set()) * 4; }
 };
 
 // Elimination, information sets, multiples, schedule.  Returns an fpcode

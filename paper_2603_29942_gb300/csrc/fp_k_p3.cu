@@ -13,4 +13,13 @@ const void *kernel_p3(int W) {
     default: return nullptr;
   }
 }
+const void *pair_table_kernel_p3(int W) {
+  switch (W) {
+    case 1: return (const void *)pair_table_kernel<3, 2, 1>;
+    case 2: return (const void *)pair_table_kernel<3, 2, 2>;
+    case 3: return (const void *)pair_table_kernel<3, 2, 3>;
+    case 4: return (const void *)pair_table_kernel<3, 2, 4>;
+    default: return nullptr;
+  }
+}
 }  // namespace fpk

@@ -13,4 +13,13 @@ const void *kernel_p7(int W) {
     default: return nullptr;
   }
 }
+const void *pair_table_kernel_p7(int W) {
+  switch (W) {
+    case 1: return (const void *)pair_table_kernel<7, 3, 1>;
+    case 2: return (const void *)pair_table_kernel<7, 3, 2>;
+    case 3: return (const void *)pair_table_kernel<7, 3, 3>;
+    case 4: return (const void *)pair_table_kernel<7, 3, 4>;
+    default: return nullptr;
+  }
+}
 }  // namespace fpk

@@ -78,12 +78,12 @@ struct CtlDyn {
 constexpr int kBinomCols = fpenum::kBinomCols;
 constexpr int kBinomBytes = kBinomCols * (fpenum::kMaxK + 1) * 8;  // 12480, a multiple of 16
 
-// Words of one information set's table: multiples, then pair signatures.
+// Words of one information set's table in global memory: the multiples,
+// then (one-row leaves) the row signatures.  Pair leaves keep only the
+// multiples there; the CTA builds the pair table after them in shared
+// memory when it stages the set (build_pairs).
 __device__ __forceinline__ int table_words(const SlotDesc &sd) {
-  if (sd.pair_sigp > 0) {  // row multiples, then the pair signatures and slice 0 of each entry (16-byte padded)
-    const int ne = (sd.p - 1) * (sd.k * (sd.k - 1) / 2);
-    return sd.k * (sd.p - 1) * sd.rwpad + ((ne * sd.pair_sigp + 3) & ~3) + ((ne * sd.W + 3) & ~3);
-  }
+  if (sd.pair_sigp > 0) return sd.k * (sd.p - 1) * sd.rwpad;
   return sd.k * ((sd.p - 1) * sd.rwpad + sig_words(sd.p, sd.r, sd.W));
 }
 
@@ -482,6 +482,59 @@ __device__ void task_prefixes(const SlotDesc &sd, const PassDesc &pd, int pass, 
 // is read once per stem (the load issued before the stem's entries, used
 // after them).
 // ---------------------------------------------------------------------------
+// Pair table of the staged information set, built by the CTA in shared
+// memory from the set's staged multiples (tab): entries run over pairs
+// y < x of rows by y descending, then x, then c in [1, p); entry (y, x, c)
+// holds the pair signature words B_i xor B_{i+1} of B = A[y] + c A[x] (the
+// exact add), zero-padded to sigp words, and, after all signatures (padded
+// to 16 bytes), B's slice 0.  The same table the host hook
+// fpcode_test_pair_entry computes, entry by entry.
+template <int P, int R, int W>
+__device__ __noinline__ void build_pairs(uint32_t *tab, int k, int rwpad, int sigp) {
+  constexpr int b = P - 1;
+  const int ne = b * (k * (k - 1) / 2);
+  uint32_t *pt = tab + k * b * rwpad;
+  uint32_t *p0 = pt + ((ne * sigp + 3) & ~3);
+  for (int e = threadIdx.x; e < ne; e += kThreads) {
+    // e = b P + (c - 1); pair P counts down the triangle: t = k - 1 - y rows
+    // above y, the largest t with t (t - 1) / 2 <= P
+    const uint32_t Pq = (uint32_t)e / (uint32_t)b;
+    const int c = e - (int)Pq * b + 1;
+    uint32_t t = (uint32_t)((1.0f + sqrtf(8.0f * (float)Pq + 1.0f)) * 0.5f);
+    while (t > 1 && t * (t - 1) / 2 > Pq) --t;
+    while ((t + 1) * t / 2 <= Pq) ++t;
+    const int y = k - 1 - (int)t;
+    const int x = y + 1 + (int)(Pq - t * (t - 1) / 2);
+    const uint32_t *ay = tab + y * b * rwpad;
+    const uint32_t *ax = tab + (x * b + (c - 1)) * rwpad;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      uint32_t sum[R];
+      fpbs::add_exact<P, R>(ay + w * R, ax + w * R, sum, P);
+#pragma unroll
+      for (int i = 0; i + 1 < R; ++i) pt[e * sigp + w * (R - 1) + i] = sum[i] ^ sum[i + 1];
+      p0[e * W + w] = sum[0];
+    }
+    for (int q = W * (R - 1); q < sigp; ++q) pt[e * sigp + q] = 0u;
+  }
+}
+
+// Test hook kernel: one CTA of kThreads stages the multiples of one
+// information set (k (p-1) rwpad words at rows) into shared memory, builds
+// its pair table there (build_pairs) and copies the pair table out.
+template <int P, int R, int W>
+__global__ void __launch_bounds__(kThreads) pair_table_kernel(const uint32_t *rows, int k, int rwpad, int sigp,
+                                                             uint32_t *out, int out_words) {
+  extern __shared__ uint4 smem_pairs[];
+  uint32_t *tab = reinterpret_cast<uint32_t *>(smem_pairs);
+  const int mw = k * (P - 1) * rwpad;
+  for (int i = threadIdx.x; i < mw; i += kThreads) tab[i] = rows[i];
+  __syncthreads();
+  build_pairs<P, R, W>(tab, k, rwpad, sigp);
+  __syncthreads();
+  for (int i = threadIdx.x; i < out_words; i += kThreads) out[i] = tab[mw + i];
+}
+
 template <int P, int R, int W>
 struct PairShape {
   static constexpr int SW = W * (R - 1);                                    // signature words of an entry
@@ -778,6 +831,12 @@ struct Fixed {
   static constexpr int DB = P == 3 ? 1 : (P == 5 || P == 7) ? 4 : 8;  // as the host's digit width
   static constexpr int kSegCache = PAIRS ? 768 : 1;  // pair-leaf segments held in shared memory
   static constexpr int kPassCache = 24;                // pass descriptors held in shared memory (one code)
+  // after staging a set: its pair table (pair-leaf codes), built in shared memory
+  static __device__ __forceinline__ void stage_pairs(uint32_t *tab, const SlotDesc &sd) {
+    if constexpr (PAIRS && (P == 3 || P == 7)) {
+      if (sd.pair_sigp > 0) build_pairs<P, R, W>(tab, sd.k, sd.rwpad, sd.pair_sigp);
+    }
+  }
   static __device__ __forceinline__ void run(const SlotDesc &sd, const PassDesc &pd, int pass, const uint32_t *tab,
                                              const fpenum::BinomCols &B, uint64_t ulo, uint64_t uhi, int lsplit,
                                              int U, SlotState *st, SlotAux *ax, unsigned long long &count) {
@@ -805,6 +864,7 @@ template <int WMAX>
 struct Multi357 {
   static constexpr int kSegCache = 1;  // batches take one-row leaves
   static constexpr int kPassCache = 1;  // and read their pass descriptors from global memory
+  static __device__ __forceinline__ void stage_pairs(uint32_t *, const SlotDesc &) {}  // one-row leaves only
   static __device__ __forceinline__ void run(const SlotDesc &sd, const PassDesc &pd, int pass, const uint32_t *tab,
                                              const fpenum::BinomCols &B, uint64_t ulo, uint64_t uhi, int lsplit,
                                              int U, SlotState *st, SlotAux *ax, unsigned long long &count) {
@@ -1378,6 +1438,10 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
           if (i0 + u * kThreads < nv) tab4[i0 + u * kThreads] = v[u];
       }
       __syncthreads();
+      if (s_cc.sd.pair_sigp > 0) {
+        V::stage_pairs(tab, s_cc.sd);
+        __syncthreads();
+      }
     }
     unsigned long long count = 0;
     SlotAux *ax = cs.aux + slot;

@@ -8,6 +8,9 @@ const void *kernel_p5(int W);
 const void *kernel_p7(int W);
 const void *kernel_generic(int r, int W);
 const void *kernel_mersenne(int p, int W);  // p = 31 or 127
+// Test hook: the pair-table builder of the p = 3 / 7 kernels, alone.
+const void *pair_table_kernel_p3(int W);
+const void *pair_table_kernel_p7(int W);
 // Batched kernel dispatching per task over p in {3, 5, 7}, W in 1..4.
 const void *kernel_multi357_narrow();  // W <= 2
 const void *kernel_multi357_wide();    // W <= 4

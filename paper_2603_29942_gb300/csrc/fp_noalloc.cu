@@ -122,7 +122,7 @@ extern "C" int fpcode_min_distance_noalloc(int p, int n, int k, const uint8_t *G
     fph::set_error("fpcode_min_distance_noalloc: no kernel for this (p, n - k)");
     return FPCODE_EINVAL;
   }
-  const int smem = (int)(((std::max<size_t>(16, P.table_bytes_per_set()) + 15) & ~(size_t)15) + fpk::kBinomBytes);
+  const int smem = (int)(((std::max<size_t>(16, P.smem_bytes_per_set()) + 15) & ~(size_t)15) + fpk::kBinomBytes);
   int per_sm = 0, sms = 0;
   s = fpd::occupancy(fn, smem, P.opts.ctas_per_sm, &per_sm);  // sets the message when nothing fits
   if (s) return s;

@@ -282,7 +282,7 @@ int fpcode_serve_submit(fpcode_server *s, const fpcode_desc *code, uint64_t *tic
     return FPCODE_EINVAL;
   }
   const size_t table_bytes = P->table.size() * sizeof(uint32_t);
-  if (P->table_bytes_per_set() > kServeTableSet || table_bytes > kServeTableCode) {
+  if (P->smem_bytes_per_set() > kServeTableSet || table_bytes > kServeTableCode) {
     fph::set_error("serve: code tables too large for a serving slot");
     return FPCODE_EINVAL;
   }

@@ -419,3 +419,26 @@ def test_lookahead_keeps_the_schedule(name, lookahead):
         if mid == 0:
             assert res.enumerated == exp["evaluated"]
         check_witness(code, res.d, res.witness)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("p,n,k", [(3, 80, 40), (7, 40, 20), (3, 150, 30), (7, 90, 12), (3, 20, 3)])
+def test_device_pair_table_matches_definition(p, n, k):
+    """The pair table the kernels build in shared memory from the staged
+    multiples equals, entry by entry, the host's computation of its
+    definition (the signature words and slice 0 of B = A[y] + c A[x])."""
+    code = inputs.single_code(11 + n, p, n, k)
+    pr = B.fpcode_prepare(code.p, code.n, code.k, code.G, B.fpcode_opts_default(pair_leaves=1))
+    sigp = B.fpcode_test_pair_mode(pr)
+    assert sigp > 0
+    m = B.fpcode_prepared_shape(pr)[0]
+    W = -(-(n - k) // 32)
+    ne = (p - 1) * (k * (k - 1) // 2)
+    off0 = (ne * sigp + 3) & ~3
+    for j in range(m):
+        dev = B.fpcode_test_pair_table_device(pr, j)
+        assert len(dev) == off0 + ((ne * W + 3) & ~3)
+        for e in range(ne):
+            host = B.fpcode_test_pair_entry(pr, j, e)
+            assert list(dev[e * sigp:(e + 1) * sigp]) == host[:sigp], (j, e)
+            assert list(dev[off0 + e * W:off0 + (e + 1) * W]) == host[sigp:], (j, e)
