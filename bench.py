@@ -77,7 +77,13 @@ FLUSH_BYTES = 256 << 20
 # version that was profiled; any later change of their code reports null
 # (the hash skips comments and blank lines).
 KERNEL_SOURCES = ["fp_kernel.cuh", "fp_enum.cuh", "fp_bitslice.cuh", "fp_types.h"]
-PROFILED_TRAFFIC: dict = {}
+_SHA_PROFILED = "40d4004593325c9abe410be6bfee9680be8cedb7d57a92fa3662fd6c66c18a9a"
+PROFILED_TRAFFIC: dict = {  # profiles/bz_kernel_*.md (the command of each capture is there)
+    "f3_n80_k40": {"bytes": 4787712 + 512, "sources_sha256": _SHA_PROFILED},
+    "probe_f3_n80_k40_g8": {"bytes": 4777984 + 53760, "sources_sha256": _SHA_PROFILED},
+    "f7_n40_k20": {"bytes": 9477888 + 0, "sources_sha256": _SHA_PROFILED},
+    "probe_f7_n40_k20_g7": {"bytes": 7575040 + 0, "sources_sha256": _SHA_PROFILED},
+}
 
 
 def code_of(text: str) -> str:
@@ -375,7 +381,7 @@ def probe_line(torch, B, code, name, g, d, stream, flush, peak_t, steps=5, warmu
     W = max(1, -(-(code.n - code.k) // 32))
     ach = size * W / (k_ms * 1e-3) / 1e12
     return {"bound": "alu", "achieved": ach, "peak": peak_t, "unit": "Tpopc/s", "frac": ach / peak_t,
-            "pass": [g, 0], "codewords": size, "kernel_ms": k_ms, "workload": name,
+            "traffic": profiled_traffic(name), "pass": [g, 0], "codewords": size, "kernel_ms": k_ms, "workload": name,
             "leaf_form": "pair" if B.fpcode_test_pair_mode(pr) else "one-row", "least_weight_in_pass": least,
             "note": "the same kernel on one pass of fixed size alone, termination off, U seeded at d"}
 
@@ -436,9 +442,14 @@ def batch_measure(args, torch, B, rank, world) -> dict:
     t_batch = max_over_ranks((time.perf_counter() - t0) / reps, world)
     launches = sorted({r.launch for r in res})
     kernel_ms = sum(next(r.t_kernel_ms for r in res if r.launch == L) for L in launches)
+    # one launch per code, with the task plan of a single code (min_steps 8)
+    one = B.fpcode_opts_default(min_steps=8)
+    for c in codes[:8]:
+        B.fpcode_min_distance_batch([c], stream, opts=one, budgets=[budget], want_witness=True)
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     for c in codes:
-        B.fpcode_min_distance_batch([c], stream, opts=opts, budgets=[budget], want_witness=True)
+        B.fpcode_min_distance_batch([c], stream, opts=one, budgets=[budget], want_witness=True)
     torch.cuda.synchronize()
     t_single = max_over_ranks(time.perf_counter() - t0, world)
     certified = int(sum_over_ranks(sum(r.status == B.OK for r in res), world))
@@ -447,7 +458,8 @@ def batch_measure(args, torch, B, rank, world) -> dict:
             "certified": certified, "budget_limited": len(all_codes) - certified, "codewords": work,
             "kernel_ms": kernel_ms, "launches_per_batch": len(launches),
             "per_code": {"codes_per_s": len(all_codes) / t_single, "ms_total": 1e3 * t_single,
-                         "form": "fpcode_min_distance_batch on one code at a time (one launch per code)"},
+                         "form": "fpcode_min_distance_batch on one code at a time (one launch per code, "
+                                 "single-code task plan)"},
             "batched_over_per_code": t_single / t_batch,
             "tuning": tuning,
             "timing": "end to end from host matrices (host preparation on all cores, H2D, launches, D2H), "
@@ -567,7 +579,8 @@ def run_default(args, rank, world, local):
                 "d": f7["res"].d, "time_to_certified_d_ms": t7, "kernel_ms": k7,
                 "codewords_per_step": f7["codewords"], "codewords_per_s": world * f7["codewords"] / (t7 * 1e-3),
                 "roofline": {"bound": "alu", "achieved": a7, "peak": peak["tpopc_s"], "unit": "Tpopc/s",
-                             "frac": a7 / peak["tpopc_s"], "ops_per_codeword": f7["W"], "leaf_form": f7["leaf_form"]},
+                             "frac": a7 / peak["tpopc_s"], "traffic": profiled_traffic(name7),
+                             "ops_per_codeword": f7["W"], "leaf_form": f7["leaf_form"]},
                 "roofline_pass_probe": probe_line(torch, B, f7["code"], "probe_f7_n40_k20_g7", 7, f7["res"].d, stream,
                                                   flush, peak["tpopc_s"]),
                 "gpu_launches": args.steps}
