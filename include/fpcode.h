@@ -111,7 +111,10 @@ typedef struct fpcode_opts {
                           p in {3, 5, 7} goes to the narrow batched kernel
                           (0 or 2: n - k <= 64, the others in a second,
                           wide launch; 4: every such code in one wide
-                          launch) */
+                          launch); 1: one launch per kernel variant (prime
+                          class and words per slice) of the single-code
+                          kernels, where codes of p = 3, 7 may take pair
+                          leaves (pair_leaves) */
 } fpcode_opts;
 
 typedef struct fpcode_result {
@@ -232,6 +235,12 @@ int fpcode_search_resume(fpcode_prepared *prep, const fpcode_checkpoint *ck, voi
  * Errors: FPCODE_EINVAL (no such pass, an empty range). */
 int fpcode_prepared_pass_slice(const fpcode_prepared *src, int pass, uint64_t task_lo, uint64_t task_hi, int u_init,
                                fpcode_prepared **out);
+
+/* The first bound of the next searches of a slice made by
+ * fpcode_prepared_pass_slice (0: none), so that one uploaded slice serves
+ * every search of the split: the bound changes, the tables stay.  Errors:
+ * FPCODE_EINVAL (not a slice, or u_init outside 0..255). */
+int fpcode_prepared_set_bound(fpcode_prepared *slice, int u_init);
 /* The codeword (n bytes, caller-owned) a packed key of `prep`'s schedule
  * stands for, rebuilt exactly from its Gamma_j rows, and its weight.
  * Errors: FPCODE_EINVAL (the key names no codeword). */
@@ -284,13 +293,13 @@ int fpcode_min_distance_batch(int num, const fpcode_desc *codes, void *stream, c
                               fpcode_result *results, uint8_t *witnesses);
 
 /* Launch settings of fpcode_min_distance_batch chosen by measurement on
- * this GPU (the batching of north_star's "words-per-row, warps-per-code and
- * chunk size chosen by an autotuner"; the paper tunes its word width and
- * isometry per configuration by hand, Sec. 4.1, Table 3).  The settings
- * searched: CTAs per SM (0: the occupancy limit, 3, 2: fewer, longer-lived
- * warps per code), min_steps (8, 16, 32, 64, 128 prefixes per lane in the
- * small passes: the chunk size) and batch_words (2: narrow and wide
- * launches by words per slice; 4: one wide launch).  A coordinate search
+ * this GPU (the paper tunes its word width and isometry per configuration
+ * by hand, Sec. 4.1, Table 3).  The settings searched: CTAs per SM (0: the
+ * occupancy limit, 3, 2: fewer, longer-lived warps per code), min_steps
+ * (8, 16, 32, 64, 128 prefixes per lane in the small passes: the chunk
+ * size) and batch_words (2: narrow and wide batched launches by words per
+ * slice; 4: one wide batched launch; 1: one launch per kernel variant,
+ * with pair leaves for the codes that take them).  A coordinate search
  * starts at the defaults, measures every value of one setting with the
  * others held (each point once, `reps` timed batches after a warm-up, end
  * to end from the host matrices), moves to the best, and stops when a round
@@ -302,7 +311,7 @@ int fpcode_min_distance_batch(int num, const fpcode_desc *codes, void *stream, c
 typedef struct fpcode_tuning {
   int ctas_per_sm;        /* chosen CTAs per SM (0: the occupancy limit) */
   int min_steps;          /* chosen prefixes per lane of small passes */
-  int batch_words;        /* chosen grouping: 2 or 4 */
+  int batch_words;        /* chosen grouping: 2, 4 or 1 */
   int evaluated;          /* settings measured by this call (0: from the cache) */
   double ms;              /* one batch with the chosen settings */
   double ms_default;      /* one batch with the default settings */

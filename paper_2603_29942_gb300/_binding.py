@@ -196,6 +196,7 @@ def _declare(lib):
         "fpcode_test_pair_table_device": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int]),
         "fpcode_prepared_pass_slice": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
                                                       ctypes.POINTER(_VP)]),
+        "fpcode_prepared_set_bound": (ctypes.c_int, [_VP, ctypes.c_int]),
         "fpcode_prepared_codeword": (ctypes.c_int, [_VP, ctypes.c_uint64, _U8P, _IP]),
         "fpcode_autotune_batch": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(fpcode_desc), _VP,
                                                  ctypes.POINTER(fpcode_opts), ctypes.c_int,
@@ -617,6 +618,11 @@ def fpcode_prepared_pass_slice(prep: Prepared, pass_index: int, task_lo: int, ta
     _check(lib().fpcode_prepared_pass_slice(prep.handle, int(pass_index), int(task_lo), int(task_hi), int(u_init),
                                             ctypes.byref(h)), "fpcode_prepared_pass_slice")
     return Prepared(h.value, prep.p, prep.n, prep.k)
+
+
+def fpcode_prepared_set_bound(slice_prep: Prepared, u_init: int) -> None:
+    """The first bound (0: none) of the next searches of a pass slice."""
+    _check(lib().fpcode_prepared_set_bound(slice_prep.handle, int(u_init)), "fpcode_prepared_set_bound")
 
 
 def fpcode_prepared_codeword(prep: Prepared, key: int):

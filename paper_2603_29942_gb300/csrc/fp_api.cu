@@ -500,6 +500,15 @@ int fpcode_prepared_pass_slice(const fpcode_prepared *src, int pass, uint64_t ta
   return FPCODE_OK;
 }
 
+int fpcode_prepared_set_bound(fpcode_prepared *slice, int u_init) {
+  if (!slice || slice->slice_hi == 0 || u_init < 0 || u_init > fpk::kMaxN) {
+    fph::set_error("fpcode_prepared_set_bound: need a pass slice and a bound in 0..255");
+    return FPCODE_EINVAL;
+  }
+  slice->init_u = u_init;
+  return FPCODE_OK;
+}
+
 void fpcode_prepared_free(fpcode_prepared *prep) {
   if (!prep) return;
   if (!prep->external) {
@@ -660,6 +669,10 @@ int fpcode_min_distance_batch(int num, const fpcode_desc *codes, void *stream, c
   if (opts) o = *opts;
   std::vector<std::unique_ptr<fph::Prepared>> preps(num);
   std::vector<int> status(num, FPCODE_OK);
+  // batch_words 1: one launch per kernel variant (prime class and words per
+  // slice), each of the single-code kernels, which also run pair-leaf
+  // codes; else the batched kernels over p in {3, 5, 7}
+  const bool per_variant = o.batch_words == 1;
   {
     // host preparation of the codes, spread over the host's cores
     const int nth = std::max(1, std::min<int>((int)std::thread::hardware_concurrency(), (num + 7) / 8));
@@ -670,7 +683,7 @@ int fpcode_min_distance_batch(int num, const fpcode_desc *codes, void *stream, c
         if (i >= num) break;
         preps[i].reset(new fph::Prepared());
         fpcode_opts oi = o;
-        oi.pair_leaves = 0;  // the batched kernels take one-row leaves
+        if (!per_variant) oi.pair_leaves = 0;  // the batched kernels take one-row leaves
         if (codes[i].budget) oi.budget = codes[i].budget;
         status[i] = fph::prepare(codes[i].p, codes[i].n, codes[i].k, codes[i].G, oi, preps[i].get());
       }
@@ -693,7 +706,7 @@ int fpcode_min_distance_batch(int num, const fpcode_desc *codes, void *stream, c
     const int narrow_w = o.batch_words == 4 ? 0 : 2;
     for (int i = 0; i < num; ++i) {
       if (status[i] != FPCODE_OK) continue;
-      if (preps[i]->variant < 12) (preps[i]->W <= narrow_w ? narrow : wide).push_back(i);
+      if (preps[i]->variant < 12 && !per_variant) (preps[i]->W <= narrow_w ? narrow : wide).push_back(i);
       else other[preps[i]->variant].push_back(i);
     }
     if (!narrow.empty()) groups.push_back(narrow);
@@ -717,7 +730,7 @@ int fpcode_min_distance_batch(int num, const fpcode_desc *codes, void *stream, c
         idx.push_back(i);
       }
     if (codesv.empty()) continue;
-    const bool multi = codesv[0]->variant < 12;
+    const bool multi = codesv[0]->variant < 12 && !per_variant;
     int wmax = 1;
     for (auto *P : codesv) wmax = std::max(wmax, P->W);
     const void *fn = multi ? fpk::kernel_multi357(wmax) : kernel_for(codesv[0]->variant);

@@ -55,27 +55,43 @@ std::vector<int> inverses(int p) {
 
 // Column-selection elimination on a k x n working matrix of bytes.
 // `owner[r]` is the pivot column of row r in the current round (-1: free).
-// Each pivot scales its row to a leading 1 and subtracts the needed
-// multiple from every other row: the p-1 multiples of the pivot row are
-// formed once, and a row update is an add and a conditional subtract of p
-// per byte (vectorisable), instead of a division.
+// Each pivot makes its row's entry 1 and clears the column in every other
+// row.  The multiples v * row of the pivot row as found (v = 1 .. p-1) are
+// formed once by repeated addition; the pivot row scaled to a leading 1 is
+// the multiple inv(a) * row (a its entry), and subtracting f times it from
+// another row adds the multiple (p - f) inv(a) * row.  Every row operation
+// is an add and a conditional subtract of p per byte (vectorisable), with
+// no table lookup and no division.
 struct Eliminator {
   int p, n, k;
   std::vector<uint8_t> M;    // row-major, values in [0, p)
   std::vector<int> inv;
-  std::vector<uint8_t> mul;   // p x p multiplication table
   std::vector<int> owner;
-  std::vector<uint8_t> mrow;  // (p-1) x n multiples of the current pivot row
-  std::vector<char> have;     // which of them are formed
+  std::vector<uint8_t> mrow;  // (p-1) x n: v * row for v = 1 .. p-1 of the current pivot row
 
   Eliminator(int p_, int n_, int k_, const uint8_t *G)
-      : p(p_), n(n_), k(k_), M(G, G + (size_t)k_ * n_), mrow((size_t)(p_ - 1) * n_), have(p_ - 1, 0) {
+      : p(p_), n(n_), k(k_), M(G, G + (size_t)k_ * n_), mrow((size_t)(p_ - 1) * n_) {
     inv = inverses(p);
-    mul.resize((size_t)p * p);
-    for (int a = 0; a < p; ++a)
-      for (int b = 0; b < p; ++b) mul[(size_t)a * p + b] = (uint8_t)(a * b % p);
   }
   void new_round() { owner.assign(k, -1); }
+  // o = (o + y) mod p on n bytes, o, y in [0, p), separate arrays
+  static void add_mod(uint8_t *__restrict__ o, const uint8_t *__restrict__ y, int n, int p) {
+    if (p < 128) {
+      // byte lanes: t = o + y < 2p <= 255; t - p wraps above t exactly when
+      // t < p, so the smaller of the two is t mod p (vectorises)
+      const uint8_t p8 = (uint8_t)p;
+      for (int i = 0; i < n; ++i) {
+        const uint8_t t = (uint8_t)(o[i] + y[i]);
+        const uint8_t u = (uint8_t)(t - p8);
+        o[i] = t < u ? t : u;
+      }
+    } else {
+      for (int i = 0; i < n; ++i) {
+        const uint16_t t = (uint16_t)(o[i] + y[i]);
+        o[i] = (uint8_t)(t >= (uint16_t)p ? t - (uint16_t)p : t);
+      }
+    }
+  }
   // Take column c as a pivot if a free row has a nonzero entry there.
   bool take(int c) {
     // locals: the byte stores below may alias any member as far as the
@@ -90,42 +106,24 @@ struct Eliminator {
       }
     if (r < 0) return false;
     uint8_t *row = &M[(size_t)r * n];
-    if (row[c] != 1) {  // scale the pivot row to a leading 1
-      const uint8_t *ms = &mul[(size_t)inv[row[c]] * p];
-      for (int i = 0; i < n; ++i) row[i] = ms[row[i]];
+    const int a = row[c];
+    uint8_t *mv = mrow.data();
+    std::memcpy(mv, row, (size_t)n);  // 1 * row
+    for (int v = 2; v < p; ++v) {    // v * row = (v - 1) * row + row
+      std::memcpy(mv + (size_t)(v - 1) * n, mv + (size_t)(v - 2) * n, (size_t)n);
+      add_mod(mv + (size_t)(v - 1) * n, row, n, p);
     }
-    // multiples (p - f) * row, formed once per pivot, for the f that occur
-    const uint16_t pp = (uint16_t)p;
-    const uint8_t p8 = (uint8_t)p;
+    const int ia = inv[a];
+    // the pivot row scaled to a leading 1: inv(a) * row
+    if (ia != 1) std::memcpy(row, mv + (size_t)(ia - 1) * n, (size_t)n);
     for (int q = 0; q < k; ++q) {
       if (q == r) continue;
       uint8_t *o = &M[(size_t)q * n];
       const int f = o[c];
       if (!f) continue;
-      uint8_t *mv = &mrow[(size_t)(f - 1) * n];
-      if (!have[f - 1]) {
-        const uint8_t *mf = &mul[(size_t)(p - f) * p];  // adding (p - f) * row subtracts f * row
-        for (int i = 0; i < n; ++i) mv[i] = mf[row[i]];
-        have[f - 1] = 1;
-      }
-      if (p < 128) {
-        // byte lanes: s = o + mv < 2p <= 255; s - p wraps above s exactly
-        // when s < p, so the smaller of the two is s mod p (vectorises)
-        uint8_t *__restrict__ od = o;
-        const uint8_t *__restrict__ md = mv;
-        for (int i = 0; i < n; ++i) {
-          const uint8_t x = (uint8_t)(od[i] + md[i]);
-          const uint8_t y = (uint8_t)(x - p8);
-          od[i] = x < y ? x : y;
-        }
-      } else {
-        for (int i = 0; i < n; ++i) {
-          const uint16_t x = (uint16_t)(o[i] + mv[i]);
-          o[i] = (uint8_t)(x >= pp ? x - pp : x);
-        }
-      }
+      const int v = (p - f) * ia % p;  // o - f * (inv(a) * row) = o + ((p - f) inv(a)) * row
+      add_mod(o, mv + (size_t)(v - 1) * n, n, p);
     }
-    std::fill(have.begin(), have.end(), (char)0);
     owner[r] = c;
     return true;
   }

@@ -59,7 +59,7 @@ namespace {
 
 const int kCtas[] = {0, 3, 2};
 const int kSteps[] = {8, 16, 32, 64, 128};
-const int kWords[] = {2, 4};
+const int kWords[] = {2, 4, 1};
 
 std::mutex g_tune_mu;
 std::map<std::string, fpcode_tuning> g_tune_cache;
@@ -143,7 +143,7 @@ int fpcode_autotune_batch(int num, const fpcode_desc *codes, void *stream, const
     y.batch_words = fph::kWords[x[2]];
     return y;
   };
-  const std::vector<int> sizes = {3, 5, 2};
+  const std::vector<int> sizes = {3, 5, 3};
   const std::vector<int> start = {0, 2, 0};  // the defaults: occupancy limit, 32 prefixes per lane, two launches
   int evals = 0;
   const std::vector<int> best =

@@ -105,16 +105,26 @@ def split_search(schedule: list[dict], *, n: int, k: int, per_round_check: bool,
 
 class GpuSlices:
     """search_slice on this process's GPU: tasks [lo, hi) of one pass of an
-    uploaded code, searched alone (fpcode_prepared_pass_slice)."""
+    uploaded code, searched alone (fpcode_prepared_pass_slice).  Each slice
+    is prepared and uploaded once and kept: later searches of the split only
+    set its first bound (fpcode_prepared_set_bound) and launch it."""
 
     def __init__(self, B, prep, stream=None):
         self.B = B
         self.prep = prep
         self.stream = stream
+        self.slices = {}
 
     def __call__(self, pass_index: int, lo: int, hi: int, u: int):
-        s = self.B.fpcode_prepared_pass_slice(self.prep, pass_index, lo, hi, u)
-        r = self.B.fpcode_min_distance_ex(s, self.stream)
+        s = self.slices.get((pass_index, lo, hi))
+        if s is None:
+            s = self.B.fpcode_prepared_pass_slice(self.prep, pass_index, lo, hi, u)
+            self.B.fpcode_prepared_upload(s, self.stream)
+            self.slices[(pass_index, lo, hi)] = s
+        else:
+            self.B.fpcode_prepared_set_bound(s, u)
+        self.B.fpcode_search_enqueue(s, self.stream)
+        r = self.B.fpcode_search_finish(s, self.stream, want_witness=False)
         return with_pass(r.best_key, pass_index), r.enumerated
 
 

@@ -224,14 +224,18 @@ def test_batch_against_oracle_mixed_primes():
             check_witness(c, rb.d, rb.witness)
 
 
-def test_batch512_sample_against_oracle():
+@pytest.mark.parametrize("words", [2, 1])
+def test_batch512_sample_against_oracle(words):
     """The batched workload at its bench size (512 codes, budget 10^8
-    codewords per code, one launch): a fixed sample spread over the batch
-    matches the oracle run alone at the same budget (status, d, per-level
-    counts, L, U) with a valid witness."""
+    codewords per code): a fixed sample spread over the batch matches the
+    oracle run alone at the same budget (status, d, per-level counts, L, U)
+    with a valid witness, in one batched launch (batch_words 2) and in one
+    launch per kernel variant with pair leaves for the codes that take
+    them (batch_words 1)."""
     codes = inputs.batch_codes(512)
     budget = 10 ** 8
-    res = B.fpcode_min_distance_batch(codes, budgets=[budget] * len(codes))
+    res = B.fpcode_min_distance_batch(codes, opts=B.fpcode_opts_default(batch_words=words),
+                                      budgets=[budget] * len(codes))
     for i in range(0, 512, 51):
         c, rb = codes[i], res[i]
         r = oracle.bz(c, budget=budget, threads=os.cpu_count() or 4)
@@ -241,12 +245,16 @@ def test_batch512_sample_against_oracle():
             check_witness(c, rb.d, rb.witness)
 
 
-def test_batch_mixed_widths_against_oracle():
+@pytest.mark.parametrize("words", [2, 4, 1])
+def test_batch_mixed_widths_against_oracle(words):
     """Codes of one, two and three words per slice in one batch run in the
-    narrow and the wide batched kernels; each matches the oracle."""
-    shapes = [(3, 70, 5), (3, 40, 6), (3, 30, 6), (7, 75, 4), (5, 100, 4), (7, 50, 8), (5, 36, 7), (3, 98, 6)]
+    narrow and the wide batched kernels, or one launch per variant with pair
+    leaves forced on for p = 3, 7 (batch_words 1); each matches the oracle."""
+    shapes = [(3, 70, 5), (3, 40, 6), (3, 30, 6), (7, 75, 4), (5, 100, 4), (7, 50, 8), (5, 36, 7), (3, 98, 6),
+              (3, 60, 20), (7, 44, 14), (3, 48, 16)]
     codes = [inputs.single_code(700 + i, p, n, k) for i, (p, n, k) in enumerate(shapes)]
-    res = B.fpcode_min_distance_batch(codes, budgets=[10 ** 7] * len(codes))
+    o = B.fpcode_opts_default(batch_words=words, pair_leaves=1 if words == 1 else 2)
+    res = B.fpcode_min_distance_batch(codes, opts=o, budgets=[10 ** 7] * len(codes))
     for c, rb in zip(codes, res):
         r = oracle.bz(c, budget=10 ** 7, threads=4)
         assert (rb.status, rb.counts, rb.L, rb.U) == (status_of_oracle(r.status), r.counts, r.L, r.U)
@@ -310,14 +318,14 @@ def test_batch_autotune_keeps_results_and_caches():
     codes = inputs.batch_codes(64, seed=7)
     budgets = [10 ** 6] * len(codes)
     t = B.fpcode_autotune_batch(codes, budgets=budgets, reps=1)
-    assert t["ctas_per_sm"] in (0, 2, 3) and t["min_steps"] in (8, 16, 32, 64, 128) and t["batch_words"] in (2, 4)
+    assert t["ctas_per_sm"] in (0, 2, 3) and t["min_steps"] in (8, 16, 32, 64, 128) and t["batch_words"] in (2, 4, 1)
     assert t["evaluated"] >= 1 and t["ms"] > 0 and t["ms_default"] > 0 and "k" in t["workload_class"]
     again = B.fpcode_autotune_batch(codes, budgets=budgets, reps=1)
     assert again["evaluated"] == 0
     assert (again["ctas_per_sm"], again["min_steps"], again["batch_words"]) == (
         t["ctas_per_sm"], t["min_steps"], t["batch_words"])
     ref = B.fpcode_min_distance_batch(codes, budgets=budgets, want_witness=False)
-    for wide in (2, 4):  # also the other grouping, whichever was chosen
+    for wide in (2, 4, 1):  # also the other groupings, whichever was chosen
         o = t["opts"]
         o.batch_words = wide
         got = B.fpcode_min_distance_batch(codes, opts=o, budgets=budgets, want_witness=False)
