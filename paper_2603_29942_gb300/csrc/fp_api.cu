@@ -717,63 +717,100 @@ int fpcode_min_distance_batch(int num, const fpcode_desc *codes, void *stream, c
   std::vector<size_t> woff(num + 1, 0);
   for (int i = 0; i < num; ++i) woff[i + 1] = woff[i] + (size_t)codes[i].n;
   std::lock_guard<std::mutex> lk(c->ws_mu);
-  cudaEvent_t e0, e1;
-  FP_CUDA(cudaEventCreate(&e0));
-  FP_CUDA(cudaEventCreate(&e1));
-  int nlaunch = -1;
-  for (auto &grp : groups) {
+  // Every group is planned and laid out first, at its own offset in the
+  // workspace and in the pinned staging; then all uploads, launches and
+  // read-backs go onto the stream back to back, with one synchronisation at
+  // the end, so the GPU does not wait for the host between groups.
+  struct Launch {
     std::vector<const fph::Prepared *> codesv;
     std::vector<int> idx;
+    const void *fn = nullptr;
+    int smem = 0, ctas = 0;
+    Layout L;
+    size_t dev_off = 0, pin_off = 0, rb_off = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+  };
+  std::vector<Launch> ls;
+  size_t dev_total = 0, pin_total = 0;
+  for (auto &grp : groups) {
+    Launch g;
     for (int i : grp)
       if (!preps[i]->passes.empty()) {
-        codesv.push_back(preps[i].get());
-        idx.push_back(i);
+        g.codesv.push_back(preps[i].get());
+        g.idx.push_back(i);
       }
-    if (codesv.empty()) continue;
-    const bool multi = codesv[0]->variant < 12 && !per_variant;
+    if (g.codesv.empty()) continue;
+    const bool multi = g.codesv[0]->variant < 12 && !per_variant;
     int wmax = 1;
-    for (auto *P : codesv) wmax = std::max(wmax, P->W);
-    const void *fn = multi ? fpk::kernel_multi357(wmax) : kernel_for(codesv[0]->variant);
-    const int smem = smem_for(codesv);
+    for (auto *P : g.codesv) wmax = std::max(wmax, P->W);
+    g.fn = multi ? fpk::kernel_multi357(wmax) : kernel_for(g.codesv[0]->variant);
+    g.smem = smem_for(g.codesv);
     int per_sm = 0;
-    s = occupancy(fn, smem, o.ctas_per_sm, &per_sm);
-    if (s) break;
-    const int ctas = c->sms * per_sm;
-    const bool many = idx.size() > 1;
-    for (int i : idx)
-      fph::plan_tasks(preps[i].get(), ctas, o.prefixes_per_lane,
+    s = occupancy(g.fn, g.smem, o.ctas_per_sm, &per_sm);
+    if (s) return s;
+    g.ctas = c->sms * per_sm;
+    const bool many = g.idx.size() > 1;
+    for (int i : g.idx)
+      fph::plan_tasks(preps[i].get(), g.ctas, o.prefixes_per_lane,
                       o.min_steps > 0 ? o.min_steps : many ? fph::kMinStepsBatch : fph::kMinStepsSingle, !many);
-    Layout L = make_layout(codesv);
-    s = ws_reserve(*c, L.total, std::max(L.static_bytes, L.dyn_bytes));
-    if (s) break;
-    fill_static(L, codesv, *c, c->ws_pinned, c->ws, 0);
-    FP_CUDA(cudaMemcpyAsync(c->ws, c->ws_pinned, L.static_bytes, cudaMemcpyHostToDevice, st));
-    FP_CUDA(cudaMemsetAsync(c->ws + L.off_states, 0, L.dyn_bytes + L.aux_bytes, st));
-    FP_CUDA(cudaEventRecord(e0, st));
-    s = launch(fn, ctas, smem, st, c->ws, L, kparams(o, 0));
-    if (s) break;
-    ++nlaunch;
-    FP_CUDA(cudaEventRecord(e1, st));
-    FP_CUDA(cudaStreamSynchronize(st));  // the staging buffer is reused for the read-back
-    FP_CUDA(cudaMemcpyAsync(c->ws_pinned, c->ws + L.off_states, L.dyn_bytes, cudaMemcpyDeviceToHost, st));
-    FP_CUDA(cudaStreamSynchronize(st));
-    float ms = 0;
-    cudaEventElapsedTime(&ms, e0, e1);
-    const SlotState *states = reinterpret_cast<const SlotState *>(c->ws_pinned);
-    CtlDyn dyn;
-    std::memcpy(&dyn, c->ws_pinned + L.dyn_bytes - sizeof(CtlDyn), sizeof(dyn));
-    for (size_t q = 0; q < idx.size(); ++q) {
-      const int i = idx[q];
-      uint8_t *w = witnesses ? witnesses + woff[i] : nullptr;
-      fph::decode_result(*preps[i], outcome_of(states[q], dyn), &results[i], w);
-      results[i].t_kernel_ms = ms;
-      results[i].launch = nlaunch;
-      results[i].t_prepare_ms = t_prep;
+    g.L = make_layout(g.codesv);
+    g.dev_off = dev_total;
+    dev_total += align256(g.L.total);
+    g.pin_off = pin_total;
+    g.rb_off = pin_total + align256(g.L.static_bytes);
+    pin_total = g.rb_off + align256(g.L.dyn_bytes);
+    ls.push_back(std::move(g));
+  }
+  s = ws_reserve(*c, std::max<size_t>(dev_total, 256), std::max<size_t>(pin_total, 256));
+  if (s) return s;
+  int err = FPCODE_OK;
+  for (auto &g : ls) {
+    char *d = c->ws + g.dev_off;
+    fill_static(g.L, g.codesv, *c, c->ws_pinned + g.pin_off, d, 0);
+    if (cudaEventCreate(&g.e0) != cudaSuccess || cudaEventCreate(&g.e1) != cudaSuccess) {
+      err = FPCODE_ECUDA;
+      break;
+    }
+    if (cudaMemcpyAsync(d, c->ws_pinned + g.pin_off, g.L.static_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(d + g.L.off_states, 0, g.L.dyn_bytes + g.L.aux_bytes, st) != cudaSuccess ||
+        cudaEventRecord(g.e0, st) != cudaSuccess) {
+      err = FPCODE_ECUDA;
+      break;
+    }
+    if ((err = launch(g.fn, g.ctas, g.smem, st, d, g.L, kparams(o, 0))) != FPCODE_OK) break;
+    if (cudaEventRecord(g.e1, st) != cudaSuccess ||
+        cudaMemcpyAsync(c->ws_pinned + g.rb_off, d + g.L.off_states, g.L.dyn_bytes, cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess) {
+      err = FPCODE_ECUDA;
+      break;
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  if (s) return s;
+  if (!err && cudaStreamSynchronize(st) != cudaSuccess) err = FPCODE_ECUDA;
+  int nlaunch = -1;
+  for (auto &g : ls) {
+    if (!err && g.e1) {
+      ++nlaunch;
+      float ms = 0;
+      cudaEventElapsedTime(&ms, g.e0, g.e1);
+      const SlotState *states = reinterpret_cast<const SlotState *>(c->ws_pinned + g.rb_off);
+      CtlDyn dyn;
+      std::memcpy(&dyn, c->ws_pinned + g.rb_off + g.L.dyn_bytes - sizeof(CtlDyn), sizeof(dyn));
+      for (size_t q = 0; q < g.idx.size(); ++q) {
+        const int i = g.idx[q];
+        uint8_t *w = witnesses ? witnesses + woff[i] : nullptr;
+        fph::decode_result(*preps[i], outcome_of(states[q], dyn), &results[i], w);
+        results[i].t_kernel_ms = ms;
+        results[i].launch = nlaunch;
+        results[i].t_prepare_ms = t_prep;
+      }
+    }
+    if (g.e0) cudaEventDestroy(g.e0);
+    if (g.e1) cudaEventDestroy(g.e1);
+  }
+  if (err) {
+    fph::set_error("fpcode_min_distance_batch: a CUDA call failed");
+    return err;
+  }
   for (int i = 0; i < num; ++i) {
     if (status[i] != FPCODE_OK) {
       std::memset(&results[i], 0, sizeof(results[i]));
