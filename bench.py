@@ -500,7 +500,7 @@ def serve_measure(args, torch, B, n_req=None) -> dict:
             results[i] = r
         if not pending and not ticket_of:
             break
-        time.sleep(0.0002)
+        time.sleep(0.00005)  # the client's poll interval (50 us)
     elapsed = time.perf_counter() - t0
     launches = B.fpcode_serve_launches(srv) - relaunch0
     B.fpcode_serve_destroy(srv)

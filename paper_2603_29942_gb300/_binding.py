@@ -660,6 +660,14 @@ class Server:
     def __init__(self, handle: int):
         self.handle = handle
         self.ks: dict[int, int] = {}
+        self.bufs: dict[int, tuple] = {}  # poll buffers by capacity, made once
+
+    def poll_buffers(self, cap: int):
+        b = self.bufs.get(cap)
+        if b is None:
+            b = ((fpcode_result * cap)(), (ctypes.c_uint64 * cap)())
+            self.bufs[cap] = b
+        return b
 
     def __del__(self):
         if getattr(self, "handle", None) and _lib is not None:
@@ -689,8 +697,7 @@ def fpcode_serve_submit(server: Server, code, budget: int = 0) -> int | None:
 
 def fpcode_serve_poll(server: Server, max_results: int = 256, want_witness: bool = True):
     """List of (ticket, Result) for codes that finished since the last poll."""
-    res = (fpcode_result * max_results)()
-    tickets = (ctypes.c_uint64 * max_results)()
+    res, tickets = server.poll_buffers(max_results)
     wit = np.zeros(max_results * MAX_N, dtype=np.uint8) if want_witness else None
     n = ctypes.c_int(0)
     _check(lib().fpcode_serve_poll(server.handle, res, tickets, wit.ctypes.data_as(_U8P) if want_witness else None,

@@ -450,3 +450,22 @@ def test_device_pair_table_matches_definition(p, n, k):
             host = B.fpcode_test_pair_entry(pr, j, e)
             assert list(dev[e * sigp:(e + 1) * sigp]) == host[:sigp], (j, e)
             assert list(dev[off0 + e * W:off0 + (e + 1) * W]) == host[sigp:], (j, e)
+
+
+def test_int_peaks_are_measured():
+    """The roofline's denominator comes from fpcode_int_peaks: positive issue
+    rates, POPC no faster than LOP3, no unit above one warp instruction per
+    SM sub-partition per clock (4 x 32 lanes), and the per-second rates equal
+    to lanes per clock x SMs x the measured clock."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    r = B.fpcode_int_peaks()
+    for key in ("lop3_per_clk_sm", "popc_per_clk_sm", "iadd_per_clk_sm", "sm_mhz"):
+        assert r[key] > 0, key
+    assert r["popc_per_clk_sm"] <= r["lop3_per_clk_sm"] * 1.05
+    for key in ("lop3_per_clk_sm", "popc_per_clk_sm", "iadd_per_clk_sm"):
+        assert r[key] <= 128 * 1.05, key
+    for per_clk, per_s in (("lop3_per_clk_sm", "lop3_per_s"), ("popc_per_clk_sm", "popc_per_s")):
+        want = r[per_clk] * sms * r["sm_mhz"] * 1e6
+        assert abs(r[per_s] - want) <= 0.10 * want, (per_s, r[per_s], want)
