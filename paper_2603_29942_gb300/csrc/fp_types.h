@@ -11,7 +11,10 @@
 
 namespace fpk {
 
-constexpr int kThreads = 256;        // threads per CTA (8 warps)
+#ifndef FPK_THREADS
+#define FPK_THREADS 256
+#endif
+constexpr int kThreads = FPK_THREADS;  // threads per CTA (256: 8 warps)
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxK = 64;            // rows: subsets are 64-bit masks
 constexpr int kMaxW = 4;             // 32-bit words per slice: n - k <= 128
