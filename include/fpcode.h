@@ -106,7 +106,8 @@ typedef struct fpcode_opts {
                           pair entries (0: 192) */
   int task_share;      /* pair leaves: a task takes 1 / (task_share * C) of
                           its pass's remaining work, C the CTAs of the
-                          grid, until task_work (0: 2) */
+                          grid, until task_work (0: 1 for a pass with more
+                          passes after it in the launch, 2 for the last) */
   int batch_words;     /* batches: words per slice up to which a code with
                           p in {3, 5, 7} goes to the narrow batched kernel
                           (0 or 2: n - k <= 64, the others in a second,

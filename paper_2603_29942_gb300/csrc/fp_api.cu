@@ -496,6 +496,9 @@ int fpcode_prepared_pass_slice(const fpcode_prepared *src, int pass, uint64_t ta
   if (s) return s;
   prep->slice_lo = task_lo;
   prep->slice_hi = task_hi;
+  // the slice's tasks are those of the pass in the source's plan: the share
+  // of a pass depends on whether passes follow it in the source schedule
+  prep->host.opts.task_share = fph::task_share_of(src->host.opts, pass + 1 == (int)src->host.passes.size());
   *out = prep;
   return FPCODE_OK;
 }

@@ -497,10 +497,25 @@ namespace {
 // own, so the groups of a task have equal work.
 constexpr uint64_t kStemCost = 8;      // a stem step, in entry evaluations
 constexpr uint64_t kMinTaskLane = 192;  // least per-lane work of a task, in entry evaluations (task_work 0)
-constexpr uint64_t kTaskShare = 2;      // guided share: 1 / (kTaskShare C) of the remaining work (task_share 0)
+// Guided share (task_share 0): a task takes 1 / (share C) of its pass's
+// remaining work.  A pass with more passes after it in the launch takes
+// share 1: CTAs that run out of its tasks move on to the next pass (run
+// ahead), so its larger tasks cost no idle lanes at its end, and there are
+// fewer claims.  The launch's last pass (a pass run alone: a probe, a
+// slice of a split search) takes share 2, so that its tail is short.
+constexpr uint64_t kTaskShareMid = 1;
+constexpr uint64_t kTaskShareLast = 2;
+
+}  // namespace
+
+int task_share_of(const fpcode_opts &o, bool last) {
+  return o.task_share > 0 ? o.task_share : (int)(last ? kTaskShareLast : kTaskShareMid);
+}
+
+namespace {
 constexpr uint64_t kSpreadLane = 4;    // a pass of at most this much work per lane of the grid is spread wide
 
-void plan_pair_pass(Prepared *P, fpk::PassDesc &d, uint64_t C) {
+void plan_pair_pass(Prepared *P, fpk::PassDesc &d, uint64_t C, bool last) {
   const int k = P->k, b = P->p - 1, g = d.g;
   const int H = g == 2 ? 1 : b / 2;
   const uint64_t lanes = (uint64_t)fpk::kThreads;
@@ -526,7 +541,7 @@ void plan_pair_pass(Prepared *P, fpk::PassDesc &d, uint64_t C) {
   // lanes as keeps two loads per lane.
   const bool spread = rem <= C * lanes * kSpreadLane;
   const uint64_t Tmin = P->opts.task_work > 0 ? (uint64_t)P->opts.task_work : kMinTaskLane;
-  const uint64_t share = P->opts.task_share > 0 ? (uint64_t)P->opts.task_share : kTaskShare;
+  const uint64_t share = (uint64_t)task_share_of(P->opts, last);
   const uint64_t T_spread = std::max<uint64_t>(2, rem / (C * lanes) + 1);
   // Stems of one group start on the same phase of the coefficient counter
   // (units of (p-1)^t stems, t <= g - 3), so the lanes of a warp take the
@@ -602,7 +617,7 @@ void plan_tasks(Prepared *P, int ctas, int fixed_pl, int min_steps, bool spread_
       continue;
     }
     if (P->pair) {
-      plan_pair_pass(P, d, C);
+      plan_pair_pass(P, d, C, &d == &P->passes.back());
       continue;
     }
     if (fixed_pl > 0) {

@@ -70,6 +70,10 @@ struct Prepared {
   size_t smem_bytes_per_set() const { return (table_words_per_set() + pair_words_per_set()) * 4; }
 };
 
+// Guided share of a pair-leaf pass (task_share, or its default for a pass
+// that is (last) or is not the last of its launch).
+int task_share_of(const fpcode_opts &o, bool last);
+
 // Elimination, information sets, multiples, schedule.  Returns an fpcode
 // status; the error text is set on failure.
 int prepare(int p, int n, int k, const uint8_t *G, const fpcode_opts &opts, Prepared *out);

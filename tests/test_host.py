@@ -635,6 +635,21 @@ def test_pair_tasks_tile_each_pass(name, ctas, lib):
         assert pos == nstems
 
 
+@pytest.mark.parametrize("name", ["f3_n80_k40", "f7_n40_k20"])
+def test_pass_slices_keep_the_schedule_plan(name, lib):
+    """A slice of a pass (one rank's part of a split search) is planned as
+    the pass is in the full schedule: the same tasks over the same stems,
+    whether the pass has passes after it (larger tasks) or is the last."""
+    pr = _prep(inputs.single(name), pair_leaves=1)
+    passes = B.fpcode_prepared_passes(pr)
+    for i in (2, 5, len(passes) - 1):
+        if passes[i][0] < 2:
+            continue
+        full = B.fpcode_test_task_ranges(pr, i, 608, 0, 8)
+        sl = B.fpcode_prepared_pass_slice(pr, i, 0, len(full), 0)
+        assert B.fpcode_test_task_ranges(sl, 0, 608, 0, 8) == full, i
+
+
 # ------------------------------------------------------------- autotuner ----
 
 def test_tune_search_finds_the_minimum_of_separable_costs(lib):
