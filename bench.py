@@ -77,9 +77,13 @@ FLUSH_BYTES = 256 << 20
 # version that was profiled; any later change of their code reports null
 # (the hash skips comments and blank lines).
 KERNEL_SOURCES = ["fp_kernel.cuh", "fp_enum.cuh", "fp_bitslice.cuh", "fp_types.h"]
-_SHA_PROFILED = "40d4004593325c9abe410be6bfee9680be8cedb7d57a92fa3662fd6c66c18a9a"
+_SHA_PROFILED = "a2c48fb23779b61af5a4c29fff75515d557943e9f91e3d3792438435a479807a"
 PROFILED_TRAFFIC: dict = {  # profiles/bz_kernel_*.md (the command of each capture is there)
-    "f3_n80_k40": {"bytes": 4787712 + 512, "sources_sha256": _SHA_PROFILED},
+    "f3_n80_k40": {"bytes": 4789248 + 512, "sources_sha256": _SHA_PROFILED},
+    "probe_f3_n80_k40_g8": {"bytes": 4791296 + 57344, "sources_sha256": _SHA_PROFILED},
+    "f7_n40_k20": {"bytes": 9473792 + 0, "sources_sha256": _SHA_PROFILED},
+    "probe_f7_n40_k20_g7": {"bytes": 7574272 + 0, "sources_sha256": _SHA_PROFILED},
+},
     "probe_f3_n80_k40_g8": {"bytes": 4777984 + 53760, "sources_sha256": _SHA_PROFILED},
     "f7_n40_k20": {"bytes": 9477888 + 0, "sources_sha256": _SHA_PROFILED},
     "probe_f7_n40_k20_g7": {"bytes": 7575040 + 0, "sources_sha256": _SHA_PROFILED},
