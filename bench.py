@@ -83,10 +83,6 @@ PROFILED_TRAFFIC: dict = {  # profiles/bz_kernel_*.md (the command of each captu
     "probe_f3_n80_k40_g8": {"bytes": 4791296 + 57344, "sources_sha256": _SHA_PROFILED},
     "f7_n40_k20": {"bytes": 9473792 + 0, "sources_sha256": _SHA_PROFILED},
     "probe_f7_n40_k20_g7": {"bytes": 7574272 + 0, "sources_sha256": _SHA_PROFILED},
-},
-    "probe_f3_n80_k40_g8": {"bytes": 4777984 + 53760, "sources_sha256": _SHA_PROFILED},
-    "f7_n40_k20": {"bytes": 9477888 + 0, "sources_sha256": _SHA_PROFILED},
-    "probe_f7_n40_k20_g7": {"bytes": 7575040 + 0, "sources_sha256": _SHA_PROFILED},
 }
 
 
