@@ -77,6 +77,13 @@ int fpcode_test_task_ranges(fpcode_prepared *prep, int pass, int ctas, int fixed
  * pass, *entries receives the pair entries the stem is evaluated against,
  * (p-1) C(k-1-q, 2) with q the stem's largest row (g = 2: all pairs).
  * Returns the words per entry, or a negative status. */
+/* The prefixes [lo, hi) every lane of every task of one-row pass `pass`
+ * (g >= 2) walks under the plan for `ctas` CTAs, task-major, lane-minor:
+ * the task's contiguous range of units split evenly over its lanes, as the
+ * kernel splits it.  Returns tasks x threads per CTA (entries past max not
+ * written), or -1. */
+int fpcode_test_lane_ranges(fpcode_prepared *prep, int pass, int ctas, int fixed_pl, int min_steps, uint64_t *lo,
+                            uint64_t *hi, int max);
 int fpcode_test_pair_mode(const fpcode_prepared *prep, int pass, uint64_t J, uint32_t *entries);
 /* Pair-table entry e of Gamma_j (pair leaves), computed on the host from
  * the prepared multiples: its pair_sigp words (the signature words of

@@ -193,6 +193,9 @@ def _declare(lib):
         "fpcode_test_pair_mode": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint32)]),
         "fpcode_test_key_coefficients": (ctypes.c_int, [_VP, ctypes.c_uint64, _IP, _IP, _IP]),
         "fpcode_test_pair_entry": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]),
+        "fpcode_test_lane_ranges": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                   ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                                   ctypes.c_int]),
         "fpcode_test_pair_table_device": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int]),
         "fpcode_prepared_pass_slice": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
                                                       ctypes.POINTER(_VP)]),
@@ -736,6 +739,19 @@ def fpcode_test_task_ranges(prep: Prepared, pass_index: int, ctas: int, fixed_pl
     if n < 0:
         raise FpcodeError(EINVAL, "fpcode_test_task_ranges")
     return [(int(lo[i]), int(hi[i])) for i in range(min(n, cap))]
+
+
+def fpcode_test_lane_ranges(prep: Prepared, pass_index: int, ctas: int, fixed_pl: int = 0, min_steps: int = 8):
+    """[(lo, hi)] of every lane of every task of a one-row pass, task-major."""
+    cap = 1 << 22
+    lo = np.zeros(cap, dtype=np.uint64)
+    hi = np.zeros(cap, dtype=np.uint64)
+    n = lib().fpcode_test_lane_ranges(prep.handle, pass_index, ctas, fixed_pl, min_steps,
+                                      lo.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                      hi.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), cap)
+    if n < 0:
+        raise FpcodeError(EINVAL, "fpcode_test_lane_ranges")
+    return lo[:min(n, cap)], hi[:min(n, cap)]
 
 
 def fpcode_test_pair_mode(prep: Prepared, pass_index: int = -1, J: int = 0):

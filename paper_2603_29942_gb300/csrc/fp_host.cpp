@@ -934,6 +934,28 @@ int fpcode_test_task_ranges(fpcode_prepared *prep, int pass, int ctas, int fixed
   return (int)d.ntasks;
 }
 
+int fpcode_test_lane_ranges(fpcode_prepared *prep, int pass, int ctas, int fixed_pl, int min_steps, uint64_t *lo,
+                            uint64_t *hi, int max) {
+  if (!prep || pass < 0 || pass >= (int)prep->host.passes.size() || !lo || !hi || max < 0) return -1;
+  fph::plan_tasks(&prep->host, ctas, fixed_pl, min_steps, min_steps <= fph::kMinStepsSingle);
+  const fpk::PassDesc &d = prep->host.passes[pass];
+  if (d.g < 2 || d.nseg > 0) return -1;  // one-row passes with g >= 2 only
+  const uint64_t total = (uint64_t)d.ntasks * fpk::kThreads;
+  int n = 0;
+  for (uint64_t t = 0; t < d.ntasks && n < max; ++t)
+    for (int lane = 0; lane < fpk::kThreads && n < max; ++lane, ++n) {
+      // as the kernel splits a task's units over its lanes (task_prefixes)
+      uint64_t ulo = 0, uhi = 0;
+      fpk::task_range(d, t, &ulo, &uhi);
+      const uint64_t pu = (uhi - ulo + fpk::kThreads - 1) / fpk::kThreads;
+      const uint64_t a = (ulo + (uint64_t)lane * pu) * d.unit;
+      const uint64_t e = std::min(uhi * d.unit, d.nprefix);
+      lo[n] = std::min(a, e);
+      hi[n] = std::min(a + pu * d.unit, e);
+    }
+  return (int)std::min<uint64_t>(total, (uint64_t)INT32_MAX);
+}
+
 int fpcode_test_pair_mode(const fpcode_prepared *prep, int pass, uint64_t J, uint32_t *entries) {
   if (!prep) return -FPCODE_EINVAL;
   const fph::Prepared &P = prep->host;

@@ -424,6 +424,26 @@ def test_task_ranges_tile_each_pass(ctas, fixed_pl, min_steps, lib):
             assert sizes[0] + 256 >= sizes[-1]  # tasks shrink as the pass drains (up to one unit)
 
 
+@pytest.mark.parametrize("name,ctas,fixed_pl,min_steps", [("f3_n80_k40", 608, 0, 8), ("f7_n40_k20", 608, 0, 8),
+                                                          ("f7_n40_k20", 152, 0, 32), ("f3_n30_k15", 7, 0, 8),
+                                                          ("f7_n40_k20", 608, 3, 8), ("f3_n80_k40", 100, 0, 32)])
+def test_lanes_tile_each_pass(name, ctas, fixed_pl, min_steps, lib):
+    """Every prefix of a one-row pass is walked by exactly one lane of one
+    task, for guided and fixed task plans."""
+    pr = _prep(inputs.single(name), pair_leaves=0)
+    passes = B.fpcode_prepared_passes(pr)
+    for i, (g, _j, _Lb, _La, _re, _size, nprefix) in enumerate(passes[:12]):
+        if g < 2 or nprefix > 1 << 21:
+            continue
+        lo, hi = B.fpcode_test_lane_ranges(pr, i, ctas, fixed_pl, min_steps)
+        lo, hi = lo.astype(np.int64), hi.astype(np.int64)
+        keep = hi > lo
+        order = np.argsort(lo[keep], kind="stable")
+        a, b = lo[keep][order], hi[keep][order]
+        assert a[0] == 0 and b[-1] == nprefix, i
+        assert (a[1:] == b[:-1]).all(), i  # no gap, no overlap
+
+
 def test_guided_tasks_are_whole_rows_and_shrink(lib):
     """A guided pass is cut into rows of one prefix unit per lane (256
     units): every task but the pass's last holds whole rows, and task sizes
