@@ -109,6 +109,19 @@ __device__ __forceinline__ unsigned long long globaltimer() {
 
 // Coherent (L2) copy of a descriptor: slots are rewritten by the host while
 // a serving kernel runs, so descriptors never come from L1.
+// Through the non-coherent (L1) path: for data that no thread of the
+// launch writes.
+template <class T>
+__device__ __forceinline__ T load_nc(const T *p) {
+  static_assert(sizeof(T) % 16 == 0, "16-byte multiple");
+  T out;
+  const uint4 *src = reinterpret_cast<const uint4 *>(p);
+  uint4 *dst = reinterpret_cast<uint4 *>(&out);
+#pragma unroll
+  for (int i = 0; i < (int)(sizeof(T) / 16); ++i) dst[i] = __ldg(src + i);
+  return out;
+}
+
 template <class T>
 __device__ __forceinline__ T load_cg(const T *p) {
   static_assert(sizeof(T) % 16 == 0, "16-byte multiple");
@@ -1358,37 +1371,43 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
   if (cs.nslots == 1 && !cs.serve) {
     // One code: its descriptor, its pass descriptors (when they fit) and
     // its pair-leaf segments are staged once, so the first claim already
-    // takes the fast path and locates its pass in shared memory.
-    const SlotDesc sd0 = load_cg(&slots[0]);
-    const int np = sd0.npasses;
+    // takes the fast path and locates its pass in shared memory.  Nothing
+    // in the launch writes them, so they are read through L1, and the slot
+    // descriptor by one thread: every CTA reads the same bytes at once, and
+    // an L2 load per warp of the grid queues thousands of requests on one
+    // line (several microseconds before the first claim).
+    if (tid == 0) s_cc.sd = load_nc(&slots[0]);
+    __syncthreads();
+    const int np = s_cc.sd.npasses, nsegs = s_cc.sd.nsegs;
+    const PassDesc *passes = s_cc.sd.passes;
+    const unsigned long long gen = s_cc.sd.seq & kGenMask;
     const int npc = np < V::kPassCache ? np : V::kPassCache;  // the first passes: where every CTA starts
     {
-      const uint4 *src = reinterpret_cast<const uint4 *>(sd0.passes);
+      const uint4 *src = reinterpret_cast<const uint4 *>(passes);
       for (int i = tid; i < npc * (int)(sizeof(PassDesc) / 16); i += kThreads)
-        reinterpret_cast<uint4 *>(s_pc)[i] = __ldcg(src + i);
+        reinterpret_cast<uint4 *>(s_pc)[i] = __ldg(src + i);
     }
     if constexpr (V::kSegCache > kSegPass) {
-      if (sd0.nsegs > 0 && sd0.nsegs <= V::kSegCache) {
-        const uint2 *src = reinterpret_cast<const uint2 *>(sd0.passes + sd0.npasses);
-        for (int i = tid; i < sd0.nsegs; i += kThreads) reinterpret_cast<uint2 *>(s_sc.seg)[i] = __ldcg(src + i);
+      if (nsegs > 0 && nsegs <= V::kSegCache) {
+        const uint2 *src = reinterpret_cast<const uint2 *>(passes + np);
+        for (int i = tid; i < nsegs; i += kThreads) reinterpret_cast<uint2 *>(s_sc.seg)[i] = __ldg(src + i);
         if (tid == 0) {
           s_sc.slot = 0;
-          s_sc.gen = sd0.seq & kGenMask;
+          s_sc.gen = gen;
           s_sc.pass = -2;
         }
       }
     }
+    __syncthreads();
     if (tid == 0) {
-      s_cc.sd = sd0;
       s_cc.slot = 0;
-      s_cc.gen = sd0.seq & kGenMask;
+      s_cc.gen = gen;
       s_cc.P = -1;
       s_npc = npc;
-    }
-    __syncthreads();
-    if (tid == 0 && np > 0) {
-      s_cc.pd = npc ? s_pc[0] : load_cg(&sd0.passes[0]);
-      s_cc.P = 0;
+      if (np > 0) {
+        s_cc.pd = npc ? s_pc[0] : load_nc(&passes[0]);
+        s_cc.P = 0;
+      }
     }
   }
   __syncthreads();
