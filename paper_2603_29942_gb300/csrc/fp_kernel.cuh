@@ -133,6 +133,13 @@ __device__ __forceinline__ T load_cg(const T *p) {
   return out;
 }
 
+// Acquire-release fence at GPU scope: orders this thread's accesses before
+// and after it (a release before a flag write, an acquire after a flag
+// read).  Cheaper than the sequentially consistent __threadfence(), which
+// only the store-then-load handshakes need (one side writes a flag and reads
+// the other's, the other the reverse).
+__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 // The best key is stored inverted (~key) so that an all-zero state means
 // "no codeword yet" and atomicMax keeps the minimum key.
 __device__ __forceinline__ uint64_t best_key(const SlotState *st) { return ~ld_vol(&st->best_key); }
@@ -1231,7 +1238,7 @@ __device__ __forceinline__ void conclude(const CtlStatic &cs, const KParams &kp,
   st->entered = entered;
   st->stop_pass = sp;
   st->status = kDoneFlag | status;
-  __threadfence();
+  fence_acq_rel();  // release: the outcome before the flag
   atomicExch(&st->finished, fin_tag(sd.seq));
   atomicOr(&cs.slot_flags[slot], kSlotFinished);
   if (cs.inflight) {
@@ -1282,39 +1289,99 @@ __device__ __forceinline__ unsigned int count_off(SlotAux *ax, int P, unsigned i
 }
 
 // Termination tests from the frontier on, after a count-off that completed
-// pass P (see finish_task).
-__device__ __forceinline__ void test_frontier(const CtlStatic &cs, const KParams &kp, CtlDyn *cd, const SlotDesc &sd,
-                                              SlotState *st, SlotAux *ax, int slot, int P, const PassDesc &pd) {
-  __threadfence();
+// pass P (see finish_task).  Returns true when this call concluded the code.
+//
+// One round of the walk reads the counts of the next kWalk passes at once
+// (and, after an acquire fence, their least weights), tests every complete
+// pass of them in order, and moves the frontier past them with one
+// compare-and-swap (a test per pass in its own round takes seven dependent
+// round trips, and a CTA that finds several passes complete holds up its
+// CTA for tens of microseconds).  Fences keep the two orders the protocol
+// rests on:
+// a count-off before the completer's read of the frontier, and a move of
+// the frontier before the mover's next read of the counts (so that of two
+// CTAs racing there, one sees the other's write).
+constexpr int kWalk = 4;
+
+__device__ __forceinline__ bool test_frontier(const CtlStatic &cs, const KParams &kp, CtlDyn *cd, const SlotDesc &sd,
+                                              SlotState *st, SlotAux *ax, int slot, int P, const PassDesc &pd,
+                                              const PassDesc *pc, int npc) {
+  int f = -1;      // the frontier, once read or moved by this call
+  int useq = 0;    // the bound after pass f - 1, once known
   for (;;) {
-    const int f = ld_vol(&st->frontier);
-    __threadfence();  // acquire: what the tester of pass f-1 wrote before moving the frontier
-    if (f >= sd.npasses || ld_vol(&st->finished)) return;
-    const PassDesc pf = f == P ? pd : load_cg(&sd.passes[f]);
-    if (atomicAdd(&ax->pass_done[f], 0u) != pf.ntasks) return;  // the frontier pass is still running
-    __threadfence();  // acquire: the records of pass f's tasks
-    const int pm = atomicOr(&ax->pass_min[f], 0);
-    const int u0 = f > 0 ? ld_vol(&ax->useq_after[f - 1]) : 0;
-    int useq = u0 ? u0 : sd.n - sd.k + 2;
-    if (pm) useq = min(useq, 256 - pm);
-    if (sd.pass_times) sd.pass_times[f] = globaltimer();
-    const bool check = !sd.per_round_check || pf.round_end;
-    const bool certified = check && pf.L_after >= useq;
-    if (certified || f + 1 >= sd.npasses) {
-      // the frontier jumps past every pass, so no later pass is ever tested
-      if (atomicCAS(&st->frontier, f, kFrontierDone) == f) conclude(cs, kp, cd, sd, st, ax, slot, f, certified);
-      return;
+    __threadfence();  // store-then-load: the count-off (or the move) before the reads below
+    int fin;
+    if (f < 0) {
+      f = ld_vol(&st->frontier);
+      fin = ld_vol(&st->finished);
+      fence_acq_rel();  // acquire: what the tester of pass f - 1 wrote before moving the frontier
+    } else {
+      fin = ld_vol(&st->finished);
     }
-    ax->useq_after[f] = useq;  // a second tester writes the same value here
-    __threadfence();
-    if (atomicCAS(&st->frontier, f, f + 1) != f) return;  // another CTA moved it
+    if (f >= sd.npasses || fin) return false;
+    const int n = min(kWalk, sd.npasses - f);
+    uint32_t done[kWalk], nt[kWalk];
+    int La[kWalk], re[kWalk];
+#pragma unroll
+    for (int i = 0; i < kWalk; ++i) {
+      done[i] = 0;
+      nt[i] = 1;
+      La[i] = 0;
+      re[i] = 0;
+      if (i < n) {
+        done[i] = (uint32_t)ld_vol(reinterpret_cast<const int32_t *>(&ax->pass_done[f + i]));
+        if (f + i == P) {
+          nt[i] = pd.ntasks;
+          La[i] = pd.L_after;
+          re[i] = pd.round_end;
+        } else if (f + i < npc) {
+          nt[i] = pc[f + i].ntasks;
+          La[i] = pc[f + i].L_after;
+          re[i] = pc[f + i].round_end;
+        } else {
+          nt[i] = __ldcg(&sd.passes[f + i].ntasks);
+          La[i] = __ldcg(&sd.passes[f + i].L_after);
+          re[i] = __ldcg(&sd.passes[f + i].round_end);
+        }
+      }
+    }
+    if (useq == 0) {
+      const int u0 = f > 0 ? ld_vol(&ax->useq_after[f - 1]) : 0;
+      useq = u0 ? u0 : sd.n - sd.k + 2;
+    }
+    if (done[0] != nt[0]) return false;  // the frontier pass is still running
+    fence_acq_rel();  // acquire: the records of the passes seen complete
+    int pm[kWalk];
+#pragma unroll
+    for (int i = 0; i < kWalk; ++i) pm[i] = i < n && done[i] == nt[i] ? ld_vol(&ax->pass_min[f + i]) : 0;
+    int j = 0;
+#pragma unroll
+    for (int i = 0; i < kWalk; ++i) {
+      if (i != j || i >= n || done[i] != nt[i]) continue;  // stop at the first pass still running
+      if (pm[i]) useq = min(useq, 256 - pm[i]);
+      if (sd.pass_times) sd.pass_times[f + i] = globaltimer();
+      const bool check = !sd.per_round_check || re[i];
+      const bool certified = check && La[i] >= useq;
+      if (certified || f + i + 1 >= sd.npasses) {
+        // the frontier jumps past every pass, so no later pass is ever tested
+        if (atomicCAS(&st->frontier, f, kFrontierDone) != f) return false;
+        conclude(cs, kp, cd, sd, st, ax, slot, f + i, certified);
+        return true;
+      }
+      ax->useq_after[f + i] = useq;  // a second tester writes the same value here
+      ++j;
+    }
+    fence_acq_rel();  // release: the bounds before the move
+    if (atomicCAS(&st->frontier, f, f + j) != f) return false;  // another CTA moved it
+    f += j;
   }
 }
 
-__device__ __forceinline__ void finish_task(const CtlStatic &cs, const KParams &kp, CtlDyn *cd, const SlotDesc &sd,
+// Returns true when this count-off concluded the code.
+__device__ __forceinline__ bool finish_task(const CtlStatic &cs, const KParams &kp, CtlDyn *cd, const SlotDesc &sd,
                                             SlotState *st, SlotAux *ax, int slot, int P, const PassDesc &pd,
-                                            unsigned int ndone) {
-  if (count_off(ax, P, ndone) == pd.ntasks) test_frontier(cs, kp, cd, sd, st, ax, slot, P, pd);
+                                            unsigned int ndone, const PassDesc *pc, int npc) {
+  return count_off(ax, P, ndone) == pd.ntasks && test_frontier(cs, kp, cd, sd, st, ax, slot, P, pd, pc, npc);
 }
 
 
@@ -1336,6 +1403,7 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
   __shared__ __align__(16) PassDesc s_pc[V::kPassCache];  // copied in 16-byte pieces
   __shared__ int s_npc;
   __shared__ int s_cmd, s_stage;
+  __shared__ int s_over;  // one-code launch: this CTA concluded the code, so it leaves without a claim
   __shared__ unsigned long long s_count, s_staged_seq;
   __shared__ int s_staged_slot, s_staged_j;
 
@@ -1357,6 +1425,7 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
     s_sc.pass = -1;
     s_sc.gen = 0;
     s_npc = 0;
+    s_over = 0;
   }
   {
     static_assert(kBinomBytes == sizeof(cs.binom->cols), "staged binomial columns");
@@ -1413,7 +1482,8 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
   __syncthreads();
   for (;;) {
     if (tid == 0) {
-      const int cmd = claim(slots, states, cs, kp, cdyn, rr, wait_t0, t_start, &s_cl, s_cc, s_sc, s_pc, s_npc, binom);
+      const int cmd =
+          s_over ? kCmdExit : claim(slots, states, cs, kp, cdyn, rr, wait_t0, t_start, &s_cl, s_cc, s_sc, s_pc, s_npc, binom);
       s_cmd = cmd;
       if (cmd == kCmdRun && cs.serve) {  // keep the serving kernel whole (at most one note per 0.5 ms)
         const unsigned long long now = globaltimer();
@@ -1475,7 +1545,9 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
         atomicAdd(&states[slot].enumerated, s_count);
         atomicAdd(&ax->pass_count[s_cl.pass], s_count);
       }
-      finish_task(cs, kp, cdyn, s_cc.sd, &states[slot], ax, slot, s_cl.pass, s_cc.pd, s_cl.ndone);
+      if (finish_task(cs, kp, cdyn, s_cc.sd, &states[slot], ax, slot, s_cl.pass, s_cc.pd, s_cl.ndone, s_pc, s_npc) &&
+          cs.nslots == 1 && !cs.serve)
+        s_over = 1;
       if (cs.inflight) {
         __threadfence();  // the task's writes before it leaves the slot
         slot_leave(cs, slot);
@@ -1489,9 +1561,9 @@ __global__ void __launch_bounds__(kThreads, FPK_MIN_BLOCKS) bz_kernel(const Slot
     // reset and its result no copy of its own.
     __shared__ int s_last;
     if (tid == 0) {
-      __threadfence();  // this CTA's writes before its count
+      fence_acq_rel();  // release: this CTA's writes before its count
       s_last = atomicAdd(&cdyn->exited, 1u) == gridDim.x - 1 ? 1 : 0;
-      if (s_last) __threadfence();
+      if (s_last) fence_acq_rel();  // acquire: every CTA's writes
     }
     __syncthreads();
     if (s_last) {
