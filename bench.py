@@ -77,12 +77,12 @@ FLUSH_BYTES = 256 << 20
 # version that was profiled; any later change of their code reports null
 # (the hash skips comments and blank lines).
 KERNEL_SOURCES = ["fp_kernel.cuh", "fp_enum.cuh", "fp_bitslice.cuh", "fp_types.h"]
-_SHA_PROFILED = "a2c48fb23779b61af5a4c29fff75515d557943e9f91e3d3792438435a479807a"
+_SHA_PROFILED = "8780d0da516689b5a57dcd3df7282efb232c48e9f0263d9e0ea74675ba62254a"
 PROFILED_TRAFFIC: dict = {  # profiles/bz_kernel_*.md (the command of each capture is there)
-    "f3_n80_k40": {"bytes": 4789248 + 512, "sources_sha256": _SHA_PROFILED},
-    "probe_f3_n80_k40_g8": {"bytes": 4791296 + 57344, "sources_sha256": _SHA_PROFILED},
-    "f7_n40_k20": {"bytes": 9473792 + 0, "sources_sha256": _SHA_PROFILED},
-    "probe_f7_n40_k20_g7": {"bytes": 7574272 + 0, "sources_sha256": _SHA_PROFILED},
+    "f3_n80_k40": {"bytes": 5725952 + 0, "sources_sha256": _SHA_PROFILED},
+    "probe_f3_n80_k40_g8": {"bytes": 5715712 + 0, "sources_sha256": _SHA_PROFILED},
+    "f7_n40_k20": {"bytes": 9477376 + 256, "sources_sha256": _SHA_PROFILED},
+    "probe_f7_n40_k20_g7": {"bytes": 7579136 + 29952, "sources_sha256": _SHA_PROFILED},
 }
 
 
