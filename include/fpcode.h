@@ -202,8 +202,8 @@ typedef struct fpcode_checkpoint {
   int p, n, k;
   int passes_done;     /* passes 0 .. passes_done - 1 of the schedule are complete */
   uint64_t best_key;   /* packed key of the best codeword found (all ones: none) */
-  uint64_t code_hash;  /* FNV-1a of (p, n, k, per_round_check, defer, pair
-                          leaves taken) and G: the schedule and key layout */
+  uint64_t code_hash;  /* 64-bit hash of (p, n, k, per_round_check, defer,
+                          pair leaves taken) and G: the schedule and key layout */
 } fpcode_checkpoint;
 
 /* After fpcode_search_finish returned FPCODE_EBUDGET: the checkpoint of that

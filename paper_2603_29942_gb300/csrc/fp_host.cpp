@@ -7,6 +7,7 @@
 #include <cmath>
 #include <chrono>
 #include <cstring>
+#include <unordered_map>
 #include <string>
 #include <vector>
 
@@ -116,13 +117,17 @@ struct Eliminator {
     const int ia = inv[a];
     // the pivot row scaled to a leading 1: inv(a) * row
     if (ia != 1) std::memcpy(row, mv + (size_t)(ia - 1) * n, (size_t)n);
+    // o - f * (inv(a) * row) = o + ((p - f) inv(a)) * row: the multiple of
+    // row to add for each entry f, once per pivot (a division per row was
+    // most of the elimination's time)
+    int vf[256];
+    for (int f = 1; f < p; ++f) vf[f] = (p - f) * ia % p;
     for (int q = 0; q < k; ++q) {
       if (q == r) continue;
       uint8_t *o = &M[(size_t)q * n];
       const int f = o[c];
       if (!f) continue;
-      const int v = (p - f) * ia % p;  // o - f * (inv(a) * row) = o + ((p - f) inv(a)) * row
-      add_mod(o, mv + (size_t)(v - 1) * n, n, p);
+      add_mod(o, mv + (size_t)(vf[f] - 1) * n, n, p);
     }
     owner[r] = c;
     return true;
@@ -204,7 +209,7 @@ int digit_bits(int p) { return digit_bits_of(p); }
 // taken as m = floor(n/k) full ones, and the passes of each round g summed
 // until the bound after the round, m (g + 1), reaches d.  Only a guide for
 // choosing the leaf form: the search itself certifies the true d.
-double expected_work(int p, int n, int k) {
+double expected_work_of(int p, int n, int k) {
   const double lq = std::log((double)p);
   double lsum = -1e300;
   int d = 1;
@@ -223,6 +228,17 @@ double expected_work(int p, int n, int k) {
     if (m * (g + 1) >= d) break;
   }
   return work;
+}
+// The same, remembered per (p, n, k) by each thread (about fifty lgamma and
+// exp calls; a stream of codes of a few shapes asks for it once per shape).
+double expected_work(int p, int n, int k) {
+  thread_local std::unordered_map<uint32_t, double> memo;
+  const uint32_t key = (uint32_t)p << 16 | (uint32_t)n << 8 | (uint32_t)k;
+  auto it = memo.find(key);
+  if (it != memo.end()) return it->second;
+  const double w = expected_work_of(p, n, k);
+  if (memo.size() < 4096) memo.emplace(key, w);
+  return w;
 }
 constexpr double kPairWork = 1e8;  // pair_leaves 2: pair leaves from this much expected work on
 
@@ -264,24 +280,26 @@ int prepare(int p, int n, int k, const uint8_t *G, const fpcode_opts &opts, Prep
       P->pair_sigp = 0;
     }
   }
-  {  // identity of the code and of the options that shape its schedule and keys
+  {  // identity of the code and of the options that shape its schedule and keys:
+     // eight bytes of G per multiply (a byte at a time was a serial chain of
+     // k n multiplies, about 4 us for a 40 x 80 matrix)
     uint64_t h = 1469598103934665603ull;
-    auto mix = [&h](uint64_t v) {
-      for (int b = 0; b < 8; ++b) {
-        h ^= (v >> (8 * b)) & 0xFF;
-        h *= 1099511628211ull;
-      }
+    auto mix = [&h](uint64_t w) {
+      h = (h ^ w) * 0x9E3779B97F4A7C15ull;
+      h ^= h >> 32;
     };
-    mix((uint64_t)p);
-    mix((uint64_t)n);
-    mix((uint64_t)k);
-    mix((uint64_t)opts.per_round_check);
-    mix((uint64_t)opts.defer);
-    mix((uint64_t)(P->pair ? 1 : 0));
-    for (size_t i = 0; i < (size_t)k * n; ++i) {
-      h ^= G[i];
-      h *= 1099511628211ull;
+    mix((uint64_t)p | (uint64_t)n << 16 | (uint64_t)k << 32);
+    mix((uint64_t)opts.per_round_check | (uint64_t)opts.defer << 8 | (uint64_t)(P->pair ? 1 : 0) << 16);
+    const size_t nb = (size_t)k * n;
+    size_t i = 0;
+    for (; i + 8 <= nb; i += 8) {
+      uint64_t w;
+      std::memcpy(&w, G + i, 8);  // byte order decides the value; it is only compared on one machine
+      mix(w);
     }
+    uint64_t tail = (uint64_t)nb << 56;
+    for (int b = 0; i < nb; ++i, ++b) tail |= (uint64_t)G[i] << (8 * b);
+    mix(tail);
     P->code_hash = h;
   }
   if (P->smem_bytes_per_set() > 96 * 1024) {

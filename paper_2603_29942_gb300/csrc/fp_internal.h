@@ -45,7 +45,7 @@ struct Prepared {
   int pair_sigp = 0;             // words per pair entry (a power of two)
   std::vector<fpk::PairSeg> segs;  // all passes' segments (PassDesc.seg_off, nseg)
   int complete = 0;              // schedule reaches the last level
-  uint64_t code_hash = 0;        // FNV-1a of (p, n, k, per_round_check, defer, pair) and G: schedule and key layout
+  uint64_t code_hash = 0;        // hash of (p, n, k, per_round_check, defer, pair) and G: schedule and key layout
   int seed_u = 0;                // least weight of the g = 1 passes (rows of the Gamma_j), 0: none;
                                  // a search starts with it as its bound (SlotDesc.seed_u)
   int L0 = 0;                    // lower bound before any pass

@@ -516,21 +516,29 @@ def test_checkpoint_and_resume_validation(lib):
 
 
 def _code_hash(prep):
-    """The code identity the library stores (FNV-1a of p, n, k, the two
-    schedule options, whether pair leaves are taken, and G), recomputed here
-    from its definition."""
+    """The code identity the library stores (a 64-bit hash of p, n, k, the
+    two schedule options, whether pair leaves are taken, and G, eight bytes
+    of G per step), recomputed here from its definition."""
+    M = (1 << 64) - 1
     h = 1469598103934665603
-    def mix(v, nbytes=8):
+
+    def mix(w):
         nonlocal h
-        for b in range(nbytes):
-            h ^= (v >> (8 * b)) & 0xFF
-            h = (h * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+        h = ((h ^ w) * 0x9E3779B97F4A7C15) & M
+        h ^= h >> 32
     code = inputs.single("f7_n40_k20")
     pair = 1 if B.fpcode_test_pair_mode(prep) > 0 else 0
-    for v in (code.p, code.n, code.k, 0, 1, pair):  # per_round_check 0, defer 1 (defaults), the leaf form
-        mix(v)
-    for byte in np.asarray(code.G, dtype=np.uint8).reshape(-1):
-        mix(int(byte), 1)
+    mix(code.p | code.n << 16 | code.k << 32)
+    mix(0 | 1 << 8 | pair << 16)  # per_round_check 0, defer 1 (defaults), the leaf form
+    g = np.asarray(code.G, dtype=np.uint8).reshape(-1).tobytes()
+    i = 0
+    while i + 8 <= len(g):
+        mix(int.from_bytes(g[i:i + 8], "little"))
+        i += 8
+    tail = (len(g) << 56) & M
+    for b, byte in enumerate(g[i:]):
+        tail |= byte << (8 * b)
+    mix(tail)
     return h
 
 
