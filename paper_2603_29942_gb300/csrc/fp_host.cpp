@@ -533,6 +533,20 @@ int task_share_of(const fpcode_opts &o, bool last) {
 namespace {
 constexpr uint64_t kSpreadLane = 4;    // a pass of at most this much work per lane of the grid is spread wide
 
+// Quotients of the task plans: 64-bit division only where 32 bits do not
+// hold the operands.
+inline uint64_t div_floor(uint64_t a, uint64_t b) {
+  return (a | b) >> 32 ? a / b : (uint64_t)((uint32_t)a / (uint32_t)b);
+}
+inline uint64_t div_up(uint64_t a, uint64_t b) { return div_floor(a + b - 1, b); }
+// floor(a / b) from a reciprocal of b, corrected to the exact quotient
+inline uint64_t div_floor_rcp(uint64_t a, uint64_t b, double binv) {
+  uint64_t q = (uint64_t)((double)a * binv);
+  while (q > 0 && q * b > a) --q;
+  while ((q + 1) * b <= a) ++q;
+  return q;
+}
+
 void plan_pair_pass(Prepared *P, fpk::PassDesc &d, uint64_t C, bool last) {
   const int k = P->k, b = P->p - 1, g = d.g;
   const int H = g == 2 ? 1 : b / 2;
@@ -543,6 +557,7 @@ void plan_pair_pass(Prepared *P, fpk::PassDesc &d, uint64_t C, bool last) {
     uint64_t E;  // entries per stem
   };
   std::vector<Blk> blks;
+  blks.reserve(g == 2 ? 1 : (size_t)H * (size_t)(k - g + 1));
   if (g == 2) {
     blks.push_back({1, -1, 1, (uint64_t)fpk::pair_entries_above(k, -1, b)});
   } else {
@@ -572,12 +587,18 @@ void plan_pair_pass(Prepared *P, fpk::PassDesc &d, uint64_t C, bool last) {
   auto close = [&]() {
     if (cur_l < 0) return;
     const uint64_t per = (lanes >> cur_l) * (uint64_t)cur_spg;
-    tasks += (uint32_t)((cur_n + per - 1) / per);
+    tasks += (uint32_t)div_up(cur_n, per);
     P->segs.back().task_end = tasks;
   };
+  // the per-block quotients below are the plan's cost (a pass has up to
+  // (p-1)/2 (k-2) blocks, a schedule a few hundred): the pass's divisor
+  // goes through a reciprocal (then corrected to the exact quotient), the
+  // others through 32 bits where they fit
+  const uint64_t Dg = share * C * lanes;
+  const double Dinv = 1.0 / (double)Dg;
+  const int lanes_log = __builtin_ctzll(lanes);  // kThreads is a power of two
   for (auto &x : blks) {
-    const uint64_t T =
-        spread ? T_spread : std::max<uint64_t>(Tmin, rem / (share * C * lanes));
+    const uint64_t T = spread ? T_spread : std::max<uint64_t>(Tmin, div_floor_rcp(rem, Dg, Dinv));
     int l = 0;
     // split a stem's entries while one lane's share exceeds the target, or
     // while the block cannot give every group a stem (at least two entry
@@ -586,12 +607,16 @@ void plan_pair_pass(Prepared *P, fpk::PassDesc &d, uint64_t C, bool last) {
            (((x.E + (1ull << l) - 1) >> l) + kStemCost > T || (lanes >> l) > x.n))
       ++l;
     const uint64_t per_stem = ((x.E + (1ull << l) - 1) >> l) + kStemCost;
-    uint64_t want = spread ? 1 : std::max<uint64_t>(1, (T + per_stem / 2) / per_stem);
+    uint64_t want = spread ? 1 : std::max<uint64_t>(1, div_floor(T + per_stem / 2, per_stem));
     // no more stems per group than spreads the block over every group
-    want = std::min<uint64_t>(want, (x.n + (lanes >> l) - 1) / (lanes >> l));
+    want = std::min<uint64_t>(want, (x.n + (lanes >> l) - 1) >> (lanes_log - l));
+    // at most 65535 stems per group (the segment's field), in whole units
+    // of the coefficient counter, and at least one unit (a unit chosen
+    // before the cap could exceed it and leave zero stems per group)
+    want = std::min<uint64_t>(want, 65535);
     uint64_t unit = 1;
     for (int t = 0; t < L && unit * (uint64_t)b <= want; ++t) unit *= (uint64_t)b;
-    want = std::min<uint64_t>(65535 / unit * unit, want / unit * unit);
+    want = unit == 1 ? want : (uint32_t)want / (uint32_t)unit * unit;
     const int spg = (int)want;
     {  // one segment per block: every stem of a task has the same entries, so its groups finish together
       close();

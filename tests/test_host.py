@@ -663,6 +663,28 @@ def test_pair_tasks_tile_each_pass(name, ctas, lib):
         assert pos == nstems
 
 
+@pytest.mark.parametrize("ctas", [1, 7, 32])
+def test_pair_plan_of_deep_passes_on_small_grids(ctas, lib):
+    """The deepest passes of a p = 7 code on a small grid want more stems per
+    group than a segment holds: the plan caps them (whole units of the
+    coefficient counter, at least one), so every pass still tiles its stems
+    with non-empty tasks.  (Choosing the unit before the cap once left zero
+    stems per group, and counting the segment's tasks divided by zero.)"""
+    code = inputs.single_code(11, 7, 30, 15)
+    pr = _prep(code, pair_leaves=1)
+    assert B.fpcode_test_pair_mode(pr) > 0
+    passes = B.fpcode_prepared_passes(pr)
+    assert max(g for g, *_ in passes) >= 10
+    for i, (g, _j, _Lb, _La, _re, _size, nstems) in enumerate(passes):
+        if g < 2:
+            continue
+        ranges = B.fpcode_test_task_ranges(pr, i, ctas, 0, 8)
+        assert ranges and all(hi > lo for lo, hi in ranges), i
+        if len(ranges) < 1 << 16:  # the whole pass came back: it tiles the stems
+            assert ranges[0][0] == 0 and ranges[-1][1] == nstems, i
+            assert all(a[1] == b[0] for a, b in zip(ranges, ranges[1:])), i
+
+
 @pytest.mark.parametrize("name", ["f3_n80_k40", "f7_n40_k20"])
 def test_pass_slices_keep_the_schedule_plan(name, lib):
     """A slice of a pass (one rank's part of a split search) is planned as
