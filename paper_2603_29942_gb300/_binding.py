@@ -12,6 +12,8 @@ import ctypes
 import os
 from dataclasses import dataclass, field
 
+from collections.abc import Sequence
+
 import numpy as np
 
 from . import build as _build
@@ -418,8 +420,51 @@ def _results_of(res: np.ndarray, ks, ns, wit) -> list[Result]:
     return out
 
 
+class BatchResults(Sequence):
+    """Results of a batch call, as a sequence of Result: a view over the
+    arrays the call filled (fpcode_result records and the witnesses), whose
+    Result objects are built on first access.  Building all of them at once
+    cost more than a millisecond per 512 codes, a sixth of a batch's time."""
+
+    def __init__(self, res: np.ndarray, ks, ns, wit):
+        self._res, self._ks, self._ns, self._wit = res, list(ks), list(ns), wit
+        self._off = [0]
+        for n in self._ns:
+            self._off.append(self._off[-1] + n)
+        self._memo: list[Result | None] = [None] * len(self._ks)
+
+    def __len__(self) -> int:
+        return len(self._ks)
+
+    def __getitem__(self, i):
+        if isinstance(i, slice):
+            return [self[j] for j in range(*i.indices(len(self)))]
+        if i < 0:
+            i += len(self)
+        if not 0 <= i < len(self):
+            raise IndexError(i)
+        r = self._memo[i]
+        if r is None:
+            r = self._memo[i] = _result_at(self._res, i, self._ks[i], self._ns[i],
+                                           self._wit[self._off[i]:self._off[i + 1]] if self._wit is not None else None)
+        return r
+
+    def field(self, name: str) -> np.ndarray:
+        """One field of every result at once (e.g. "d", "status", "enumerated")."""
+        return self._res[name]
+
+
+def _result_at(res: np.ndarray, i: int, k: int, n: int, w) -> Result:
+    r = res[i]
+    m = int(r["m"])
+    return Result(int(r["status"]), int(r["d"]), int(r["L"]), int(r["U"]), m, int(r["npasses"]),
+                  int(r["enumerated"]), r["counts"][:k + 1].tolist(), r["kj"][:max(m, 0)].tolist(),
+                  float(r["t_prepare_ms"]), float(r["t_kernel_ms"]), float(r["t_total_ms"]), w, int(r["launch"]),
+                  int(r["best_key"]))
+
+
 def fpcode_min_distance_batch(codes, stream=None, opts: fpcode_opts | None = None, budgets=None,
-                              want_witness: bool = True) -> list[Result]:
+                              want_witness: bool = True) -> BatchResults:
     """codes: objects with p, n, k, G (e.g. inputs.Code).  The codes'
     matrices are packed into one buffer and the descriptors and results are
     numpy structured arrays with the C layouts, so the call's Python cost
@@ -447,7 +492,7 @@ def fpcode_min_distance_batch(codes, stream=None, opts: fpcode_opts | None = Non
                                            ctypes.cast(res.ctypes.data, ctypes.POINTER(fpcode_result)),
                                            wit.ctypes.data_as(_U8P) if want_witness else None),
            "fpcode_min_distance_batch")
-    return _results_of(res[:num], ks, ns, wit)
+    return BatchResults(res[:num], ks, ns, wit)
 
 
 def _descs(codes, budgets=None):

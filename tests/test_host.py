@@ -738,3 +738,33 @@ def test_tune_search_moves_until_a_round_finds_nothing(lib):
     for v in range(4):  # a coordinate-wise minimum over the runnable points
         assert cost2[v, b1] < 0 or cost2[v, b1] >= cost2[b0, b1]
         assert cost2[b0, v] < 0 or cost2[b0, v] >= cost2[b0, b1]
+
+
+def test_batch_results_view_equals_eager_results():
+    """The batch call's results view builds each Result on first access from
+    the returned arrays: every field, the witness slices, negative indices
+    and slices equal the eagerly built list."""
+    codes = inputs.batch_codes(64)
+    ns, ks = [c.n for c in codes], [c.k for c in codes]
+    rng = np.random.default_rng(1)
+    res = np.zeros(len(codes), dtype=B._RESULT_DT)
+    for f in ("status", "d", "L", "U", "m", "npasses", "launch"):
+        res[f] = rng.integers(0, 20, len(codes))
+    res["enumerated"] = rng.integers(0, 10 ** 9, len(codes))
+    res["best_key"] = rng.integers(0, 2 ** 62, len(codes), dtype=np.int64).astype(np.uint64)
+    res["counts"] = rng.integers(0, 1000, (len(codes), 65))
+    res["kj"] = rng.integers(0, 60, (len(codes), 255))
+    res["t_kernel_ms"] = rng.random(len(codes))
+    wit = rng.integers(0, 7, sum(ns)).astype(np.uint8)
+    eager = B._results_of(res, ks, ns, wit)
+    view = B.BatchResults(res, ks, ns, wit)
+    assert len(view) == len(eager)
+
+    def fields(r):
+        return (r.status, r.d, r.L, r.U, r.m, r.npasses, r.enumerated, r.counts, r.kj, r.t_prepare_ms, r.t_kernel_ms,
+                r.t_total_ms, r.launch, r.best_key, r.witness.tolist())
+    assert [fields(r) for r in view] == [fields(r) for r in eager]
+    assert fields(view[-1]) == fields(eager[-1]) and [fields(r) for r in view[3:9]] == [fields(r) for r in eager[3:9]]
+    assert (view.field("d") == np.array([r.d for r in eager])).all()
+    with pytest.raises(IndexError):
+        view[len(codes)]
