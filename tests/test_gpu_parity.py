@@ -207,6 +207,35 @@ def test_batch_equals_alone():
             check_witness(c, rb.d, rb.witness)
 
 
+def test_random_small_codes_against_oracle():
+    """A seeded sweep of small random codes (p in {3, 5, 7, 11, 31, 127},
+    n <= 34, both leaf forms where they apply, both schedule modes, with
+    and without a budget): status, d, L, U and the per-level counts equal
+    the oracle's, and every certified search's witness has weight d and
+    lies in the code."""
+    import random
+    rng = random.Random(20261203)
+    seen = 0
+    for i in range(150):
+        p = rng.choice([3, 3, 5, 7, 7, 11, 31, 127])
+        n = rng.randint(6, 34)
+        k = rng.randint(1, min(n, 14 if p <= 7 else 8))
+        unlimited_ok = p == 3 or (p <= 7 and k <= 10)
+        budget = rng.choice([0, 10 ** 5, 10 ** 6] if unlimited_ok else [10 ** 5, 10 ** 6])
+        prc = rng.choice([0, 1])
+        c = inputs.single_code(12000 + i, p, n, k)
+        r = oracle.bz(c, budget=budget, per_round_check=bool(prc), threads=1)
+        for pair in ((0, 1) if p in (3, 7) and k >= 3 else (0,)):
+            g, _ = run(c, budget=budget, per_round_check=prc, pair_leaves=pair)
+            case = (i, p, n, k, budget, prc, pair)
+            assert (g.status, g.L, g.U, g.counts) == (status_of_oracle(r.status), r.L, r.U, r.counts), case
+            if r.status == oracle.OK:
+                assert g.d == r.d, case
+                check_witness(c, g.d, g.witness)
+            seen += 1
+    assert seen >= 150
+
+
 def test_batch_against_oracle_mixed_primes():
     rng = np.random.default_rng(77)
     codes = []
